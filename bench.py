@@ -1,0 +1,336 @@
+"""Benchmark of the RPCholesky-preconditioned CG hot path on one GB300.
+
+Workload (the configuration the headline metric is quoted on): full-data KRR
+with mixed precision and iterative refinement -- N = 100000 points, d = 16,
+x uniform on [0,1]^16 with 5% of the rows duplicated plus 1e-6 jitter,
+Gaussian sigma = 0.5, mu = 1e-7 (shift mu N), 4 right-hand sides
+y_r = sum_j cos(2 pi r x_j) + noise, RPCholesky rank 1000 (B = 100), inner
+float32 PCG with float64 refinement to relative residual 1e-6.  Inputs are
+synthetic (seeded), resident in HBM before the timed region.
+
+One step = the whole hot path once: krr_rpcholesky (pivot sampling, column
+evaluation, Schur update, block Cholesky, triangular solve, residual
+downdate) + krr_pcg_solve (Woodbury core, fused products, preconditioner
+applies, PCG updates, float64 refinement residuals).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica of the step
+(the method has no data-parallel exchange at this size); value = entries of
+all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-1e-6 residual & kernel evals/s vs plain FP64 path; p50/p99 latency"
+UNIT = "kernel_evals/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=100_000, help="points (workload size)")
+    ap.add_argument("--fp64-path", action="store_true",
+                    help="also time the plain float64 path (one step, slow)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist, rank, world
+    torch.cuda.set_device(0)
+    return None, 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def entries_rpcholesky(N, k):
+    # Alg. 3 evaluates the diagonal and one kernel column per pivot
+    return float(N) * (k + 1)
+
+
+def run_native(args):
+    import torch
+    import paper_2304_12465_gb300 as K
+    from inputs import make_c2_mixed
+
+    dist, rank, world = dist_setup(args.gpus)
+    K.load()
+    w = make_c2_mixed(n=args.n)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X = torch.from_numpy(w.X).to(dev)
+    Y = torch.from_numpy(w.Y).to(dev)
+    alpha = torch.empty_like(Y)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(profile=False):
+        f = K.krr_rpcholesky(X, w.kernel, w.sigma, w.k, w.block, seed=w.seed)
+        a, info = K.krr_pcg_solve(X, w.kernel, w.sigma, Y, w.mu, f, tol=w.tol, prec="mixed",
+                                  out=alpha)
+        rank_ = f.rank
+        f.free()
+        if info["status"] != "KRR_OK":
+            raise RuntimeError(f"solve did not converge: {info}")
+        info["entries"] = entries_rpcholesky(w.N, rank_) + info["kernel_entries"]
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    K.krr_set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = K.krr_launch_count()
+    step_ms, infos = [], []
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    launches = K.krr_launch_count() - launches0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    K.krr_set_profiling(False)
+
+    total_ms = float(sum(step_ms))
+    entries = float(sum(i["entries"] for i in infos))
+    if dist:
+        t = torch.tensor([total_ms, entries], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, entries = float(tmax[0]), float(t[1])
+    value = entries / (total_ms / 1e3)
+
+    # roofline of the dominant kernel: the float32 fused product
+    kmv_ms = sum(i["kmv_ms"] for i in infos)
+    kmv_n = sum(i["kmv_launches"] for i in infos)
+    per_launch_ms = kmv_ms / max(kmv_n, 1)
+    flop_per_entry = 2 * w.d + 1 + 2 * w.m          # dot (d FMA) + c_i + c_j + m FMA
+    flop_per_launch = flop_per_entry * float(w.N) * w.N
+    achieved = flop_per_launch / (per_launch_ms / 1e3) / 1e12
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA units x clock
+    kmv64_ms = sum(i["kmv64_ms"] for i in infos)
+    kmv64_n = sum(i["kmv64_launches"] for i in infos)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"full-data KRR, N={w.N}, d={w.d}, 5% near-duplicates, "
+                               f"Gaussian sigma={w.sigma}, mu={w.mu}, m={w.m} RHS, "
+                               f"RPCholesky k={w.k} B={w.block}, mixed precision + float64 "
+                               f"refinement, tol={w.tol}",
+                   "N": w.N, "d": w.d, "m": w.m, "k": w.k, "block": w.block,
+                   "kernel": "gaussian", "sigma": w.sigma, "mu": w.mu, "tol": w.tol,
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_tol_s": total_ms / args.steps / 1e3,
+        "pcg": {"iters": [i["iters"] for i in infos],
+                "outer_refinements": [i["outer_refinements"] for i in infos],
+                "rel_residual_fp64": [i["rel_residual"] for i in infos],
+                "t_build_core_s": [i["t_build_s"] for i in infos],
+                "t_solve_s": [i["t_solve_s"] for i in infos],
+                "kmv32_ms_per_launch": per_launch_ms, "kmv32_launches": kmv_n,
+                "kmv64_ms_per_launch": kmv64_ms / max(kmv64_n, 1),
+                "kmv64_launches": kmv64_n},
+        "roofline": {"kernel": "kmv32_kernel (fused float32 product)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"152 SM x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                                   "(max SM clock); derived, not measured",
+                     "flop_per_entry": flop_per_entry,
+                     "entries_per_launch": float(w.N) * w.N},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and args.fp64_path:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = K.krr_rpcholesky(X, w.kernel, w.sigma, w.k, w.block, seed=w.seed)
+        a64, i64 = K.krr_pcg_solve(X, w.kernel, w.sigma, Y, w.mu, f, tol=w.tol, prec="fp64")
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        f.free()
+        result["fp64_path"] = {"time_to_tol_s": t64, "iters": i64["iters"],
+                               "status": i64["status"],
+                               "speedup_mixed_vs_fp64": t64 / (total_ms / args.steps / 1e3)}
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    Xh, Yh = w.X, w.Y
+    alpha_h = np.empty_like(Yh)
+    t0 = time.perf_counter()
+    f = K.krr_rpcholesky(Xh, w.kernel, w.sigma, w.k, w.block, seed=w.seed)
+    a_h, info_h = K.krr_pcg_solve(Xh, w.kernel, w.sigma, Yh, w.mu, f, tol=w.tol, prec="mixed",
+                                  out=alpha_h)
+    t_e2e = time.perf_counter() - t0
+    e2e_entries = entries_rpcholesky(w.N, f.rank) + info_h["kernel_entries"]
+    f.free()
+    result["e2e"] = {"value": e2e_entries * world / t_e2e, "unit": UNIT,
+                     "h2d_bytes_per_step": int(2 * Xh.nbytes + Yh.nbytes),
+                     "d2h_bytes_per_step": int(alpha_h.nbytes),
+                     "seconds_per_step": t_e2e}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, target_s: float = 6.0):
+    """The oracle's float64 product on a bounded sample of rows of the same
+    workload, timed on this host's cores; kernel evaluations per second."""
+    import oracle as O
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((w.m, w.N))
+    rows = np.sort(rng.choice(w.N, 64, replace=False))
+    t0 = time.perf_counter()
+    O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows)
+    dt = time.perf_counter() - t0
+    nrows = int(min(w.N, max(64, 64 * target_s / max(dt, 1e-3))))
+    rows = np.sort(rng.choice(w.N, nrows, replace=False))
+    t0 = time.perf_counter()
+    O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nrows * float(w.N) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"float64 oracle product (A + lam I)V, {nrows} of {w.N} rows x {w.N} "
+                      f"columns, m={w.m}, d={w.d}, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, per step a bounded sample of the
+    same workload (kernel entries of the product on a row subset)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from inputs import make_c2_mixed
+    import oracle as O
+    w = make_c2_mixed(n=args.n)
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((w.m, w.N))
+    nrows = 256
+    rows = np.sort(rng.choice(w.N, nrows, replace=False))
+    for _ in range(args.warmup):
+        O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows[:32])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows)
+    dt = time.perf_counter() - t0
+    value = args.steps * nrows * float(w.N) / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"float64 oracle product (A + lam I)V on {nrows} of {w.N} rows x {w.N} columns "
+              f"per step, m={w.m}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"full-data KRR, N={w.N}, d={w.d}, Gaussian sigma={w.sigma}, "
+                               f"mu={w.mu}, m={w.m} RHS (oracle row sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

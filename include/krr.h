@@ -1,0 +1,247 @@
+/*
+ * krr.h -- C ABI of the GB300 (sm_103a) kernel ridge regression library.
+ *
+ * Method: "Robust, randomized preconditioning for kernel ridge regression"
+ * (Diaz, Epperly, Frangella, Tropp, Webber).
+ *   full-data KRR   (A + lambda I) alpha = y                     Sec. 2.1
+ *   RPCholesky preconditioned CG                                 Alg. 1, Alg. 3
+ *   restricted KRR  [A(S,:)A(:,S) + lambda A(S,S)] beta = A(S,:) y   Sec. 2.2
+ *   KRILL preconditioned CG                                      Alg. 2
+ * with A_ij = kappa(x_i, x_j) generated on the fly and never stored.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - X is N x d, row-major float64 (point i is X[i*d .. i*d+d-1]), 1 <= d <= 32.
+ * - Right-hand-side / solution blocks are N x m (or k x m) column-major
+ *   float64: column c starts at c*N (c*k).  1 <= m <= 16.
+ * - mu is the regularisation per data point; the shift is lambda = mu * N
+ *   (the paper's mu, Sec. 2.1.2, quoted there as mu / N).
+ * - Array arguments may be host or device pointers: the library asks the CUDA
+ *   runtime which one it got and copies host data in / out itself.  Device
+ *   pointers must belong to the current device.  The caller owns every array
+ *   it passes; handles (krr_factor, krill_precond) own their device memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Work is enqueued on it; calls return after their results are complete
+ *   (each call synchronises the stream before returning).
+ * - No call aborts, traps or exits.  Invalid arguments return KRR_EINVAL
+ *   before any launch; CUDA failures return KRR_ECUDA.  krr_last_error()
+ *   describes the last failure of the calling thread.
+ * - The library is built for sm_103a only and never falls back to the CPU.
+ */
+#ifndef KRR_GB300_H
+#define KRR_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KRR_API __attribute__((visibility("default")))
+#else
+#define KRR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KRR_OK = 0,
+    KRR_EINVAL = 1,      /* bad argument (checked before any launch)          */
+    KRR_ENOMEM = 2,      /* device allocation failed                          */
+    KRR_ECUDA = 3,       /* CUDA runtime error                                */
+    KRR_ECHOL = 4,       /* non-positive pivot in a k x k Cholesky factor     */
+    KRR_EBREAKDOWN = 5,  /* p^T M p <= 0 or NaN in PCG                        */
+    KRR_ENOCONV = 6,     /* maxit reached before the tolerance                */
+    KRR_ETIMEOUT = 7     /* a bounded device-side wait gave up                */
+} krr_status;
+
+typedef enum {
+    KRR_GAUSSIAN = 0,    /* exp(-||x-y||^2 / (2 sigma^2)), Sec. 2.1.2          */
+    KRR_LAPLACE_L1 = 1,  /* exp(-||x-y||_1 / sigma), l1 distance, Sec. 5.1     */
+    KRR_MATERN52 = 2     /* (1 + q + q^2/3) exp(-q), q = sqrt(5)||x-y||/sigma;
+                            not in the paper: textbook Matern, nu = 5/2        */
+} krr_kernel;
+
+typedef enum {
+    KRR_PREC_FP64 = 0,   /* every step in float64                             */
+    KRR_PREC_MIXED = 1   /* float32 kernel tiles and inner PCG, float64 outer
+                            iterative refinement, CG scalars and k x k core    */
+} krr_precision;
+
+typedef struct krr_factor krr_factor;        /* RPCholesky factor F, pivots S */
+typedef struct krill_precond krill_precond;  /* KRILL preconditioner          */
+
+typedef struct {
+    int iters;               /* PCG iterations (max over columns; for the
+                                mixed path, summed over refinement steps)    */
+    int outer_refinements;   /* float64 residual recomputations (mixed path)  */
+    int rank;                /* factor rank used                              */
+    int reserved;
+    double rel_residual;     /* max over columns of ||y - M x|| / ||y||,
+                                recomputed in float64 after the solve         */
+    double kernel_entries;   /* kernel entries kappa(x_i, x_j) evaluated      */
+    double t_build_s;        /* preconditioner core build time (s)            */
+    double t_solve_s;        /* PCG time (s)                                  */
+    double kmv_ms;           /* summed device time of the float32 fused
+                                product kernel (CUDA events on `stream`);
+                                filled only while krr_set_profiling(1) is on  */
+    int kmv_launches;        /* number of float32 fused-product launches      */
+    int kmv64_launches;      /* number of float64 fused-product launches      */
+    double kmv64_ms;         /* summed device time of the float64 product     */
+} krr_info;
+
+/* ------------------------------------------------------------------------ */
+/* Fused matrix-free product (Alg. 1 "Product"):                             */
+/*   Y = (A + lambda I) V,  A_ij = kappa(x_i, x_j), never stored.            */
+/* precision KRR_PREC_FP64 evaluates in float64 with direct differences;     */
+/* KRR_PREC_MIXED evaluates kernel tiles in float32 (distances from row      */
+/* norms of centred points) and accumulates in float32.                      */
+/* V, Y: N x m column-major float64.  Y may not alias V.                     */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern,
+                       double sigma, double lambda, const double *V, int m,
+                       double *Y, krr_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Pivot sampling of Alg. 3: ndraw i.i.d. indices with probability           */
+/* proportional to the residual diagonal dres (length N).  Weights are the    */
+/* fixed-point integers floor(min(dres_i, 1) * 2^F) for dres_i > dfloor and   */
+/* 0 otherwise, F = 62 - ceil(log2 N); draw j of block t uses word 0 of       */
+/* Philox4x64-10 with counter (t, j, 0, 0) and key (seed,                     */
+/* 0x5250434850495653), target = floor(u W / 2^64), and picks the smallest i  */
+/* whose inclusive prefix sum exceeds the target.  Writes ndraw indices to    */
+/* `draws` and sets *ndraw_out = ndraw, or *ndraw_out = 0 (and no draws) when */
+/* every weight is zero.  0 < ndraw <= 1024; dres entries must be <= 1 in     */
+/* meaning (larger values count as 1).                                        */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_rpc_sample(const double *dres, int64_t N, double dfloor,
+                                  uint64_t seed, uint64_t t, int ndraw, int64_t *draws,
+                                  int *ndraw_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Blocked RPCholesky (Alg. 3) with block size `block` (0 = Alg. 1's rule     */
+/* min(100, ceil(k/10))), rank k <= min(N, 4096), block <= 128.  Each block   */
+/* draws min(block, k - i) pivots (krr_rpc_sample with t = block counter and  */
+/* dfloor = the drop threshold N * 2^-52 * max_i A_ii),                       */
+/* keeps the first occurrence of each, forms G = A(:,S') - F F(S',:)^T,       */
+/* factors G(S',S') pivot by pivot dropping any candidate whose Schur value   */
+/* is <= N * 2^-52 * max_i A_ii, appends G R^{-1} to F and subtracts its      */
+/* squared row norms from the residual diagonal; every candidate of a block   */
+/* gets residual 0.  Stops early (rank < k) if every weight becomes zero.     */
+/* All arithmetic is float64.  *F_out receives a new handle (free with        */
+/* krr_factor_free).                                                          */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_rpcholesky(const double *X, int64_t N, int d, krr_kernel kern,
+                          double sigma, int k, int block, uint64_t seed,
+                          void *stream, krr_factor **F_out);
+
+/* Rank reached, number of blocks drawn and N of a factor. */
+KRR_API krr_status krr_factor_info(const krr_factor *F, int64_t *N, int *rank,
+                           int *nblocks);
+
+/* Copy a factor out: F_out N x rank column-major float64, pivots int64[rank]
+ * in column order, dres float64[N] (the final residual diagonal).  Any output
+ * pointer may be NULL to skip it. */
+KRR_API krr_status krr_factor_export(const krr_factor *F, double *F_out, int64_t *pivots,
+                             double *dres);
+
+KRR_API void krr_factor_free(krr_factor *F);
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioner of Alg. 1 in Woodbury form (identical in exact arithmetic   */
+/* to the paper's SVD form):                                                  */
+/*   Z = P^{-1} R,  P = F F^T + lambda I,                                    */
+/*   P^{-1} = lambda^{-1} (I - F (lambda I + F^T F)^{-1} F^T).               */
+/* The k x k core lambda I + F^T F is factored in float64 (KRR_ECHOL if it is */
+/* not numerically positive definite) and cached in the factor per (mu,       */
+/* precision).  KRR_PREC_MIXED streams F in float32.  R, Z: N x m.           */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_precond_apply(const krr_factor *F, double mu, const double *R,
+                             int m, double *Z, krr_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* RPCholesky-preconditioned CG (Alg. 1; PCG as in Sec. 3: zero initial      */
+/* iterate, each column stops when its recursive relative residual            */
+/* ||r|| / ||y|| <= tol).                                                     */
+/*   KRR_PREC_FP64 : float64 throughout.                                      */
+/*   KRR_PREC_MIXED: iterative refinement -- an outer float64 loop x += d,    */
+/*     r = y - (A + lambda I) x recomputed with the float64 product, around   */
+/*     an inner float32 PCG (float32 kernel tiles, float64 CG scalars) that   */
+/*     solves (A + lambda I) d = r to a loose tolerance; stops when the       */
+/*     float64 relative residual is <= tol.                                   */
+/* F may be NULL (no preconditioner beyond lambda^{-1} I).  maxit bounds the  */
+/* PCG iterations per column (<= 0 selects 1000).  Y, alpha_out: N x m.       */
+/* info (optional) receives iteration counts, the float64 residual and times. */
+/* Returns KRR_ENOCONV (with the best iterate in alpha_out) if the tolerance  */
+/* was not reached.                                                           */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel kern,
+                         double sigma, const double *Y, int m, double mu,
+                         const krr_factor *F, double tol, int maxit,
+                         krr_precision prec, double *alpha_out, void *stream,
+                         krr_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* Sparse sign embedding of Alg. 2 (Sec. 2.2.1): Phi is s x N; column n has   */
+/* zeta distinct rows, entries +-zeta^{-1/2}.  Rows of column n are drawn from */
+/* Philox4x64-10 words (counter (n, q, 0, 0), key (seed, 0x53534531524f5753), */
+/* q = 0, 1, ..., words 0..3 in order) as floor(u s / 2^64), rejecting        */
+/* repeats; the sign of the t-th kept row is bit t of word 0 of counter       */
+/* (n, 0, 0, 0), key (seed, 0x535345325349474e), bit 1 meaning negative.      */
+/* rows: int32 N x zeta, vals: float64 N x zeta (row-major, acceptance order).*/
+/* 1 <= zeta <= min(s, 64).                                                   */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_sparse_sign(int64_t N, int s, int zeta, uint64_t seed,
+                           int32_t *rows, double *vals, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* KRILL build (Alg. 2):                                                      */
+/*   H = lambda A(S,S) + N 2^-52 tr(A(S,S)) I,  Phi = SparseSign(s, N, zeta), */
+/*   B = Phi A(:,S),  P = B^T B + H,  C = Cholesky(P) (float64).              */
+/* centers: int64[k], distinct, in [0, N) (the paper samples them uniformly). */
+/* sketch_rows s (0 = 2k), zeta (0 = ceil(ln(k+1))).  The handle keeps a      */
+/* device copy of X and the centers.  k <= 8192.                              */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krill_build(const double *X, int64_t N, int d, krr_kernel kern,
+                       double sigma, const int64_t *centers, int k, double mu,
+                       int sketch_rows, int zeta, uint64_t seed, void *stream,
+                       krill_precond **P_out);
+
+/* Copy KRILL intermediates out (any pointer may be NULL): H, P and the upper
+ * Cholesky factor C (P = C^T C) as k x k column-major float64, and the sketch
+ * B as s x k column-major float64; *s_out receives s. */
+KRR_API krr_status krill_export(const krill_precond *P, double *H, double *Bsk,
+                        double *Pm, double *Cu, int *s_out);
+
+/* ------------------------------------------------------------------------ */
+/* KRILL PCG (Alg. 2): solves [A(S,:)A(:,S) + H] beta = A(S,:) y with the     */
+/* preconditioner beta -> C^{-1}(C^{-T} beta).  Iterative refinement: the     */
+/* right-hand side and each outer residual use float64 kernel entries; the    */
+/* inner PCG (float64 k-vectors and CG scalars) regenerates the N x k block   */
+/* A(:,S) in float32 for its products.  Stops when the float64 relative       */
+/* residual is <= tol.  Y: N x m, beta_out: k x m.                            */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krill_solve(const krill_precond *P, const double *Y, int m,
+                       double tol, int maxit, double *beta_out, void *stream,
+                       krr_info *info);
+
+KRR_API void krill_free(krill_precond *P);
+
+/* Timing instrumentation: while on (non-zero), solves record CUDA events
+ * around every fused-product launch on the caller's stream and report the
+ * summed device time in krr_info.kmv_ms / kmv_launches. */
+KRR_API void krr_set_profiling(int on);
+
+/* Message for the last failure on the calling thread ("" if none). */
+KRR_API const char *krr_last_error(void);
+
+/* Library version string. */
+KRR_API const char *krr_version(void);
+
+/* Number of kernels this library has launched in the process so far. */
+KRR_API uint64_t krr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRR_GB300_H */

@@ -52,9 +52,10 @@ def lib():
         L.orc_fixed_point_bits.restype = C.c_int
         L.orc_fixed_point_bits.argtypes = [C.c_int64]
         L.orc_fixed_point_weight.restype = C.c_uint64
-        L.orc_fixed_point_weight.argtypes = [C.c_double, C.c_int]
+        L.orc_fixed_point_weight.argtypes = [C.c_double, C.c_double, C.c_int]
         L.orc_rpc_sample.restype = C.c_int
-        L.orc_rpc_sample.argtypes = [dp, C.c_int64, C.c_uint64, C.c_uint64, C.c_int, ip]
+        L.orc_rpc_sample.argtypes = [dp, C.c_int64, C.c_double, C.c_uint64, C.c_uint64,
+                                     C.c_int, ip]
         L.orc_rpcholesky.restype = C.c_int
         L.orc_rpcholesky.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
                                      C.c_int, C.c_int, C.c_uint64, dp, ip, dp, ip, dp]
@@ -156,15 +157,22 @@ def fixed_point_bits(N: int) -> int:
     return lib().orc_fixed_point_bits(N)
 
 
-def fixed_point_weight(dres: float, fbits: int) -> int:
-    return int(lib().orc_fixed_point_weight(dres, fbits))
+def fixed_point_weight(dres: float, fbits: int, dfloor: float = 0.0) -> int:
+    return int(lib().orc_fixed_point_weight(dres, dfloor, fbits))
 
 
-def rpc_sample(dres, seed: int, t: int, ndraw: int) -> np.ndarray:
-    """Draws of block t of Alg. 3 (empty if every weight is zero)."""
+def drop_threshold(N: int, maxdiag: float = 1.0) -> float:
+    """N eps max_i A_ii: drop threshold of the block Cholesky and floor of the
+    sampling weights."""
+    return N * EPS_MACH * maxdiag
+
+
+def rpc_sample(dres, seed: int, t: int, ndraw: int, dfloor: float = 0.0) -> np.ndarray:
+    """Draws of block t of Alg. 3 (empty if every weight is zero); residuals
+    at or below dfloor carry no weight."""
     dres = _f64(dres)
     out = np.empty(ndraw, dtype=np.int64)
-    got = lib().orc_rpc_sample(_d(dres), dres.shape[0], seed, t, ndraw, _i(out))
+    got = lib().orc_rpc_sample(_d(dres), dres.shape[0], dfloor, seed, t, ndraw, _i(out))
     return out[:got]
 
 

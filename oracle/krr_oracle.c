@@ -161,7 +161,9 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
 /* ------------------------------------------------------------------------ */
 /* Pivot sampling of Alg. 3: i.i.d. draws s ~ d / Sum(d).                     */
 /* Reading used for bit reproducibility: weights are the fixed-point values  */
-/* w_i = floor(clamp(d_i, 0, 1) * 2^F), F = 62 - ceil(log2 N), summed as     */
+/* w_i = floor(min(d_i, 1) * 2^F) for d_i > dfloor and 0 otherwise (dfloor  */
+/* is the drop threshold below, so numerically zero residuals are never     */
+/* drawn), F = 62 - ceil(log2 N), summed as                                 */
 /* 64-bit integers; draw j of block t takes u = Philox(counter (t, j, 0, 0), */
 /* key (seed, pivot tag)) word 0, target = floor(u * W / 2^64), and returns  */
 /* the smallest i whose inclusive prefix sum exceeds target.  The diagonal    */
@@ -177,22 +179,22 @@ static int ceil_log2_i64(int64_t n)
 
 int orc_fixed_point_bits(int64_t N) { return 62 - ceil_log2_i64(N); }
 
-uint64_t orc_fixed_point_weight(double dres, int fbits)
+uint64_t orc_fixed_point_weight(double dres, double dfloor, int fbits)
 {
     double v = dres;
-    if (!(v > 0.0)) return 0;           /* negative, zero or NaN */
+    if (!(v > 0.0) || !(v > dfloor)) return 0;   /* at or below the floor, or NaN */
     if (v > 1.0) v = 1.0;
     return (uint64_t)floor(ldexp(v, fbits));
 }
 
-int orc_rpc_sample(const double *dres, int64_t N, uint64_t seed, uint64_t t,
-                   int ndraw, int64_t *draws)
+int orc_rpc_sample(const double *dres, int64_t N, double dfloor, uint64_t seed,
+                   uint64_t t, int ndraw, int64_t *draws)
 {
     int fbits = orc_fixed_point_bits(N);
     uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
     uint64_t run = 0;
     for (int64_t i = 0; i < N; ++i) {
-        run += orc_fixed_point_weight(dres[i], fbits);
+        run += orc_fixed_point_weight(dres[i], dfloor, fbits);
         W[i] = run;
     }
     if (run == 0) { free(W); return 0; }
@@ -227,7 +229,8 @@ int orc_rpc_sample(const double *dres, int64_t N, uint64_t seed, uint64_t t,
 /* Cholesky runs pivot by pivot in S' order; a candidate whose Schur value   */
 /* is <= N * eps * max_i A_ii is dropped from S' (not resampled).  The scale */
 /* is the initial diagonal, so a block whose candidates all have rounding-   */
-/* level residuals cannot pass the test.                                     */
+/* level residuals cannot pass the test.  The same threshold is the floor    */
+/* below which residuals carry no sampling weight.                           */
 /* Every candidate drawn in a block, kept or dropped, gets d = 0 exactly.    */
 /* F is N x k column-major and must be zeroed by the caller; S receives the  */
 /* kept pivots in column order; dres receives the final residual diagonal.   */
@@ -257,11 +260,12 @@ int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
     double *R = (double *)malloc(sizeof(double) * (size_t)B * (size_t)B);
     double *Fn = (double *)malloc(sizeof(double) * (size_t)N * (size_t)B);
 
+    const double thr = (double)N * DBL_EPSILON * maxdiag;
     int rank = 0;
     uint64_t t = 0;
     while (rank < k) {
         int nd = (k - rank < B) ? (k - rank) : B;
-        int got = orc_rpc_sample(dres, N, seed, t, nd, draws);
+        int got = orc_rpc_sample(dres, N, thr, seed, t, nd, draws);
         ++t;
         if (got == 0) break;
 
@@ -284,7 +288,6 @@ int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
         }
 
         /* R = Cholesky(G(S', S')), upper triangular, with the drop rule */
-        double thr = (double)N * DBL_EPSILON * maxdiag;
         memset(R, 0, sizeof(double) * (size_t)B * (size_t)B);
         int na = 0;
         for (int c = 0; c < nc; ++c) {

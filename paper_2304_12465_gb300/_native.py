@@ -1,0 +1,96 @@
+"""ctypes declarations of the C ABI in include/krr.h.
+
+Loading builds the sm_103a library first if it is missing or stale; there is
+no CPU implementation to fall back to, so a missing CUDA toolkit or library is
+an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+KRR_OK, KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, KRR_ECHOL, KRR_EBREAKDOWN, KRR_ENOCONV, \
+    KRR_ETIMEOUT = range(8)
+STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA",
+                4: "KRR_ECHOL", 5: "KRR_EBREAKDOWN", 6: "KRR_ENOCONV", 7: "KRR_ETIMEOUT"}
+
+GAUSSIAN, LAPLACE_L1, MATERN52 = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class KrrInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_refinements", C.c_int), ("rank", C.c_int),
+                ("reserved", C.c_int), ("rel_residual", C.c_double),
+                ("kernel_entries", C.c_double), ("t_build_s", C.c_double),
+                ("t_solve_s", C.c_double), ("kmv_ms", C.c_double),
+                ("kmv_launches", C.c_int), ("kmv64_launches", C.c_int),
+                ("kmv64_ms", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class KrrError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+# Every function the header declares, with its ctypes signature.
+_vp = C.c_void_p
+_i64, _u64, _int, _dbl = C.c_int64, C.c_uint64, C.c_int, C.c_double
+SIGNATURES = {
+    "krr_kmatvec": (_int, [_vp, _i64, _int, _int, _dbl, _dbl, _vp, _int, _vp, _int, _vp]),
+    "krr_rpc_sample": (_int, [_vp, _i64, _dbl, _u64, _u64, _int, _vp, C.POINTER(_int), _vp]),
+    "krr_rpcholesky": (_int, [_vp, _i64, _int, _int, _dbl, _int, _int, _u64, _vp,
+                              C.POINTER(_vp)]),
+    "krr_factor_info": (_int, [_vp, C.POINTER(_i64), C.POINTER(_int), C.POINTER(_int)]),
+    "krr_factor_export": (_int, [_vp, _vp, _vp, _vp]),
+    "krr_factor_free": (None, [_vp]),
+    "krr_precond_apply": (_int, [_vp, _dbl, _vp, _int, _vp, _int, _vp]),
+    "krr_pcg_solve": (_int, [_vp, _i64, _int, _int, _dbl, _vp, _int, _dbl, _vp, _dbl, _int,
+                             _int, _vp, _vp, C.POINTER(KrrInfo)]),
+    "krr_sparse_sign": (_int, [_i64, _int, _int, _u64, _vp, _vp, _vp]),
+    "krill_build": (_int, [_vp, _i64, _int, _int, _dbl, _vp, _int, _dbl, _int, _int, _u64, _vp,
+                           C.POINTER(_vp)]),
+    "krill_export": (_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(_int)]),
+    "krill_solve": (_int, [_vp, _vp, _int, _dbl, _int, _vp, _vp, C.POINTER(KrrInfo)]),
+    "krill_free": (None, [_vp]),
+    "krr_set_profiling": (None, [_int]),
+    "krr_last_error": (C.c_char_p, []),
+    "krr_version": (C.c_char_p, []),
+    "krr_launch_count": (C.c_uint64, []),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(auto_build: bool = True):
+    """Load libkrr_gb300.so (building it first when allowed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if auto_build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkrr_gb300.so not found at {path}; build it with "
+                           "paper_2304_12465_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def check(status: int, where: str, allow=()) -> int:
+    if status != KRR_OK and status not in allow:
+        msg = _LIB.krr_last_error().decode() if _LIB is not None else ""
+        raise KrrError(status, where, msg)
+    return status

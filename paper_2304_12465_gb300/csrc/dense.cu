@@ -1,0 +1,341 @@
+// Dense building blocks: strided SIMT GEMM (float32 / float64), blocked
+// float64 Cholesky and blocked lower-triangular inverse.  Used for the k x k
+// cores of Alg. 1 (lambda I + F^T F) and Alg. 2 (B^T B + H), the Schur update
+// of Alg. 3 and the triangular solves of both preconditioners.
+#include "dense.cuh"
+
+namespace krr {
+
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(G_THREADS)
+gemm_kernel(int M, int N, int K, const T *__restrict__ A, int64_t sai, int64_t sak,
+            const T *__restrict__ B, int64_t sbk, int64_t sbj, T *__restrict__ out,
+            int64_t ldo, int64_t slice_stride, int kslice, T alpha, T beta, int direct) {
+  __shared__ T As[GB_K][GB_M + 1];
+  __shared__ T Bs[GB_K][GB_N + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
+  const int kb = blockIdx.z * kslice;
+  const int ke = min(K, kb + kslice);
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+  const bool a_kfast = (sak == 1 && sai != 1);
+  const bool b_kfast = (sbk == 1 && sbj != 1);
+  for (int k0 = kb; k0 < ke; k0 += GB_K) {
+#pragma unroll
+    for (int e = 0; e < (GB_M * GB_K) / G_THREADS; ++e) {
+      const int idx = tid + e * G_THREADS;
+      int ii, kk;
+      if (a_kfast) { kk = idx % GB_K; ii = idx / GB_K; }
+      else { ii = idx % GB_M; kk = idx / GB_M; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      As[kk][ii] = (gi < M && gk < ke) ? A[(int64_t)gi * sai + (int64_t)gk * sak] : T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < (GB_N * GB_K) / G_THREADS; ++e) {
+      const int idx = tid + e * G_THREADS;
+      int jj, kk;
+      if (b_kfast) { kk = idx % GB_K; jj = idx / GB_K; }
+      else { jj = idx % GB_N; kk = idx / GB_N; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      Bs[kk][jj] = (gj < N && gk < ke) ? B[(int64_t)gk * sbk + (int64_t)gj * sbj] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  T *o = out + (int64_t)blockIdx.z * slice_stride;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+      if (gi < M && gj < N) {
+        T *dst = o + (int64_t)gi + (int64_t)gj * ldo;
+        if (direct) *dst = (beta == T(0)) ? alpha * acc[r][c] : fma(alpha, acc[r][c], beta * *dst);
+        else *dst = acc[r][c];
+      }
+    }
+}
+
+// C = beta C + alpha * sum_z P_z, P_z (M x N, ld M) in slices.
+template <typename T>
+__global__ void gemm_combine_kernel(int M, int N, const T *__restrict__ P, int slices,
+                                    T alpha, T beta, T *__restrict__ C, int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    T acc = 0;
+    for (int z = 0; z < slices; ++z) acc += P[(int64_t)z * total + e];
+    T *c = C + (int64_t)i + (int64_t)j * ldc;
+    *c = (beta == T(0)) ? alpha * acc : beta * (*c) + alpha * acc;
+  }
+}
+
+int gemm_auto_split(int M, int N, int K) {
+  const int64_t tiles = (int64_t)((M + GB_M - 1) / GB_M) * ((N + GB_N - 1) / GB_N);
+  const int64_t want = (int64_t)num_sms() * 4;
+  if (tiles >= want || K < 4 * GB_K) return 1;
+  int64_t sk = (want + tiles - 1) / tiles;
+  const int64_t maxk = K / (8 * GB_K);
+  if (sk > maxk) sk = maxk;
+  if (sk > 64) sk = 64;
+  return (int)(sk < 1 ? 1 : sk);
+}
+
+template <typename T>
+krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k) {
+  if (g.M <= 0 || g.N <= 0) return KRR_OK;
+  if (g.K <= 0) {
+    // C = beta C
+    DevBuf<T> z;
+    KRR_TRY(z.alloc((size_t)g.M * g.N, s));
+    KRR_CUDA_TRY(cudaMemsetAsync(z.p, 0, sizeof(T) * (size_t)g.M * g.N, s));
+    gemm_combine_kernel<T><<<ceil_div((int64_t)g.M * g.N, 256), 256, 0, s>>>(
+        g.M, g.N, z.p, 1, g.alpha, g.beta, g.C, g.ldc);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  }
+  if (split_k < 1) split_k = 1;
+  int kslice = (g.K + split_k - 1) / split_k;
+  kslice = (kslice + GB_K - 1) / GB_K * GB_K;
+  const int slices = (g.K + kslice - 1) / kslice;
+  dim3 grid((g.M + GB_M - 1) / GB_M, (g.N + GB_N - 1) / GB_N, slices);
+  if (slices == 1) {
+    gemm_kernel<T><<<grid, G_THREADS, 0, s>>>(g.M, g.N, g.K, g.A, g.sai, g.sak, g.B, g.sbk,
+                                             g.sbj, g.C, g.ldc, 0, kslice, g.alpha, g.beta, 1);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  }
+  DevBuf<T> P;
+  KRR_TRY(P.alloc((size_t)slices * g.M * g.N, s));
+  gemm_kernel<T><<<grid, G_THREADS, 0, s>>>(g.M, g.N, g.K, g.A, g.sai, g.sak, g.B, g.sbk,
+                                           g.sbj, P.p, g.M, (int64_t)g.M * g.N, kslice,
+                                           T(1), T(0), 0);
+  KRR_LAUNCH_CHECK();
+  int64_t total = (int64_t)g.M * g.N;
+  int blocks = ceil_div(total, 256);
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+  gemm_combine_kernel<T><<<blocks, 256, 0, s>>>(g.M, g.N, P.p, slices, g.alpha, g.beta,
+                                                g.C, g.ldc);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+template krr_status gemm<double>(const Gemm<double> &, cudaStream_t, int);
+template krr_status gemm<float>(const Gemm<float> &, cudaStream_t, int);
+
+// ------------------------------------------------------------ Cholesky
+constexpr int CH_NB = 64;
+
+// Factors the w x w diagonal block at A (lda) in place (lower) and writes the
+// inverse of its factor to Dinv (CH_NB x CH_NB, column-major, zero padded).
+// factor == 0: the block already holds a lower factor; only invert it.
+__global__ void __launch_bounds__(256)
+potrf_diag_kernel(double *__restrict__ A, int w, int64_t lda, double *__restrict__ Dinv,
+                  int *__restrict__ status, int factor) {
+  extern __shared__ double smem[];
+  double *sA = smem;                        // CH_NB x (CH_NB+1)
+  double *sW = smem + CH_NB * (CH_NB + 1);  // CH_NB x (CH_NB+1)
+  const int tid = threadIdx.x;
+  constexpr int LD = CH_NB + 1;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e % w, j = e / w;
+    sA[i * LD + j] = (i >= j) ? A[i + (int64_t)j * lda] : 0.0;
+  }
+  __syncthreads();
+  if (factor) {
+    for (int j = 0; j < w; ++j) {
+      if (tid == 0) {
+        const double p = sA[j * LD + j];
+        if (!(p > 0.0)) atomicExch(status, 1);
+        sA[j * LD + j] = sqrt(p);
+      }
+      __syncthreads();
+      const double dj = sA[j * LD + j];
+      for (int i = j + 1 + tid; i < w; i += blockDim.x) sA[i * LD + j] /= dj;
+      __syncthreads();
+      const int rem = w - j - 1;
+      for (int e = tid; e < rem * rem; e += blockDim.x) {
+        const int i = j + 1 + e % rem, l = j + 1 + e / rem;
+        if (l <= i) sA[i * LD + l] -= sA[i * LD + j] * sA[l * LD + j];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = e % w, j = e / w;
+      if (i >= j) A[i + (int64_t)j * lda] = sA[i * LD + j];
+    }
+  }
+  // inverse of the lower factor, one column per thread (forward substitution)
+  if (tid < CH_NB) {
+    const int c = tid;
+    for (int i = 0; i < CH_NB; ++i) {
+      double v = 0.0;
+      if (c < w && i < w && i >= c) {
+        v = (i == c) ? 1.0 : 0.0;
+        for (int l = c; l < i; ++l) v -= sA[i * LD + l] * sW[l * LD + c];
+        v /= sA[i * LD + i];
+      }
+      sW[i * LD + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < CH_NB * CH_NB; e += blockDim.x) {
+    const int i = e % CH_NB, j = e / CH_NB;
+    Dinv[i + j * CH_NB] = sW[i * LD + j];
+  }
+}
+
+static krr_status diag_block(double *A, int w, int64_t lda, double *Dinv, int *status,
+                             int factor, cudaStream_t s) {
+  const size_t smem = 2 * CH_NB * (CH_NB + 1) * sizeof(double);
+  KRR_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  potrf_diag_kernel<<<1, 256, smem, s>>>(A, w, lda, Dinv, status, factor);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+__global__ void copy_block_kernel(const double *__restrict__ src, int64_t lds, int rows,
+                                  int cols, double *__restrict__ dst, int64_t ldd) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % rows), j = (int)(e / rows);
+    dst[i + j * ldd] = src[i + j * lds];
+  }
+}
+
+krr_status potrf_lower(double *A, int n, int64_t lda, cudaStream_t s) {
+  if (n <= 0) return KRR_OK;
+  DevBuf<int> status;
+  KRR_TRY(status.alloc(1, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(int), s));
+  DevBuf<double> dinv, T;
+  KRR_TRY(dinv.alloc(CH_NB * CH_NB, s));
+  KRR_TRY(T.alloc((size_t)n * CH_NB, s));
+  for (int o = 0; o < n; o += CH_NB) {
+    const int w = (n - o < CH_NB) ? n - o : CH_NB;
+    double *Abb = A + o + (int64_t)o * lda;
+    KRR_TRY(diag_block(Abb, w, lda, dinv.p, status.p, 1, s));
+    const int r = n - o - w;
+    if (r <= 0) break;
+    double *A21 = Abb + w;
+    // T (r x w) = A21 Dinv^T
+    Gemm<double> g;
+    g.M = r; g.N = w; g.K = w;
+    g.A = A21; g.sai = 1; g.sak = lda;
+    g.B = dinv.p; g.sbk = CH_NB; g.sbj = 1;
+    g.alpha = 1.0; g.beta = 0.0; g.C = T.p; g.ldc = r;
+    KRR_TRY(gemm(g, s));
+    copy_block_kernel<<<ceil_div((int64_t)r * w, 256), 256, 0, s>>>(T.p, r, r, w, A21, lda);
+    KRR_LAUNCH_CHECK();
+    // A22 -= T T^T
+    Gemm<double> u;
+    u.M = r; u.N = r; u.K = w;
+    u.A = T.p; u.sai = 1; u.sak = r;
+    u.B = T.p; u.sbk = r; u.sbj = 1;
+    u.alpha = -1.0; u.beta = 1.0; u.C = A21 + (int64_t)w * lda; u.ldc = lda;
+    KRR_TRY(gemm(u, s, gemm_auto_split(r, r, w)));
+  }
+  int h = 0;
+  KRR_CUDA_TRY(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("Cholesky factorisation met a non-positive pivot (matrix not numerically "
+              "positive definite)");
+    return KRR_ECHOL;
+  }
+  return KRR_OK;
+}
+
+krr_status trinv_lower(const double *L, int n, int64_t lda, double *W, cudaStream_t s) {
+  if (n <= 0) return KRR_OK;
+  KRR_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * n, s));
+  DevBuf<int> status;
+  KRR_TRY(status.alloc(1, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(int), s));
+  const int nb = (n + CH_NB - 1) / CH_NB;
+  DevBuf<double> dinv, T;
+  KRR_TRY(dinv.alloc((size_t)nb * CH_NB * CH_NB, s));
+  KRR_TRY(T.alloc((size_t)CH_NB * n, s));
+  for (int b = 0; b < nb; ++b) {
+    const int o = b * CH_NB;
+    const int w = (n - o < CH_NB) ? n - o : CH_NB;
+    KRR_TRY(diag_block(const_cast<double *>(L) + o + (int64_t)o * lda, w, lda,
+                       dinv.p + (size_t)b * CH_NB * CH_NB, status.p, 0, s));
+    copy_block_kernel<<<ceil_div((int64_t)w * w, 256), 256, 0, s>>>(
+        dinv.p + (size_t)b * CH_NB * CH_NB, CH_NB, w, w, W + o + (int64_t)o * n, n);
+    KRR_LAUNCH_CHECK();
+  }
+  for (int b = 1; b < nb; ++b) {
+    const int o = b * CH_NB;
+    const int w = (n - o < CH_NB) ? n - o : CH_NB;
+    // T (w x o) = L(o:o+w, 0:o) W(0:o, 0:o)
+    Gemm<double> g;
+    g.M = w; g.N = o; g.K = o;
+    g.A = L + o; g.sai = 1; g.sak = lda;
+    g.B = W; g.sbk = 1; g.sbj = n;
+    g.alpha = 1.0; g.beta = 0.0; g.C = T.p; g.ldc = w;
+    KRR_TRY(gemm(g, s));
+    // W(o:o+w, 0:o) = -Dinv_b T
+    Gemm<double> h;
+    h.M = w; h.N = o; h.K = w;
+    h.A = dinv.p + (size_t)b * CH_NB * CH_NB; h.sai = 1; h.sak = CH_NB;
+    h.B = T.p; h.sbk = 1; h.sbj = w;
+    h.alpha = -1.0; h.beta = 0.0; h.C = W + o; h.ldc = n;
+    KRR_TRY(gemm(h, s));
+  }
+  return KRR_OK;
+}
+
+__global__ void add_diag_kernel(double *A, int n, int64_t lda, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + (int64_t)i * lda] += v;
+}
+
+krr_status add_diagonal(double *A, int n, int64_t lda, double v, cudaStream_t s) {
+  if (n <= 0) return KRR_OK;
+  add_diag_kernel<<<ceil_div(n, 256), 256, 0, s>>>(A, n, lda, v);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+__global__ void symmetrize_kernel(double *A, int n, int64_t lda) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (j > i) A[i + (int64_t)j * lda] = A[j + (int64_t)i * lda];
+  }
+}
+
+krr_status symmetrize_lower(double *A, int n, int64_t lda, cudaStream_t s) {
+  if (n <= 0) return KRR_OK;
+  int blocks = ceil_div((int64_t)n * n, 256);
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+  symmetrize_kernel<<<blocks, 256, 0, s>>>(A, n, lda);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+}  // namespace krr

@@ -1,0 +1,285 @@
+// Host drivers of the fused product (Alg. 1 "Product"), point preparation,
+// split reduction and kernel-column evaluation.
+#include "kmv.cuh"
+#include "kmv_dispatch.cuh"
+
+namespace krr {
+
+cudaError_t launch_kmv32_gauss(int DP, int M, dim3 g, cudaStream_t s, const Kmv32Args &a);
+cudaError_t launch_kmv32_laplace(int DP, int M, dim3 g, cudaStream_t s, const Kmv32Args &a);
+cudaError_t launch_kmv32_matern(int DP, int M, dim3 g, cudaStream_t s, const Kmv32Args &a);
+cudaError_t launch_kmv64_gauss(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
+cudaError_t launch_kmv64_laplace(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
+cudaError_t launch_kmv64_matern(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
+
+cudaError_t launch_kmv32_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
+                             const Kmv32Args &a) {
+  switch (kern) {
+    case KGAUSS: return launch_kmv32_gauss(DP, M, g, s, a);
+    case KLAPLACE: return launch_kmv32_laplace(DP, M, g, s, a);
+    case KMATERN: return launch_kmv32_matern(DP, M, g, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kmv64_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
+                             const Kmv64Args &a) {
+  switch (kern) {
+    case KGAUSS: return launch_kmv64_gauss(DP, M, g, s, a);
+    case KLAPLACE: return launch_kmv64_laplace(DP, M, g, s, a);
+    case KMATERN: return launch_kmv64_matern(DP, M, g, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------- preparation
+__global__ void column_mean_kernel(const double *__restrict__ X, int64_t N, int d,
+                                   double *__restrict__ mean) {
+  __shared__ double red[32];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += X[i * d + k];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) mean[k] = v / (double)N;
+  }
+}
+
+__global__ void prepare_f32_kernel(const double *__restrict__ X, int64_t N, int d, int dp,
+                                   const double *__restrict__ mean, double scale,
+                                   int with_norm, float *__restrict__ xt,
+                                   float *__restrict__ cn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double nrm = 0.0;
+  for (int k = 0; k < dp; ++k) {
+    float v = 0.0f;
+    if (k < d) v = (float)((X[i * d + k] - mean[k]) * scale);
+    xt[i * dp + k] = v;
+    nrm += (double)v * (double)v;
+  }
+  cn[i] = with_norm ? (float)(-0.5 * nrm) : 0.0f;
+}
+
+krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, double sigma,
+                              cudaStream_t s, PointsF32 &P) {
+  P.dp = (d + 3) / 4 * 4;
+  P.d = d;
+  P.N = N;
+  P.kern = kern;
+  P.sigma = sigma;
+  KRR_TRY(P.xt.alloc((size_t)N * P.dp, s));
+  KRR_TRY(P.cn.alloc((size_t)N, s));
+  DevBuf<double> mean;
+  KRR_TRY(mean.alloc(d, s));
+  column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, mean.p);
+  KRR_LAUNCH_CHECK();
+  const double log2e = 1.4426950408889634;
+  double scale;
+  int with_norm = 1;
+  if (kern == KGAUSS) {
+    scale = std::sqrt(log2e) / sigma;
+  } else if (kern == KMATERN) {
+    scale = std::sqrt(5.0) / sigma;
+  } else {
+    scale = log2e / sigma;
+    with_norm = 0;
+  }
+  prepare_f32_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, mean.p, scale,
+                                                      with_norm, P.xt.p, P.cn.p);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+// ---------------------------------------------------------- reduction
+template <typename T, int MAXM>
+__global__ void kmv_reduce_kernel(const T *__restrict__ part, int splits, int M,
+                                  int64_t N, int m, T lambda, const T *__restrict__ V,
+                                  int64_t ldv, T *__restrict__ Y, int64_t ldy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int c = 0; c < m; ++c) {
+    T acc = 0;
+    for (int sp = 0; sp < splits; ++sp) acc += part[((int64_t)sp * M + c) * N + i];
+    Y[(int64_t)c * ldy + i] = acc + lambda * V[(int64_t)c * ldv + i];
+  }
+}
+
+static int pad_m(int m) {
+  if (m <= 1) return 1;
+  if (m <= 2) return 2;
+  if (m <= 4) return 4;
+  if (m <= 8) return 8;
+  return 16;
+}
+
+// Column splits so the grid is about `waves` full waves of `per_sm` CTAs.
+static int choose_splits(int64_t row_tiles, int64_t N, int tj, int per_sm, int waves) {
+  const int64_t target = (int64_t)num_sms() * per_sm * waves;
+  int64_t splits = (target + row_tiles - 1) / row_tiles;
+  const int64_t max_splits = (N + tj - 1) / tj;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  return (int)splits;
+}
+
+krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv, int m,
+                   float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
+  const int64_t N = P.N;
+  if (N == 0 || m == 0) return KRR_OK;
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    const int rows = KMV_THREADS * kmv32_rows_per_thread(P.dp, M);
+    const int64_t row_tiles = (N + rows - 1) / rows;
+    const int splits = choose_splits(row_tiles, N, KMV_TJ, 2, 8);
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * N;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    Kmv32Args a{P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, part.p};
+    KmvTimer tm;
+    tm.begin(s);
+    cudaError_t e = launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    tm.end(s);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("fused product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<float, 16><<<ceil_div(N, 256), 256, 0, s>>>(
+        part.p, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
+        Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
+                   double lambda, const double *V, int64_t ldv, int m, double *Y,
+                   int64_t ldy, cudaStream_t s, DevBuf<double> &part) {
+  if (N == 0 || m == 0) return KRR_OK;
+  const int dp = (d + 3) / 4 * 4;
+  double inv_scale = (kern == KGAUSS) ? 1.0 / (2.0 * sigma * sigma) : 1.0 / sigma;
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    const int64_t row_tiles = (N + KMV64_THREADS - 1) / KMV64_THREADS;
+    const int splits = choose_splits(row_tiles, N, KMV64_TJ, 4, 4);
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV64_TJ - 1) / KMV64_TJ * KMV64_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * N;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    Kmv64Args a{Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, part.p};
+    KmvTimer tm(1);
+    tm.begin(s);
+    cudaError_t e = launch_kmv64_any(kern, dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    tm.end(s);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("float64 product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<double, 16><<<ceil_div(N, 256), 256, 0, s>>>(
+        part.p, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
+        Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+// ------------------------------------------------------- conversions
+__global__ void f64_to_f32_kernel(const double *__restrict__ a, float *__restrict__ b,
+                                  int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f32_to_f64_kernel(const float *__restrict__ a, double *__restrict__ b,
+                                  int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+krr_status convert_f64_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s) {
+  if (n == 0) return KRR_OK;
+  f64_to_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status convert_f32_to_f64(const float *src, double *dst, int64_t n, cudaStream_t s) {
+  if (n == 0) return KRR_OK;
+  f32_to_f64_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+// ---------------------------------------------------- kernel columns
+// One thread per (row, column) pair; the selected points are staged in
+// shared memory (nc <= 128 points of <= 32 coordinates).
+__global__ void kernel_columns_kernel(const double *__restrict__ X, int64_t N, int d,
+                                      int kern, double sigma,
+                                      const int64_t *__restrict__ cols, int nc,
+                                      double *__restrict__ G, int64_t ldg) {
+  extern __shared__ double sp[];
+  for (int idx = threadIdx.x; idx < nc * d; idx += blockDim.x)
+    sp[idx] = X[cols[idx / d] * d + idx % d];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double xi[32];
+  for (int k = 0; k < d; ++k) xi[k] = X[i * d + k];
+  for (int c = 0; c < nc; ++c)
+    G[(int64_t)c * ldg + i] = kappa_point_f64(xi, sp + c * d, d, kern, sigma);
+}
+
+krr_status kernel_columns_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
+                              const int64_t *cols, int nc, double *G, int64_t ldg,
+                              cudaStream_t s) {
+  if (nc == 0 || N == 0) return KRR_OK;
+  for (int c0 = 0; c0 < nc; c0 += 128) {
+    const int ncg = (nc - c0 < 128) ? nc - c0 : 128;
+    const size_t smem = (size_t)ncg * d * sizeof(double);
+    if (smem > 48 * 1024)
+      KRR_CUDA_TRY(cudaFuncSetAttribute(kernel_columns_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    kernel_columns_kernel<<<ceil_div(N, 128), 128, smem, s>>>(
+        Xd, N, d, kern, sigma, cols + c0, ncg, G + (int64_t)c0 * ldg, ldg);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+__global__ void kernel_diag_kernel(const double *__restrict__ X, int64_t N, int d,
+                                   int kern, double sigma, double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  out[i] = kappa_point_f64(X + i * d, X + i * d, d, kern, sigma);
+}
+
+krr_status kernel_diag_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
+                           double *out, cudaStream_t s) {
+  if (N == 0) return KRR_OK;
+  kernel_diag_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, kern, sigma, out);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+}  // namespace krr

@@ -1,0 +1,68 @@
+// Host-side interface of the fused product (kmatvec.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace krr {
+
+// Points prepared for the float32 product: centred, scaled, padded to DP
+// (a multiple of 4) coordinates, plus the per-point constant c_i.
+struct PointsF32 {
+  DevBuf<float> xt;   // N x dp
+  DevBuf<float> cn;   // N
+  int dp = 0;
+  int d = 0;
+  int64_t N = 0;
+  int kern = 0;
+  double sigma = 0.0;
+};
+
+krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
+                              double sigma, cudaStream_t s, PointsF32 &P);
+
+// Y (m x ldy, float32) = (A + lambda I) V (m x ldv, float32).
+krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv,
+                   int m, float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part);
+
+// Y (m x ldy, float64) = (A + lambda I) V (m x ldv, float64); Xd N x d float64.
+krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
+                   double lambda, const double *V, int64_t ldv, int m, double *Y,
+                   int64_t ldy, cudaStream_t s, DevBuf<double> &part);
+
+// Number of kernel entries one product evaluates (N^2).
+inline double kmv_entries(int64_t N) { return (double)N * (double)N; }
+
+// Element-wise conversions between float64 and float32 blocks.
+krr_status convert_f64_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
+krr_status convert_f32_to_f64(const float *src, double *dst, int64_t n, cudaStream_t s);
+
+// Kernel function value on device, float64, from direct coordinate
+// differences (the definitions of Sec. 2.1.2 / Sec. 5.1 / textbook Matern).
+__device__ __forceinline__ double kappa_point_f64(const double *a, const double *b,
+                                                  int d, int kern, double sigma) {
+  double s = 0.0;
+  if (kern == KLAPLACE) {
+    for (int k = 0; k < d; ++k) s += fabs(a[k] - b[k]);
+    return exp(-s / sigma);
+  }
+  for (int k = 0; k < d; ++k) {
+    const double t = a[k] - b[k];
+    s = fma(t, t, s);
+  }
+  if (kern == KMATERN) {
+    const double q = sqrt(5.0 * s) / sigma;
+    return (1.0 + q + q * q / 3.0) * exp(-q);
+  }
+  return exp(-s / (2.0 * sigma * sigma));
+}
+
+// G (nc x ldg column-major, rows 0..N-1) = A(:, cols), float64.
+krr_status kernel_columns_f64(const double *Xd, int64_t N, int d, int kern,
+                              double sigma, const int64_t *cols, int nc, double *G,
+                              int64_t ldg, cudaStream_t s);
+
+// out[i] = kappa(x_i, x_i) for all i (float64).
+krr_status kernel_diag_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
+                           double *out, cudaStream_t s);
+
+}  // namespace krr

@@ -1,0 +1,102 @@
+// Compile-time dispatch of the fused product kernels over the padded point
+// dimension DP (multiple of 4, <= 32) and the padded right-hand-side count M
+// (1, 2, 4, 8, 16).  Each kernel type is instantiated in its own translation
+// unit (kmv_gauss.cu, kmv_laplace.cu, kmv_matern.cu) to keep builds parallel.
+#pragma once
+
+#include "kmv_kernels.cuh"
+
+namespace krr {
+
+struct Kmv32Args {
+  const float *xt;
+  const float *cn;
+  const float *V;
+  int64_t ldv, N;
+  int m;
+  int64_t chunk;
+  float *part;
+};
+
+struct Kmv64Args {
+  const double *X;
+  int d;
+  const double *V;
+  int64_t ldv, N;
+  int m;
+  int64_t chunk;
+  double inv_scale;
+  double *part;
+};
+
+template <int KERN, int DP>
+cudaError_t launch_kmv32_m(int M, dim3 grid, cudaStream_t s, const Kmv32Args &a) {
+  switch (M) {
+#define KRR_CASE(MM)                                                              \
+  case MM:                                                                        \
+    kmv32_kernel<KERN, DP, MM><<<grid, KMV_THREADS, 0, s>>>(a.xt, a.cn, a.V, a.ldv, \
+                                                           a.N, a.m, a.chunk,      \
+                                                           a.part);                \
+    break;
+    KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
+#undef KRR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KERN>
+cudaError_t launch_kmv32(int DP, int M, dim3 grid, cudaStream_t s, const Kmv32Args &a) {
+  switch (DP) {
+    case 4: return launch_kmv32_m<KERN, 4>(M, grid, s, a);
+    case 8: return launch_kmv32_m<KERN, 8>(M, grid, s, a);
+    case 12: return launch_kmv32_m<KERN, 12>(M, grid, s, a);
+    case 16: return launch_kmv32_m<KERN, 16>(M, grid, s, a);
+    case 20: return launch_kmv32_m<KERN, 20>(M, grid, s, a);
+    case 24: return launch_kmv32_m<KERN, 24>(M, grid, s, a);
+    case 28: return launch_kmv32_m<KERN, 28>(M, grid, s, a);
+    case 32: return launch_kmv32_m<KERN, 32>(M, grid, s, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int KERN, int DP>
+cudaError_t launch_kmv64_m(int M, dim3 grid, cudaStream_t s, const Kmv64Args &a) {
+  switch (M) {
+#define KRR_CASE(MM)                                                                \
+  case MM:                                                                          \
+    kmv64_kernel<KERN, DP, MM><<<grid, KMV64_THREADS, 0, s>>>(a.X, a.d, a.V, a.ldv,   \
+                                                             a.N, a.m, a.chunk,      \
+                                                             a.inv_scale, a.part);   \
+    break;
+    KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
+#undef KRR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KERN>
+cudaError_t launch_kmv64(int DP, int M, dim3 grid, cudaStream_t s, const Kmv64Args &a) {
+  switch (DP) {
+    case 4: return launch_kmv64_m<KERN, 4>(M, grid, s, a);
+    case 8: return launch_kmv64_m<KERN, 8>(M, grid, s, a);
+    case 12: return launch_kmv64_m<KERN, 12>(M, grid, s, a);
+    case 16: return launch_kmv64_m<KERN, 16>(M, grid, s, a);
+    case 20: return launch_kmv64_m<KERN, 20>(M, grid, s, a);
+    case 24: return launch_kmv64_m<KERN, 24>(M, grid, s, a);
+    case 28: return launch_kmv64_m<KERN, 28>(M, grid, s, a);
+    case 32: return launch_kmv64_m<KERN, 32>(M, grid, s, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Per-kernel entry points, defined in kmv_{gauss,laplace,matern}.cu.
+cudaError_t launch_kmv32_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
+                             const Kmv32Args &a);
+cudaError_t launch_kmv64_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
+                             const Kmv64Args &a);
+
+}  // namespace krr

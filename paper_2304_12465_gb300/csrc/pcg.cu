@@ -1,0 +1,507 @@
+// Alg. 1 preconditioner (Woodbury form of the paper's SVD form) and PCG
+// (Sec. 3: zero initial iterate, stop on the recursive relative residual),
+// plus the mixed-precision iterative refinement around a float32 inner PCG.
+#include <chrono>
+
+#include "dense.cuh"
+#include "kmv.cuh"
+#include "pcg.cuh"
+#include "rpc.cuh"
+
+namespace krr {
+
+// ------------------------------------------------ tall skinny products
+constexpr int TT_ROWS = 512;   // rows per block of the transposed product
+constexpr int RED_BLOCKS = 512;
+
+// part[b][l][c] = sum_{n in block b} F[n + l N] R[c][n]
+template <typename TF, typename TR>
+__global__ void __launch_bounds__(256)
+tall_t_kernel(const TF *__restrict__ F, int64_t N, int rank, const TR *__restrict__ R,
+              int m, double *__restrict__ part) {
+  extern __shared__ double sR[];  // m x TT_ROWS
+  const int64_t n0 = (int64_t)blockIdx.x * TT_ROWS;
+  const int nr = (int)min((int64_t)TT_ROWS, N - n0);
+  for (int e = threadIdx.x; e < m * TT_ROWS; e += blockDim.x) {
+    const int c = e / TT_ROWS, n = e % TT_ROWS;
+    sR[e] = (n < nr) ? (double)R[(int64_t)c * N + n0 + n] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = warp; l < rank; l += blockDim.x >> 5) {
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    const TF *col = F + (int64_t)l * N + n0;
+    for (int n = lane; n < nr; n += 32) {
+      const double f = (double)col[n];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < m) acc[c] = fma(f, sR[c * TT_ROWS + n], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c < m) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) part[((int64_t)blockIdx.x * rank + l) * m + c] = v;
+      }
+    }
+  }
+}
+
+// t[c][l] = sum_b part[b][l][c]
+__global__ void tall_t_reduce_kernel(const double *__restrict__ part, int nb, int rank, int m,
+                                     double *__restrict__ t) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rank * m) return;
+  const int l = e / m, c = e % m;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += part[((int64_t)b * rank + l) * m + c];
+  t[(int64_t)c * rank + l] = acc;
+}
+
+// u[c][i] = sum_{l <= i} W[i + l rank] t[c][l]   (W lower triangular)
+__global__ void lower_gemv_kernel(const double *__restrict__ W, int rank,
+                                  const double *__restrict__ t, int m,
+                                  double *__restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rank) return;
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int l = 0; l <= i; ++l) {
+    const double w = W[i + (int64_t)l * rank];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < m) acc[c] = fma(w, t[(int64_t)c * rank + l], acc[c]);
+  }
+  for (int c = 0; c < m; ++c) u[(int64_t)c * rank + i] = acc[c];
+}
+
+// v[c][i] = sum_{l >= i} W[l + i rank] u[c][l]   (W^T, one warp per i)
+__global__ void lower_t_gemv_kernel(const double *__restrict__ W, int rank,
+                                    const double *__restrict__ u, int m,
+                                    double *__restrict__ v) {
+  const int warps = blockDim.x >> 5;
+  const int i = blockIdx.x * warps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= rank) return;
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  const double *col = W + (int64_t)i * rank;
+  for (int l = i + lane; l < rank; l += 32) {
+    const double w = col[l];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < m) acc[c] = fma(w, u[(int64_t)c * rank + l], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    if (c < m) {
+      const double s = warp_sum(acc[c]);
+      if (lane == 0) v[(int64_t)c * rank + i] = s;
+    }
+  }
+}
+
+// Z[c][n] = (R[c][n] - sum_l F[n + l N] v[c][l]) / lambda
+template <typename TF, typename TR>
+__global__ void __launch_bounds__(256)
+tall_n_kernel(const TF *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
+              int m, const TR *__restrict__ R, double inv_lambda, TR *__restrict__ Z) {
+  constexpr int LCH = 256;
+  __shared__ double sv[16 * LCH];
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int l0 = 0; l0 < rank; l0 += LCH) {
+    const int nl = min(LCH, rank - l0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * LCH; e += blockDim.x) {
+      const int c = e / LCH, l = e % LCH;
+      sv[c * LCH + l] = (l < nl) ? v[(int64_t)c * rank + l0 + l] : 0.0;
+    }
+    __syncthreads();
+    if (n < N) {
+      for (int l = 0; l < nl; ++l) {
+        const double f = (double)F[n + (int64_t)(l0 + l) * N];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < m) acc[c] = fma(f, sv[c * LCH + l], acc[c]);
+      }
+    }
+  }
+  if (n < N) {
+    for (int c = 0; c < m; ++c)
+      Z[(int64_t)c * N + n] = (TR)(((double)R[(int64_t)c * N + n] - acc[c]) * inv_lambda);
+  }
+}
+
+template <typename TF, typename TR>
+static krr_status nystrom_apply_impl(const TF *F, int64_t N, int rank, const double *W,
+                                     double lambda, const TR *R, int m, TR *Z,
+                                     cudaStream_t s) {
+  if (rank == 0) {
+    // P = lambda I
+    DevBuf<double> zero;
+    KRR_TRY(zero.alloc(m, s));
+    KRR_CUDA_TRY(cudaMemsetAsync(zero.p, 0, sizeof(double) * m, s));
+    tall_n_kernel<TF, TR><<<ceil_div(N, 256), 256, 0, s>>>(F, N, 0, zero.p, m, R,
+                                                           1.0 / lambda, Z);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  }
+  const int nb = ceil_div(N, TT_ROWS);
+  DevBuf<double> part, t, u, v;
+  KRR_TRY(part.alloc((size_t)nb * rank * m, s));
+  KRR_TRY(t.alloc((size_t)rank * m, s));
+  KRR_TRY(u.alloc((size_t)rank * m, s));
+  KRR_TRY(v.alloc((size_t)rank * m, s));
+  const size_t smem = (size_t)m * TT_ROWS * sizeof(double);
+  KRR_CUDA_TRY(cudaFuncSetAttribute(tall_t_kernel<TF, TR>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+  tall_t_kernel<TF, TR><<<nb, 256, smem, s>>>(F, N, rank, R, m, part.p);
+  KRR_LAUNCH_CHECK();
+  tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 256), 256, 0, s>>>(part.p, nb, rank, m,
+                                                                      t.p);
+  KRR_LAUNCH_CHECK();
+  lower_gemv_kernel<<<ceil_div(rank, 128), 128, 0, s>>>(W, rank, t.p, m, u.p);
+  KRR_LAUNCH_CHECK();
+  lower_t_gemv_kernel<<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u.p, m, v.p);
+  KRR_LAUNCH_CHECK();
+  tall_n_kernel<TF, TR><<<ceil_div(N, 256), 256, 0, s>>>(F, N, rank, v.p, m, R,
+                                                         1.0 / lambda, Z);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status nystrom_apply_f64(const krr_factor *f, const NystromCore *c, const double *R,
+                             int m, double *Z, cudaStream_t s) {
+  return nystrom_apply_impl<double, double>(f->F, f->N, c->rank, c->W, c->lambda, R, m, Z, s);
+}
+
+krr_status nystrom_apply_f32(const krr_factor *f, const NystromCore *c, const float *R,
+                             int m, float *Z, cudaStream_t s) {
+  return nystrom_apply_impl<float, float>(c->F32, f->N, c->rank, c->W, c->lambda, R, m, Z, s);
+}
+
+// ------------------------------------------------------- core build
+krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s,
+                        const NystromCore **out) {
+  std::lock_guard<std::mutex> lk(f->mtx);
+  for (const auto &c : f->cores)
+    if (c.mu == mu && c.prec == prec) {
+      *out = &c;
+      return KRR_OK;
+    }
+  auto t0 = std::chrono::steady_clock::now();
+  NystromCore c;
+  c.mu = mu;
+  c.prec = prec;
+  c.lambda = mu * (double)f->N;
+  c.rank = f->rank;
+  const int r = f->rank;
+  const int64_t N = f->N;
+  if (r > 0) {
+    const double *Fp = f->F;
+    DevBuf<double> Fround;
+    if (prec == KRR_PREC_MIXED) {
+      KRR_TRY(dev_alloc(&c.F32, (size_t)N * r));
+      KRR_TRY(convert_f64_to_f32(f->F, c.F32, N * r, s));
+      KRR_TRY(Fround.alloc((size_t)N * r, s));
+      KRR_TRY(convert_f32_to_f64(c.F32, Fround.p, N * r, s));
+      Fp = Fround.p;
+    }
+    DevBuf<double> Gm;
+    KRR_TRY(Gm.alloc((size_t)r * r, s));
+    Gemm<double> g;
+    g.M = r; g.N = r; g.K = (int)N;
+    g.A = Fp; g.sai = N; g.sak = 1;
+    g.B = Fp; g.sbk = 1; g.sbj = N;
+    g.alpha = 1.0; g.beta = 0.0; g.C = Gm.p; g.ldc = r;
+    KRR_TRY(gemm(g, s, gemm_auto_split(r, r, (int)N)));
+    KRR_TRY(add_diagonal(Gm.p, r, r, c.lambda, s));
+    krr_status st = potrf_lower(Gm.p, r, r, s);
+    if (st != KRR_OK) {
+      if (c.F32) cudaFree(c.F32);
+      return st;
+    }
+    KRR_TRY(dev_alloc(&c.W, (size_t)r * r));
+    KRR_TRY(trinv_lower(Gm.p, r, r, c.W, s));
+    KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  c.build_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  f->cores.push_back(c);
+  *out = &f->cores.back();
+  return KRR_OK;
+}
+
+// ---------------------------------------------------------- PCG kernels
+template <typename T>
+__global__ void dots_kernel(const T *__restrict__ a, const T *__restrict__ b, int64_t N,
+                            int m, double *__restrict__ part) {
+  __shared__ double red[32];
+  for (int c = 0; c < m; ++c) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+      s = fma((double)a[(int64_t)c * N + i], (double)b[(int64_t)c * N + i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      part[(int64_t)c * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ double sum_parts(const double *part, int nb, int c) {
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += part[(int64_t)c * nb + b];
+  return t;
+}
+
+// alpha_c = rz_c / (p_c . q_c) for active columns; breakdown flag otherwise.
+__global__ void pcg_alpha_kernel(const double *__restrict__ part, int nb, int m,
+                                 PcgScalars *__restrict__ sc) {
+  const int c = threadIdx.x;
+  if (c >= m) return;
+  const double pq = sum_parts(part, nb, c);
+  double a = 0.0;
+  if (sc->active[c]) {
+    if (!(pq > 0.0)) {
+      sc->breakdown = 1;
+      sc->active[c] = 0;
+    } else {
+      a = sc->rz[c] / pq;
+    }
+  }
+  sc->alpha[c] = a;
+}
+
+// Convergence test on the recursive residual.
+__global__ void pcg_resid_kernel(const double *__restrict__ part, int nb, int m, int it,
+                                 PcgScalars *__restrict__ sc) {
+  const int c = threadIdx.x;
+  if (c >= m) return;
+  const double rr = sum_parts(part, nb, c);
+  if (sc->active[c]) {
+    const double rel = sqrt(rr / sc->bb[c]);
+    sc->relres[c] = rel;
+    sc->iters[c] = it;
+    if (rel <= sc->tol[c]) sc->active[c] = 0;
+  }
+}
+
+__global__ void pcg_beta_kernel(const double *__restrict__ part, int nb, int m,
+                                PcgScalars *__restrict__ sc) {
+  const int c = threadIdx.x;
+  if (c >= m) return;
+  const double rz = sum_parts(part, nb, c);
+  double b = 0.0;
+  if (sc->active[c]) {
+    b = rz / sc->rz[c];
+    sc->rz[c] = rz;
+  }
+  sc->beta[c] = b;
+}
+
+__global__ void pcg_init_kernel(const double *__restrict__ part_bb,
+                                const double *__restrict__ part_rz, int nb, int m,
+                                const double *__restrict__ tol, PcgScalars *__restrict__ sc) {
+  const int c = threadIdx.x;
+  if (c >= m) return;
+  const double bb = sum_parts(part_bb, nb, c);
+  sc->bb[c] = bb;
+  sc->rz[c] = sum_parts(part_rz, nb, c);
+  sc->tol[c] = tol[c];
+  sc->iters[c] = 0;
+  sc->relres[c] = (bb > 0.0) ? 1.0 : 0.0;
+  sc->active[c] = (bb > 0.0) ? 1 : 0;
+  if (c == 0) sc->breakdown = 0;
+}
+
+// x += alpha p; r -= alpha q
+template <typename T>
+__global__ void pcg_update_kernel(T *__restrict__ x, T *__restrict__ r,
+                                  const T *__restrict__ p, const T *__restrict__ q, int64_t N,
+                                  int m, const PcgScalars *__restrict__ sc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    const double a = sc->alpha[c];
+    if (a != 0.0) {
+      x[e] = (T)((double)x[e] + a * (double)p[e]);
+      r[e] = (T)((double)r[e] - a * (double)q[e]);
+    }
+  }
+}
+
+// p = z + beta p (active columns)
+template <typename T>
+__global__ void pcg_dir_kernel(T *__restrict__ p, const T *__restrict__ z, int64_t N, int m,
+                               const PcgScalars *__restrict__ sc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    if (sc->active[c]) p[e] = (T)((double)z[e] + sc->beta[c] * (double)p[e]);
+  }
+}
+
+static unsigned vec_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------------ PCG driver
+template <typename T>
+krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
+                   const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats) {
+  DevBuf<T> r, z, p, q;
+  KRR_TRY(r.alloc((size_t)N * m, s));
+  KRR_TRY(z.alloc((size_t)N * m, s));
+  KRR_TRY(p.alloc((size_t)N * m, s));
+  KRR_TRY(q.alloc((size_t)N * m, s));
+  DevBuf<double> part1, part2, dtol;
+  KRR_TRY(part1.alloc((size_t)RED_BLOCKS * m, s));
+  KRR_TRY(part2.alloc((size_t)RED_BLOCKS * m, s));
+  KRR_TRY(dtol.alloc(m, s));
+  DevBuf<PcgScalars> sc;
+  KRR_TRY(sc.alloc(1, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(dtol.p, tol_host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)N * m, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(T) * (size_t)N * m, cudaMemcpyDeviceToDevice, s));
+  KRR_TRY(ops.precond(r.p, z.p, s));
+  dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, r.p, N, m, part1.p);
+  KRR_LAUNCH_CHECK();
+  dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, z.p, N, m, part2.p);
+  KRR_LAUNCH_CHECK();
+  pcg_init_kernel<<<1, 32, 0, s>>>(part1.p, part2.p, RED_BLOCKS, m, dtol.p, sc.p);
+  KRR_LAUNCH_CHECK();
+  KRR_CUDA_TRY(cudaMemcpyAsync(p.p, z.p, sizeof(T) * (size_t)N * m, cudaMemcpyDeviceToDevice, s));
+  PcgScalars h;
+  KRR_CUDA_TRY(cudaMemcpyAsync(&h, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  int it = 0;
+  bool any = false;
+  for (int c = 0; c < m; ++c) any = any || h.active[c];
+  while (any && it < maxit) {
+    KRR_TRY(ops.product(p.p, q.p, s));
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(p.p, q.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_alpha_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    pcg_update_kernel<T><<<vec_grid(N * m), 256, 0, s>>>(x, r.p, p.p, q.p, N, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    ++it;
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, r.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_resid_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, it, sc.p);
+    KRR_LAUNCH_CHECK();
+    KRR_CUDA_TRY(cudaMemcpyAsync(&h, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    KRR_CUDA_TRY(cudaStreamSynchronize(s));
+    any = false;
+    for (int c = 0; c < m; ++c) any = any || h.active[c];
+    if (!any || it >= maxit) break;
+    KRR_TRY(ops.precond(r.p, z.p, s));
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, z.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_beta_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    pcg_dir_kernel<T><<<vec_grid(N * m), 256, 0, s>>>(p.p, z.p, N, m, sc.p);
+    KRR_LAUNCH_CHECK();
+  }
+  if (stats) {
+    stats->products += it;
+    int mx = 0;
+    double worst = 0.0;
+    bool conv = true;
+    for (int c = 0; c < m; ++c) {
+      mx = (h.iters[c] > mx) ? h.iters[c] : mx;
+      worst = (h.relres[c] > worst) ? h.relres[c] : worst;
+      if (h.relres[c] > tol_host[c]) conv = false;
+    }
+    stats->iters_max = mx;
+    stats->relres_max = worst;
+    stats->converged = conv;
+    stats->breakdown = h.breakdown != 0;
+    for (int c = 0; c < m; ++c) {
+      stats->col_iters[c] = h.iters[c];
+      stats->col_relres[c] = h.relres[c];
+    }
+  }
+  return KRR_OK;
+}
+
+template krr_status pcg_run<double>(const PcgOps<double> &, int64_t, int, const double *,
+                                    double *, const double *, int, cudaStream_t, PcgStats *);
+template krr_status pcg_run<float>(const PcgOps<float> &, int64_t, int, const float *,
+                                   float *, const double *, int, cudaStream_t, PcgStats *);
+
+// ----------------------------------------------------- vector helpers
+__global__ void residual_kernel(const double *__restrict__ y, const double *__restrict__ mx,
+                                double *__restrict__ r, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    r[e] = y[e] - mx[e];
+}
+
+__global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__ d, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += (double)d[e];
+}
+
+krr_status tri_apply_lower(const double *W, int rank, const double *t, int m, double *u,
+                           cudaStream_t s) {
+  lower_gemv_kernel<<<ceil_div(rank, 128), 128, 0, s>>>(W, rank, t, m, u);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
+                             cudaStream_t s) {
+  lower_t_gemv_kernel<<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u, m, v);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status residual_f64(const double *y, const double *mx, double *r, int64_t n,
+                        cudaStream_t s) {
+  residual_kernel<<<vec_grid(n), 256, 0, s>>>(y, mx, r, n);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status add_f32_to_f64(double *x, const float *d, int64_t n, cudaStream_t s) {
+  add_f32_kernel<<<vec_grid(n), 256, 0, s>>>(x, d, n);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+krr_status column_norms(const double *a, int64_t N, int m, double *out_host, cudaStream_t s) {
+  DevBuf<double> part;
+  KRR_TRY(part.alloc((size_t)RED_BLOCKS * m, s));
+  dots_kernel<double><<<RED_BLOCKS, 256, 0, s>>>(a, a, N, m, part.p);
+  KRR_LAUNCH_CHECK();
+  std::vector<double> h((size_t)RED_BLOCKS * m);
+  KRR_CUDA_TRY(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * h.size(),
+                               cudaMemcpyDeviceToHost, s));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int c = 0; c < m; ++c) {
+    double t = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) t += h[(size_t)c * RED_BLOCKS + b];
+    out_host[c] = std::sqrt(t);
+  }
+  return KRR_OK;
+}
+
+}  // namespace krr

@@ -1,0 +1,60 @@
+// PCG driver interface (pcg.cu).
+#pragma once
+
+#include <functional>
+#include <vector>
+
+#include "common.cuh"
+
+namespace krr {
+
+constexpr int PCG_MAX_M = 16;
+
+// Device-resident per-column CG scalars (float64).
+struct PcgScalars {
+  double rz[PCG_MAX_M];
+  double bb[PCG_MAX_M];
+  double alpha[PCG_MAX_M];
+  double beta[PCG_MAX_M];
+  double relres[PCG_MAX_M];
+  double tol[PCG_MAX_M];
+  int active[PCG_MAX_M];
+  int iters[PCG_MAX_M];
+  int breakdown;
+};
+
+// Operator and preconditioner of one PCG run, on m x N column-major blocks.
+template <typename T>
+struct PcgOps {
+  std::function<krr_status(const T *in, T *out, cudaStream_t)> product;
+  std::function<krr_status(const T *in, T *out, cudaStream_t)> precond;
+};
+
+struct PcgStats {
+  int products = 0;       // operator applications
+  int iters_max = 0;
+  double relres_max = 0;  // recursive residual at exit
+  bool converged = false;
+  bool breakdown = false;
+  int col_iters[PCG_MAX_M] = {0};
+  double col_relres[PCG_MAX_M] = {0};
+};
+
+// Standard PCG with zero initial iterate; column c stops when its recursive
+// relative residual is <= tol_host[c] (each column has its own scalars).
+template <typename T>
+krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
+                   const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats);
+
+// u (m x rank) = W t and v = W^T u for a lower-triangular W (rank x rank).
+krr_status tri_apply_lower(const double *W, int rank, const double *t, int m, double *u,
+                           cudaStream_t s);
+krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
+                             cudaStream_t s);
+
+krr_status residual_f64(const double *y, const double *mx, double *r, int64_t n,
+                        cudaStream_t s);
+krr_status add_f32_to_f64(double *x, const float *d, int64_t n, cudaStream_t s);
+krr_status column_norms(const double *a, int64_t N, int m, double *out_host, cudaStream_t s);
+
+}  // namespace krr

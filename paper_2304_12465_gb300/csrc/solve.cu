@@ -1,0 +1,269 @@
+// Solve drivers: RPCholesky-preconditioned CG (Alg. 1) in float64 or with
+// mixed-precision iterative refinement, and KRILL PCG (Alg. 2).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "dense.cuh"
+#include "kmv.cuh"
+#include "krill.cuh"
+#include "pcg.cuh"
+#include "rpc.cuh"
+#include "solve.cuh"
+
+namespace krr {
+
+template <typename T>
+__global__ void scale_kernel(const T *__restrict__ in, T *__restrict__ out, int64_t n, double a) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)((double)in[e] * a);
+}
+
+template <typename T>
+static krr_status scale(const T *in, T *out, int64_t n, double a, cudaStream_t s) {
+  int64_t g = (n + 255) / 256;
+  if (g > num_sms() * 8) g = num_sms() * 8;
+  scale_kernel<T><<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(in, out, n, a);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double sigma,
+                            const double *Y, int m, double mu, const krr_factor *F,
+                            double tol, int maxit, int prec, double *alpha, cudaStream_t s,
+                            krr_info *info) {
+  const double lambda = mu * (double)N;
+  auto t0 = std::chrono::steady_clock::now();
+  const NystromCore *core = nullptr;
+  if (F && F->rank > 0) KRR_TRY(nystrom_core(F, mu, prec, s, &core));
+  const double t_build = core ? core->build_s : 0.0;
+  auto t1 = std::chrono::steady_clock::now();
+  (void)t0;
+  std::vector<double> tolv(m, tol);
+  double entries = 0.0;
+  int outer = 0, iters_total = 0;
+  double relres = 0.0;
+  krr_status final_status = KRR_OK;
+
+  if (prec == KRR_PREC_FP64) {
+    DevBuf<double> part;
+    PcgOps<double> ops;
+    ops.product = [&](const double *in, double *out, cudaStream_t st) {
+      return kmv_f64(Xd, N, d, kern, sigma, lambda, in, N, m, out, N, st, part);
+    };
+    ops.precond = [&](const double *in, double *out, cudaStream_t st) {
+      if (core) return nystrom_apply_f64(F, core, in, m, out, st);
+      return scale<double>(in, out, N * m, 1.0 / lambda, st);
+    };
+    PcgStats stats;
+    KRR_TRY(pcg_run<double>(ops, N, m, Y, alpha, tolv.data(), maxit, s, &stats));
+    iters_total = stats.iters_max;
+    entries += kmv_entries(N) * stats.products;
+    if (stats.breakdown) final_status = KRR_EBREAKDOWN;
+    else if (!stats.converged) final_status = KRR_ENOCONV;
+    relres = stats.relres_max;
+    if (info) {
+      DevBuf<double> mx, r;
+      KRR_TRY(mx.alloc((size_t)N * m, s));
+      KRR_TRY(r.alloc((size_t)N * m, s));
+      KRR_TRY(kmv_f64(Xd, N, d, kern, sigma, lambda, alpha, N, m, mx.p, N, s, part));
+      entries += kmv_entries(N);
+      KRR_TRY(residual_f64(Y, mx.p, r.p, N * m, s));
+      std::vector<double> rn(m), yn(m);
+      KRR_TRY(column_norms(r.p, N, m, rn.data(), s));
+      KRR_TRY(column_norms(Y, N, m, yn.data(), s));
+      relres = 0.0;
+      for (int c = 0; c < m; ++c) relres = std::max(relres, yn[c] > 0 ? rn[c] / yn[c] : rn[c]);
+    }
+  } else {
+    // iterative refinement: float64 outer loop around a float32 inner PCG
+    PointsF32 P;
+    KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
+    DevBuf<float> part32, b32, d32;
+    DevBuf<double> part64, mx, r64;
+    KRR_TRY(b32.alloc((size_t)N * m, s));
+    KRR_TRY(d32.alloc((size_t)N * m, s));
+    KRR_TRY(mx.alloc((size_t)N * m, s));
+    KRR_TRY(r64.alloc((size_t)N * m, s));
+    KRR_CUDA_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * N * m, s));
+    KRR_CUDA_TRY(cudaMemcpyAsync(r64.p, Y, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, s));
+    PcgOps<float> ops;
+    const float lam32 = (float)lambda;
+    ops.product = [&](const float *in, float *out, cudaStream_t st) {
+      return kmv_f32(P, lam32, in, N, m, out, N, st, part32);
+    };
+    ops.precond = [&](const float *in, float *out, cudaStream_t st) {
+      if (core) return nystrom_apply_f32(F, core, in, m, out, st);
+      return scale<float>(in, out, N * m, 1.0 / lambda, st);
+    };
+    std::vector<double> yn(m), rn(m);
+    KRR_TRY(column_norms(Y, N, m, yn.data(), s));
+    rn = yn;
+    const int max_outer = 12;
+    double prev_worst = 1e300;
+    final_status = KRR_ENOCONV;
+    int budget = maxit;
+    while (true) {
+      double worst = 0.0;
+      for (int c = 0; c < m; ++c) worst = std::max(worst, yn[c] > 0 ? rn[c] / yn[c] : 0.0);
+      relres = worst;
+      if (worst <= tol) { final_status = KRR_OK; break; }
+      if (outer >= max_outer || budget <= 0) break;
+      if (outer > 0 && worst > 0.5 * prev_worst) break;  // refinement stagnated
+      prev_worst = worst;
+      // inner tolerances: aim a little below what the outer test needs, but
+      // not below what float32 arithmetic can certify
+      std::vector<double> inner_tol(m);
+      for (int c = 0; c < m; ++c) {
+        const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
+        inner_tol[c] = (rel > tol) ? std::max(0.3 * tol / rel, 2e-6) : 1.0;
+      }
+      // columns already converged get a zero right-hand side (no work)
+      KRR_TRY(convert_f64_to_f32(r64.p, b32.p, N * m, s));
+      for (int c = 0; c < m; ++c) {
+        const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
+        if (!(rel > tol)) KRR_CUDA_TRY(cudaMemsetAsync(b32.p + (int64_t)c * N, 0, sizeof(float) * N, s));
+      }
+      PcgStats st;
+      KRR_TRY(pcg_run<float>(ops, N, m, b32.p, d32.p, inner_tol.data(), budget, s, &st));
+      iters_total += st.iters_max;
+      budget -= st.iters_max;
+      entries += kmv_entries(N) * st.products;
+      KRR_TRY(add_f32_to_f64(alpha, d32.p, N * m, s));
+      KRR_TRY(kmv_f64(Xd, N, d, kern, sigma, lambda, alpha, N, m, mx.p, N, s, part64));
+      entries += kmv_entries(N);
+      KRR_TRY(residual_f64(Y, mx.p, r64.p, N * m, s));
+      KRR_TRY(column_norms(r64.p, N, m, rn.data(), s));
+      ++outer;
+      if (st.breakdown) { final_status = KRR_EBREAKDOWN; break; }
+    }
+    if (final_status != KRR_OK && final_status != KRR_EBREAKDOWN) {
+      double worst = 0.0;
+      for (int c = 0; c < m; ++c) worst = std::max(worst, yn[c] > 0 ? rn[c] / yn[c] : 0.0);
+      relres = worst;
+      if (worst <= tol) final_status = KRR_OK;
+    }
+  }
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters_total;
+    info->outer_refinements = outer;
+    info->rank = F ? F->rank : 0;
+    info->rel_residual = relres;
+    info->kernel_entries = entries;
+    info->t_build_s = t_build;
+    info->t_solve_s = seconds_since(t1);
+  }
+  if (final_status == KRR_ENOCONV)
+    set_error("PCG did not reach the tolerance (relative residual %.3e > %.3e)", relres, tol);
+  if (final_status == KRR_EBREAKDOWN) set_error("PCG breakdown: p^T M p <= 0 or NaN");
+  return final_status;
+}
+
+// --------------------------------------------------------------- KRILL
+__global__ void axpy_sub_kernel(const double *__restrict__ b, const double *__restrict__ mx,
+                                double *__restrict__ r, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    r[e] = b[e] - mx[e];
+}
+
+__global__ void add_f64_kernel(double *__restrict__ x, const double *__restrict__ d, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += d[e];
+}
+
+krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, double tol,
+                              int maxit, double *beta, cudaStream_t s, krr_info *info) {
+  auto t1 = std::chrono::steady_clock::now();
+  const int k = P->k;
+  DevBuf<double> b, tmp, r, dx, mx, u64, v64;
+  KRR_TRY(b.alloc((size_t)k * m, s));
+  KRR_TRY(tmp.alloc((size_t)k * m, s));
+  KRR_TRY(r.alloc((size_t)k * m, s));
+  KRR_TRY(dx.alloc((size_t)k * m, s));
+  KRR_TRY(mx.alloc((size_t)k * m, s));
+  KRR_TRY(krill_rhs(P, Y, m, b.p, s));
+  double entries = (double)P->N * k;
+  DevBuf<float> u;
+  DevBuf<double> v;
+  PcgOps<double> ops;
+  ops.product = [&](const double *in, double *out, cudaStream_t st) {
+    return krill_product(P, in, m, out, st, u, v);
+  };
+  ops.precond = [&](const double *in, double *out, cudaStream_t st) {
+    return krill_precond_apply(P, in, m, tmp.p, out, st);
+  };
+  KRR_CUDA_TRY(cudaMemsetAsync(beta, 0, sizeof(double) * k * m, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(r.p, b.p, sizeof(double) * k * m, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> bn(m), rn(m);
+  KRR_TRY(column_norms(b.p, k, m, bn.data(), s));
+  rn = bn;
+  int outer = 0, iters_total = 0, budget = maxit;
+  double relres = 1.0, prev = 1e300;
+  krr_status final_status = KRR_ENOCONV;
+  bool breakdown = false;
+  while (true) {
+    double worst = 0.0;
+    for (int c = 0; c < m; ++c) worst = std::max(worst, bn[c] > 0 ? rn[c] / bn[c] : 0.0);
+    relres = worst;
+    if (worst <= tol) { final_status = KRR_OK; break; }
+    if (outer >= 12 || budget <= 0) break;
+    if (outer > 0 && worst > 0.5 * prev) break;
+    prev = worst;
+    std::vector<double> itol(m);
+    for (int c = 0; c < m; ++c) {
+      const double rel = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+      itol[c] = (rel > tol) ? std::max(0.3 * tol / rel, 1e-5) : 1.0;
+      if (!(rel > tol)) KRR_CUDA_TRY(cudaMemsetAsync(r.p + (int64_t)c * k, 0, sizeof(double) * k, s));
+    }
+    PcgStats st;
+    KRR_TRY(pcg_run<double>(ops, k, m, r.p, dx.p, itol.data(), budget, s, &st));
+    iters_total += st.iters_max;
+    budget -= st.iters_max;
+    entries += 2.0 * (double)P->N * k * st.products;
+    add_f64_kernel<<<ceil_div((int64_t)k * m, 256), 256, 0, s>>>(beta, dx.p, (int64_t)k * m);
+    KRR_LAUNCH_CHECK();
+    KRR_TRY(krill_product64(P, beta, m, mx.p, s, u64, v64));
+    entries += 2.0 * (double)P->N * k;
+    axpy_sub_kernel<<<ceil_div((int64_t)k * m, 256), 256, 0, s>>>(b.p, mx.p, r.p, (int64_t)k * m);
+    KRR_LAUNCH_CHECK();
+    KRR_TRY(column_norms(r.p, k, m, rn.data(), s));
+    ++outer;
+    if (st.breakdown) { breakdown = true; break; }
+  }
+  if (final_status != KRR_OK) {
+    double worst = 0.0;
+    for (int c = 0; c < m; ++c) worst = std::max(worst, bn[c] > 0 ? rn[c] / bn[c] : 0.0);
+    relres = worst;
+    if (worst <= tol) final_status = KRR_OK;
+  }
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters_total;
+    info->outer_refinements = outer;
+    info->rank = k;
+    info->rel_residual = relres;
+    info->kernel_entries = entries;
+    info->t_build_s = P->build_s;
+    info->t_solve_s = seconds_since(t1);
+  }
+  if (breakdown && final_status != KRR_OK) {
+    set_error("KRILL PCG breakdown");
+    return KRR_EBREAKDOWN;
+  }
+  if (final_status != KRR_OK) {
+    set_error("KRILL PCG did not reach the tolerance (%.3e > %.3e)", relres, tol);
+    return KRR_ENOCONV;
+  }
+  return KRR_OK;
+}
+
+}  // namespace krr

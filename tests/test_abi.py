@@ -1,0 +1,90 @@
+"""CPU checks of the C ABI boundary: the library builds and loads, exports every
+function include/krr.h declares, the Python binding covers them, and argument
+validation answers KRR_EINVAL before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "krr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return re.findall(r"KRR_API\s+(?:krr_status|void|const char \*|uint64_t)\s*(\w+)\s*\(", text)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2304_12465_gb300 as K
+    return K.load()
+
+
+def test_header_declares_the_calls():
+    names = declared_functions()
+    for must in ("krr_rpcholesky", "krr_pcg_solve", "krill_build", "krill_solve",
+                 "krr_kmatvec", "krr_rpc_sample", "krr_sparse_sign", "krr_precond_apply"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_symbol():
+    import paper_2304_12465_gb300 as K
+    assert set(declared_functions()) == set(K.SIGNATURES)
+
+
+def test_only_abi_symbols_are_exported():
+    import subprocess
+    import paper_2304_12465_gb300 as K
+    K.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", K.library_path()], capture_output=True,
+                         text=True).stdout
+    text_syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(declared_functions()) <= text_syms
+    assert not [s for s in text_syms if s.startswith("_ZN3krr")]
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.krr_version()
+
+
+def _einval(status, lib, fragment):
+    assert status == 1
+    assert fragment in lib.krr_last_error().decode()
+
+
+def test_argument_validation_before_any_launch(lib):
+    X = np.zeros((4, 2))
+    V = np.zeros((1, 4))
+    Y = np.zeros((1, 4))
+    p = lambda a: C.c_void_p(a.ctypes.data)
+    _einval(lib.krr_kmatvec(p(X), 0, 2, 0, 1.0, 0.1, p(V), 1, p(Y), 0, None), lib, "N must")
+    _einval(lib.krr_kmatvec(p(X), 4, 0, 0, 1.0, 0.1, p(V), 1, p(Y), 0, None), lib, "d must")
+    _einval(lib.krr_kmatvec(p(X), 4, 33, 0, 1.0, 0.1, p(V), 1, p(Y), 0, None), lib, "d must")
+    _einval(lib.krr_kmatvec(p(X), 4, 2, 7, 1.0, 0.1, p(V), 1, p(Y), 0, None), lib, "kernel")
+    _einval(lib.krr_kmatvec(p(X), 4, 2, 0, -1.0, 0.1, p(V), 1, p(Y), 0, None), lib, "sigma")
+    _einval(lib.krr_kmatvec(p(X), 4, 2, 0, float("nan"), 0.1, p(V), 1, p(Y), 0, None), lib,
+            "sigma")
+    _einval(lib.krr_kmatvec(p(X), 4, 2, 0, 1.0, 0.1, p(V), 17, p(Y), 0, None), lib, "m must")
+    _einval(lib.krr_kmatvec(p(X), 4, 2, 0, 1.0, 0.1, p(V), 1, p(Y), 9, None), lib, "precision")
+    h = C.c_void_p()
+    _einval(lib.krr_rpcholesky(p(X), 4, 2, 0, 1.0, 5, 0, 0, None, C.byref(h)), lib, "k must")
+    _einval(lib.krr_rpcholesky(p(X), 4, 2, 0, 1.0, 2, 129, 0, None, C.byref(h)), lib, "block")
+    assert not h.value
+    info = None
+    _einval(lib.krr_pcg_solve(p(X), 4, 2, 0, 1.0, p(Y), 1, 0.0, None, 1e-6, 0, 0, p(Y), None,
+                              info), lib, "mu")
+    _einval(lib.krr_pcg_solve(p(X), 4, 2, 0, 1.0, p(Y), 1, 1e-3, None, 1.5, 0, 0, p(Y), None,
+                              info), lib, "tol")
+    rows = np.zeros((4, 2), dtype=np.int32)
+    _einval(lib.krr_sparse_sign(4, 3, 4, 0, p(rows), p(V), None), lib, "zeta")
+    _einval(lib.krr_sparse_sign(4, 8, 65, 0, p(rows), p(V), None), lib, "zeta")
+    _einval(lib.krr_rpc_sample(p(V), 4, 0.0, 0, 0, 0, p(rows), C.byref(C.c_int()), None), lib,
+            "ndraw")

@@ -1,0 +1,82 @@
+"""GPU parity of the fused product (A + lambda I) V against the oracle.
+
+float64 path: direct differences and float64 exp, compared entrywise with
+rtol 1e-12.  float32 path: errors are bounded by the float32 unit roundoff
+times the condition of the sum; each entry must satisfy
+|Y32 - Y| <= 2e-5 (A|V| + lambda|V|) -- the kernel value carries ~1e-6
+relative error from the argument and ex2, the accumulation a few 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from inputs import make_c1_plain_fp64, make_c2_mixed
+from gpu_common import f32_product_bound, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+KERNS = [O.GAUSSIAN, O.LAPLACE_L1, O.MATERN52]
+
+
+@pytest.fixture(scope="module")
+def K():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,d,m", [(1, 1, 1), (65, 3, 1), (700, 8, 4), (1500, 16, 3),
+                                   (1029, 20, 16), (513, 32, 2), (300, 5, 9)])
+def test_fp64_product(K, kern, N, d, m):
+    rng = np.random.default_rng(N * 7 + d + kern)
+    X = rng.standard_normal((N, d))
+    V = rng.standard_normal((m, N))
+    ref = O.kmatvec(X, kern, 1.3, 0.25, V)
+    got = K.krr_kmatvec(X, kern, 1.3, 0.25, V, prec="fp64")
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,d,m", [(1, 1, 1), (65, 3, 1), (700, 8, 4), (3000, 16, 4),
+                                   (1029, 20, 16), (513, 32, 2), (2000, 12, 8)])
+def test_fp32_product(K, kern, N, d, m):
+    rng = np.random.default_rng(N * 11 + d + kern)
+    X = rng.standard_normal((N, d))
+    V = rng.standard_normal((m, N))
+    ref = O.kmatvec(X, kern, 1.1, 0.5, V)
+    bound = f32_product_bound(X, kern, 1.1, 0.5, V)
+    got = K.krr_kmatvec(X, kern, 1.1, 0.5, V, prec="mixed")
+    assert np.all(np.abs(got - ref) <= 2e-5 * bound)
+
+
+def test_device_and_host_pointers_agree(K):
+    w = make_c1_plain_fp64(n=777)
+    V = np.random.default_rng(0).standard_normal((2, w.N))
+    host = K.krr_kmatvec(w.X, w.kernel, w.sigma, w.lam, V, prec="fp64")
+    dev = K.krr_kmatvec(to_dev(w.X), w.kernel, w.sigma, w.lam, to_dev(V), prec="fp64")
+    np.testing.assert_array_equal(host, dev.cpu().numpy())
+
+
+def test_deterministic(K):
+    w = make_c1_plain_fp64(n=4096)
+    V = np.random.default_rng(1).standard_normal((1, w.N))
+    a = K.krr_kmatvec(w.X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+    b = K.krr_kmatvec(w.X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_sampled_rows(K, prec):
+    """The 100000-point, d = 16 ill-conditioned workload with 4 right-hand
+    sides: GPU product on all rows, oracle on 48 sampled rows."""
+    w = make_c2_mixed()
+    rng = np.random.default_rng(2)
+    V = rng.standard_normal((w.m, w.N))
+    rows = np.sort(rng.choice(w.N, 48, replace=False))
+    got = K.krr_kmatvec(to_dev(w.X), w.kernel, w.sigma, w.lam, to_dev(V), prec=prec)
+    got = got.cpu().numpy()[:, rows]
+    ref = O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows)
+    if prec == "fp64":
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    else:
+        bound = f32_product_bound(w.X, w.kernel, w.sigma, w.lam, V, rows)
+        assert np.all(np.abs(got - ref) <= 2e-5 * bound)

@@ -1,0 +1,113 @@
+"""GPU parity of the Alg. 1 preconditioner and PCG, float64 and mixed paths.
+
+float64 path: the same pivots give the same preconditioner, so the GPU and
+oracle iterates track each other; alpha must match the oracle's to relative
+error 1e-10 at tol 1e-10.  Mixed path: alpha must match the float64 oracle
+to relative error 1e-6 when solved to a residual where alpha is pinned
+(cond(A + lambda I) x tol << 1e-6), and at the working tolerance the float64
+residual, recomputed by the oracle, must be <= tol.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from inputs import make_c1_plain_fp64, make_c2_mixed
+from gpu_common import rel_err, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def c1(K):
+    w = make_c1_plain_fp64()
+    ref_f = O.rpcholesky(w.X, w.kernel, w.sigma, w.k, w.block, 0)
+    f = K.krr_rpcholesky(w.X, w.kernel, w.sigma, w.k, w.block, 0)
+    return w, ref_f, f
+
+
+def test_precond_apply(K, c1):
+    w, ref_f, f = c1
+    R = np.random.default_rng(0).standard_normal((3, w.N))
+    pre = O.nystrom_preconditioner(ref_f.F, w.lam)
+    ref = np.stack([pre.apply(r) for r in R])
+    got = K.krr_precond_apply(f, w.mu, R, prec="fp64")
+    assert rel_err(got, ref) < 1e-10
+    got32 = K.krr_precond_apply(f, w.mu, R, prec="mixed")
+    assert rel_err(got32, ref) < 1e-4
+
+
+def test_fp64_solve_matches_oracle(K, c1):
+    w, ref_f, f = c1
+    ref = O.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, ref_f.F, tol=w.tol)
+    alpha, info = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=w.tol, prec="fp64")
+    assert info["status"] == "KRR_OK"
+    assert abs(info["iters"] - ref.iters[0]) <= 1
+    assert rel_err(alpha, ref.alpha) < 1e-10
+    assert info["rel_residual"] < 2 * w.tol
+    # pinned to the dense Cholesky solve
+    A = O.kernel_block(w.X, w.kernel, w.sigma)
+    dense = sla.cho_solve(sla.cho_factor(A + w.lam * np.eye(w.N)), w.Y[0])
+    assert rel_err(alpha[0], dense) < 1e-6
+
+
+def test_mixed_solve_matches_oracle(K, c1):
+    w, ref_f, f = c1
+    ref = O.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, ref_f.F, tol=1e-12)
+    alpha, info = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=1e-10, prec="mixed")
+    assert info["status"] == "KRR_OK"
+    assert rel_err(alpha, ref.alpha) < 1e-6
+    alpha6, info6 = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=1e-6, prec="mixed")
+    assert info6["status"] == "KRR_OK"
+    rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, alpha6)
+    assert rr.max() <= 1e-6
+    assert abs(rr.max() - info6["rel_residual"]) < 1e-9
+
+
+def test_no_preconditioner_and_zero_rhs(K):
+    w = make_c1_plain_fp64(n=600)
+    Y = np.vstack([w.Y, np.zeros((1, w.N))])
+    alpha, info = K.krr_pcg_solve(w.X, w.kernel, w.sigma, Y, 1e-3, None, tol=1e-10, prec="fp64")
+    assert info["status"] == "KRR_OK"
+    assert not alpha[1].any()
+    A = O.kernel_block(w.X, w.kernel, w.sigma)
+    dense = np.linalg.solve(A + 1e-3 * w.N * np.eye(w.N), w.Y[0])
+    assert rel_err(alpha[0], dense) < 1e-8
+
+
+@pytest.mark.parametrize("kern", [O.LAPLACE_L1, O.MATERN52])
+def test_other_kernels_mixed(K, kern):
+    w = make_c2_mixed(n=6000, m=2, k=300)
+    f = K.krr_rpcholesky(w.X, kern, 1.0, w.k, 30, 3)
+    alpha, info = K.krr_pcg_solve(w.X, kern, 1.0, w.Y, 1e-6, f, tol=1e-6, prec="mixed")
+    assert info["status"] == "KRR_OK"
+    rr = O.true_relres(w.X, kern, 1.0, 1e-6 * w.N, w.Y, alpha)
+    assert rr.max() <= 1e-6
+
+
+def test_ill_conditioned_mixed_scaled(K):
+    """The near-duplicate workload at 20000 points, 4 right-hand sides."""
+    w = make_c2_mixed(n=20_000, k=400)
+    f = K.krr_rpcholesky(w.X, w.kernel, w.sigma, w.k, 40, 1)
+    alpha, info = K.krr_pcg_solve(to_dev(w.X), w.kernel, w.sigma, to_dev(w.Y), w.mu, f,
+                                  tol=w.tol, prec="mixed")
+    assert info["status"] == "KRR_OK"
+    rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, alpha.cpu().numpy())
+    assert rr.max() <= w.tol
+
+
+def test_full_size_mixed_solve(K):
+    """100000 points, d = 16, rank 1000, 4 right-hand sides, tol 1e-6: the
+    float64 residual recomputed by the oracle meets the tolerance."""
+    w = make_c2_mixed()
+    f = K.krr_rpcholesky(to_dev(w.X), w.kernel, w.sigma, w.k, w.block, w.seed)
+    alpha, info = K.krr_pcg_solve(to_dev(w.X), w.kernel, w.sigma, to_dev(w.Y), w.mu, f,
+                                  tol=w.tol, prec="mixed")
+    assert info["status"] == "KRR_OK", info
+    rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, alpha.cpu().numpy())
+    assert rr.max() <= w.tol * 1.001

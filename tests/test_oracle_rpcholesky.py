@@ -25,7 +25,7 @@ def brute_rpcholesky(A, k, B, seed):
     t = 0
     while F.shape[1] < k:
         nd = min(B, k - F.shape[1])
-        draws = independent_sample(d, seed, t, nd)
+        draws = independent_sample(d, seed, t, nd, N * 2.0 ** -52)
         t += 1
         if len(draws) == 0:
             break

@@ -48,10 +48,11 @@ def test_philox_random_counters():
         np.testing.assert_array_equal(O.philox4x64(ctr, key), numpy_philox_block(ctr, key))
 
 
-def independent_sample(dres, seed, t, ndraw):
+def independent_sample(dres, seed, t, ndraw, dfloor=0.0):
     N = len(dres)
     fbits = 62 - int(np.ceil(np.log2(N))) if N > 1 else 62
-    w = [int(np.floor(min(max(v, 0.0), 1.0) * 2.0 ** fbits)) if v > 0 else 0 for v in dres]
+    w = [int(np.floor(min(v, 1.0) * 2.0 ** fbits)) if (v > 0 and v > dfloor) else 0
+         for v in dres]
     W = np.cumsum(np.array(w, dtype=object))
     tot = int(W[-1])
     if tot == 0:
@@ -85,6 +86,9 @@ def test_sampler_matches_independent_restatement(N):
         got = O.rpc_sample(dres, 99, t, 50)
         ref = independent_sample(dres, 99, t, 50)
         np.testing.assert_array_equal(got, ref)
+    floor = float(np.median(dres))
+    np.testing.assert_array_equal(O.rpc_sample(dres, 5, 1, 50, floor),
+                                  independent_sample(dres, 5, 1, 50, floor))
 
 
 def test_sampler_all_zero_returns_nothing():
@@ -96,6 +100,11 @@ def test_sampler_never_draws_zero_weight():
     dres = np.zeros(1000)
     dres[[17, 500, 999]] = [0.2, 1e-9, 0.7]
     draws = np.concatenate([O.rpc_sample(dres, 3, t, 100) for t in range(50)])
+    assert set(np.unique(draws)) <= {17, 500, 999}
+    # residuals at or below the floor carry no weight
+    dres[[3, 4]] = [1e-13, O.drop_threshold(1000)]
+    draws = np.concatenate([O.rpc_sample(dres, 3, t, 100, O.drop_threshold(1000))
+                            for t in range(50)])
     assert set(np.unique(draws)) <= {17, 500, 999}
 
 
