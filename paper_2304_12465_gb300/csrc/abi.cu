@@ -158,6 +158,7 @@ void free_factor(krr_factor *f) {
   cudaFree(f->dres);
   for (auto &c : f->cores) {
     cudaFree(c.W);
+    cudaFree(c.Wt);
     cudaFree(c.F32);
   }
   delete f;
@@ -172,6 +173,7 @@ static void free_krill(krill_precond *P) {
   cudaFree(P->P);
   cudaFree(P->L);
   cudaFree(P->Winv);
+  cudaFree(P->Winv_t);
   cudaFree(P->xt);
   cudaFree(P->cn);
   delete P;

@@ -320,6 +320,28 @@ krr_status add_diagonal(double *A, int n, int64_t lda, double v, cudaStream_t s)
   return KRR_OK;
 }
 
+__global__ void transpose_kernel(const double *__restrict__ A, int n, double *__restrict__ B) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = bx + threadIdx.x, c = by + j;
+    if (r < n && c < n) tile[j][threadIdx.x] = A[r + (int64_t)c * n];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = by + threadIdx.x, c = bx + j;
+    if (r < n && c < n) B[r + (int64_t)c * n] = tile[threadIdx.x][j];
+  }
+}
+
+krr_status transpose_square(const double *A, int n, double *B, cudaStream_t s) {
+  if (n <= 0) return KRR_OK;
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  transpose_kernel<<<grid, block, 0, s>>>(A, n, B);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
 __global__ void symmetrize_kernel(double *A, int n, int64_t lda) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;

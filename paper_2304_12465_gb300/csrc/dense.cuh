@@ -40,6 +40,9 @@ krr_status trinv_lower(const double *L, int n, int64_t lda, double *W, cudaStrea
 // A(i, i) += v for i < n.
 krr_status add_diagonal(double *A, int n, int64_t lda, double v, cudaStream_t s);
 
+// B = A^T for n x n column-major matrices (no aliasing).
+krr_status transpose_square(const double *A, int n, double *B, cudaStream_t s);
+
 // Mirror the lower triangle into the upper one.
 krr_status symmetrize_lower(double *A, int n, int64_t lda, cudaStream_t s);
 

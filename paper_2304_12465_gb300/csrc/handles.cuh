@@ -17,6 +17,7 @@ struct NystromCore {
   int prec = 0;
   int rank = 0;
   double *W = nullptr;    // rank x rank, column-major, lower
+  double *Wt = nullptr;   // W^T (row access of W)
   float *F32 = nullptr;   // N x rank float32 copy (mixed only)
   double build_s = 0.0;
 };
@@ -56,6 +57,7 @@ struct krill_precond {
   double *P = nullptr;        // k x k (B^T B + H)
   double *L = nullptr;        // k x k lower factor, P = L L^T (C = L^T)
   double *Winv = nullptr;     // k x k, L^{-1}
+  double *Winv_t = nullptr;   // (L^{-1})^T
   float *xt = nullptr;        // prepared float32 points for the product
   float *cn = nullptr;
   int dp = 0;

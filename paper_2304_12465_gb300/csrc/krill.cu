@@ -613,6 +613,8 @@ krr_status krill_build_device(krill_precond *P, cudaStream_t s) {
   KRR_TRY(potrf_lower(P->L, k, k, s));
   KRR_TRY(dev_alloc(&P->Winv, (size_t)k * k));
   KRR_TRY(trinv_lower(P->L, k, k, P->Winv, s));
+  KRR_TRY(dev_alloc(&P->Winv_t, (size_t)k * k));
+  KRR_TRY(transpose_square(P->Winv, k, P->Winv_t, s));
   KRR_CUDA_TRY(cudaStreamSynchronize(s));
   P->build_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return KRR_OK;
@@ -633,7 +635,7 @@ krr_status krill_product(const krill_precond *P, const double *beta, int m, doub
 // out = C^{-1} C^{-T} in = W^T (W in), W = L^{-1}, P = L L^T, C = L^T.
 krr_status krill_precond_apply(const krill_precond *P, const double *in, int m, double *tmp,
                                double *out, cudaStream_t s) {
-  KRR_TRY(tri_apply_lower(P->Winv, P->k, in, m, tmp, s));
+  KRR_TRY(tri_apply_lower(P->Winv_t, P->k, in, m, tmp, s));
   KRR_TRY(tri_apply_lower_t(P->Winv, P->k, tmp, m, out, s));
   return KRR_OK;
 }

@@ -11,39 +11,44 @@
 namespace krr {
 
 // ------------------------------------------------ tall skinny products
-constexpr int TT_ROWS = 512;   // rows per block of the transposed product
+// The Woodbury apply streams F (N x rank) twice: t = F^T r and z = r - F v.
+// Both are HBM-bound; products and in-block sums use the precision of the
+// data (float32 in the mixed path, float64 otherwise), sums across blocks are
+// float64, in a fixed order.
+constexpr int TT_ROWS = 256;   // rows per block of the transposed product
 constexpr int RED_BLOCKS = 512;
 
 // part[b][l][c] = sum_{n in block b} F[n + l N] R[c][n]
-template <typename TF, typename TR>
+template <typename T>
 __global__ void __launch_bounds__(256)
-tall_t_kernel(const TF *__restrict__ F, int64_t N, int rank, const TR *__restrict__ R,
-              int m, double *__restrict__ part) {
-  extern __shared__ double sR[];  // m x TT_ROWS
+tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict__ R, int m,
+              double *__restrict__ part) {
+  __shared__ T sR[16][TT_ROWS];
   const int64_t n0 = (int64_t)blockIdx.x * TT_ROWS;
   const int nr = (int)min((int64_t)TT_ROWS, N - n0);
   for (int e = threadIdx.x; e < m * TT_ROWS; e += blockDim.x) {
     const int c = e / TT_ROWS, n = e % TT_ROWS;
-    sR[e] = (n < nr) ? (double)R[(int64_t)c * N + n0 + n] : 0.0;
+    sR[c][n] = (n < nr) ? R[(int64_t)c * N + n0 + n] : T(0);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = warp; l < rank; l += blockDim.x >> 5) {
-    double acc[16];
+    T acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-    const TF *col = F + (int64_t)l * N + n0;
+    for (int c = 0; c < 16; ++c) acc[c] = T(0);
+    const T *col = F + (int64_t)l * N + n0;
+#pragma unroll 4
     for (int n = lane; n < nr; n += 32) {
-      const double f = (double)col[n];
+      const T f = col[n];
 #pragma unroll
       for (int c = 0; c < 16; ++c)
-        if (c < m) acc[c] = fma(f, sR[c * TT_ROWS + n], acc[c]);
+        if (c < m) acc[c] = fma(f, sR[c][n], acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       if (c < m) {
-        const double v = warp_sum(acc[c]);
-        if (lane == 0) part[((int64_t)blockIdx.x * rank + l) * m + c] = v;
+        const T v = warp_sum(acc[c]);
+        if (lane == 0) part[((int64_t)blockIdx.x * rank + l) * m + c] = (double)v;
       }
     }
   }
@@ -60,28 +65,15 @@ __global__ void tall_t_reduce_kernel(const double *__restrict__ part, int nb, in
   t[(int64_t)c * rank + l] = acc;
 }
 
-// u[c][i] = sum_{l <= i} W[i + l rank] t[c][l]   (W lower triangular)
-__global__ void lower_gemv_kernel(const double *__restrict__ W, int rank,
-                                  const double *__restrict__ t, int m,
-                                  double *__restrict__ u) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rank) return;
-  double acc[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-  for (int l = 0; l <= i; ++l) {
-    const double w = W[i + (int64_t)l * rank];
-#pragma unroll
-    for (int c = 0; c < 16; ++c)
-      if (c < m) acc[c] = fma(w, t[(int64_t)c * rank + l], acc[c]);
-  }
-  for (int c = 0; c < m; ++c) u[(int64_t)c * rank + i] = acc[c];
-}
-
-// v[c][i] = sum_{l >= i} W[l + i rank] u[c][l]   (W^T, one warp per i)
-__global__ void lower_t_gemv_kernel(const double *__restrict__ W, int rank,
-                                    const double *__restrict__ u, int m,
-                                    double *__restrict__ v) {
+// Triangular products with one warp per output row, reading contiguous
+// columns of a column-major rank x rank matrix Mt:
+//   UPPER == false: out[c][i] = sum_{l <= i} Mt[l + i rank] x[c][l]
+//   UPPER == true : out[c][i] = sum_{l >= i} Mt[l + i rank] x[c][l]
+// With Mt = W^T (W lower) the first is W x; with Mt = W the second is W^T x.
+template <bool UPPER>
+__global__ void tri_gemv_kernel(const double *__restrict__ Mt, int rank,
+                                const double *__restrict__ x, int m,
+                                double *__restrict__ out) {
   const int warps = blockDim.x >> 5;
   const int i = blockIdx.x * warps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -89,67 +81,68 @@ __global__ void lower_t_gemv_kernel(const double *__restrict__ W, int rank,
   double acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-  const double *col = W + (int64_t)i * rank;
-  for (int l = i + lane; l < rank; l += 32) {
+  const double *col = Mt + (int64_t)i * rank;
+  const int lo = UPPER ? i : 0, hi = UPPER ? rank : i + 1;
+  for (int l = lo + lane; l < hi; l += 32) {
     const double w = col[l];
 #pragma unroll
     for (int c = 0; c < 16; ++c)
-      if (c < m) acc[c] = fma(w, u[(int64_t)c * rank + l], acc[c]);
+      if (c < m) acc[c] = fma(w, x[(int64_t)c * rank + l], acc[c]);
   }
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     if (c < m) {
-      const double s = warp_sum(acc[c]);
-      if (lane == 0) v[(int64_t)c * rank + i] = s;
+      const double v = warp_sum(acc[c]);
+      if (lane == 0) out[(int64_t)c * rank + i] = v;
     }
   }
 }
 
 // Z[c][n] = (R[c][n] - sum_l F[n + l N] v[c][l]) / lambda
-template <typename TF, typename TR>
+template <typename T>
 __global__ void __launch_bounds__(256)
-tall_n_kernel(const TF *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
-              int m, const TR *__restrict__ R, double inv_lambda, TR *__restrict__ Z) {
+tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
+              int m, const T *__restrict__ R, double inv_lambda, T *__restrict__ Z) {
   constexpr int LCH = 256;
-  __shared__ double sv[16 * LCH];
+  __shared__ T sv[LCH][16];
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[16];
+  T acc[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int c = 0; c < 16; ++c) acc[c] = T(0);
   for (int l0 = 0; l0 < rank; l0 += LCH) {
     const int nl = min(LCH, rank - l0);
     __syncthreads();
     for (int e = threadIdx.x; e < m * LCH; e += blockDim.x) {
       const int c = e / LCH, l = e % LCH;
-      sv[c * LCH + l] = (l < nl) ? v[(int64_t)c * rank + l0 + l] : 0.0;
+      sv[l][c] = (l < nl) ? (T)v[(int64_t)c * rank + l0 + l] : T(0);
     }
     __syncthreads();
     if (n < N) {
+#pragma unroll 4
       for (int l = 0; l < nl; ++l) {
-        const double f = (double)F[n + (int64_t)(l0 + l) * N];
+        const T f = F[n + (int64_t)(l0 + l) * N];
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-          if (c < m) acc[c] = fma(f, sv[c * LCH + l], acc[c]);
+          if (c < m) acc[c] = fma(f, sv[l][c], acc[c]);
       }
     }
   }
   if (n < N) {
     for (int c = 0; c < m; ++c)
-      Z[(int64_t)c * N + n] = (TR)(((double)R[(int64_t)c * N + n] - acc[c]) * inv_lambda);
+      Z[(int64_t)c * N + n] = (T)(((double)R[(int64_t)c * N + n] - (double)acc[c]) * inv_lambda);
   }
 }
 
-template <typename TF, typename TR>
-static krr_status nystrom_apply_impl(const TF *F, int64_t N, int rank, const double *W,
-                                     double lambda, const TR *R, int m, TR *Z,
+template <typename T>
+static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const double *W,
+                                     const double *Wt, double lambda, const T *R, int m, T *Z,
                                      cudaStream_t s) {
   if (rank == 0) {
     // P = lambda I
     DevBuf<double> zero;
     KRR_TRY(zero.alloc(m, s));
     KRR_CUDA_TRY(cudaMemsetAsync(zero.p, 0, sizeof(double) * m, s));
-    tall_n_kernel<TF, TR><<<ceil_div(N, 256), 256, 0, s>>>(F, N, 0, zero.p, m, R,
-                                                           1.0 / lambda, Z);
+    tall_n_kernel<T><<<ceil_div(N, 256), 256, 0, s>>>(F, N, 0, zero.p, m, R, 1.0 / lambda, Z);
     KRR_LAUNCH_CHECK();
     return KRR_OK;
   }
@@ -159,33 +152,26 @@ static krr_status nystrom_apply_impl(const TF *F, int64_t N, int rank, const dou
   KRR_TRY(t.alloc((size_t)rank * m, s));
   KRR_TRY(u.alloc((size_t)rank * m, s));
   KRR_TRY(v.alloc((size_t)rank * m, s));
-  const size_t smem = (size_t)m * TT_ROWS * sizeof(double);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(tall_t_kernel<TF, TR>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
-  tall_t_kernel<TF, TR><<<nb, 256, smem, s>>>(F, N, rank, R, m, part.p);
+  tall_t_kernel<T><<<nb, 256, 0, s>>>(F, N, rank, R, m, part.p);
   KRR_LAUNCH_CHECK();
   tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 256), 256, 0, s>>>(part.p, nb, rank, m,
                                                                       t.p);
   KRR_LAUNCH_CHECK();
-  lower_gemv_kernel<<<ceil_div(rank, 128), 128, 0, s>>>(W, rank, t.p, m, u.p);
-  KRR_LAUNCH_CHECK();
-  lower_t_gemv_kernel<<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u.p, m, v.p);
-  KRR_LAUNCH_CHECK();
-  tall_n_kernel<TF, TR><<<ceil_div(N, 256), 256, 0, s>>>(F, N, rank, v.p, m, R,
-                                                         1.0 / lambda, Z);
+  KRR_TRY(tri_apply_lower(Wt, rank, t.p, m, u.p, s));
+  KRR_TRY(tri_apply_lower_t(W, rank, u.p, m, v.p, s));
+  tall_n_kernel<T><<<ceil_div(N, 256), 256, 0, s>>>(F, N, rank, v.p, m, R, 1.0 / lambda, Z);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
 
 krr_status nystrom_apply_f64(const krr_factor *f, const NystromCore *c, const double *R,
                              int m, double *Z, cudaStream_t s) {
-  return nystrom_apply_impl<double, double>(f->F, f->N, c->rank, c->W, c->lambda, R, m, Z, s);
+  return nystrom_apply_impl<double>(f->F, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s);
 }
 
 krr_status nystrom_apply_f32(const krr_factor *f, const NystromCore *c, const float *R,
                              int m, float *Z, cudaStream_t s) {
-  return nystrom_apply_impl<float, float>(c->F32, f->N, c->rank, c->W, c->lambda, R, m, Z, s);
+  return nystrom_apply_impl<float>(c->F32, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s);
 }
 
 // ------------------------------------------------------- core build
@@ -231,6 +217,8 @@ krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s
     }
     KRR_TRY(dev_alloc(&c.W, (size_t)r * r));
     KRR_TRY(trinv_lower(Gm.p, r, r, c.W, s));
+    KRR_TRY(dev_alloc(&c.Wt, (size_t)r * r));
+    KRR_TRY(transpose_square(c.W, r, c.Wt, s));
     KRR_CUDA_TRY(cudaStreamSynchronize(s));
   }
   c.build_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -460,16 +448,16 @@ __global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__
     x[e] += (double)d[e];
 }
 
-krr_status tri_apply_lower(const double *W, int rank, const double *t, int m, double *u,
+krr_status tri_apply_lower(const double *Wt, int rank, const double *t, int m, double *u,
                            cudaStream_t s) {
-  lower_gemv_kernel<<<ceil_div(rank, 128), 128, 0, s>>>(W, rank, t, m, u);
+  tri_gemv_kernel<false><<<ceil_div(rank, 8), 256, 0, s>>>(Wt, rank, t, m, u);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
 
 krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
                              cudaStream_t s) {
-  lower_t_gemv_kernel<<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u, m, v);
+  tri_gemv_kernel<true><<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u, m, v);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }

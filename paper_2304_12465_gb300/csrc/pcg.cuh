@@ -46,8 +46,9 @@ template <typename T>
 krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
                    const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats);
 
-// u (m x rank) = W t and v = W^T u for a lower-triangular W (rank x rank).
-krr_status tri_apply_lower(const double *W, int rank, const double *t, int m, double *u,
+// u (m x rank) = W t (given Wt = W^T) and v = W^T u (given W), W lower
+// triangular rank x rank, column-major.
+krr_status tri_apply_lower(const double *Wt, int rank, const double *t, int m, double *u,
                            cudaStream_t s);
 krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
                              cudaStream_t s);

@@ -44,16 +44,28 @@ def test_precond_apply(K, c1):
 
 def test_fp64_solve_matches_oracle(K, c1):
     w, ref_f, f = c1
+    # equal iteration counts: the float64 iterates agree to rounding
+    ref100 = O.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, ref_f.F, tol=1e-300, maxit=100)
+    a100, i100 = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=1e-300, maxit=100,
+                                 prec="fp64")
+    assert i100["status"] == "KRR_ENOCONV" and i100["iters"] == 100
+    assert rel_err(a100, ref100.alpha) < 1e-10
+    # to the tolerance: same stopping iteration up to rounding of the
+    # recursive residual near the threshold, float64 residual below tol
     ref = O.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, ref_f.F, tol=w.tol)
     alpha, info = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=w.tol, prec="fp64")
     assert info["status"] == "KRR_OK"
-    assert abs(info["iters"] - ref.iters[0]) <= 1
-    assert rel_err(alpha, ref.alpha) < 1e-10
+    assert abs(info["iters"] - ref.iters[0]) <= 5
     assert info["rel_residual"] < 2 * w.tol
-    # pinned to the dense Cholesky solve
+    rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, alpha)
+    assert rr.max() < 2 * w.tol
+    # pinned to the dense Cholesky solve: error <= cond(A + lam I) x residual
     A = O.kernel_block(w.X, w.kernel, w.sigma)
-    dense = sla.cho_solve(sla.cho_factor(A + w.lam * np.eye(w.N)), w.Y[0])
-    assert rel_err(alpha[0], dense) < 1e-6
+    M = A + w.lam * np.eye(w.N)
+    dense = sla.cho_solve(sla.cho_factor(M), w.Y[0])
+    cond = np.linalg.cond(M)
+    assert rel_err(alpha[0], dense) < max(1e-9, 2 * cond * w.tol)
+    assert rel_err(alpha[0], ref.alpha[0]) < max(1e-9, 4 * cond * w.tol)
 
 
 def test_mixed_solve_matches_oracle(K, c1):
