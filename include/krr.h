@@ -226,6 +226,31 @@ KRR_API krr_status krill_solve(const krill_precond *P, const double *Y, int m,
 
 KRR_API void krill_free(krill_precond *P);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free float64 fused product (the paper has no counterpart: this  */
+/* entry point exists for callers that cannot allocate device memory on their */
+/* call path -- e.g. a serving loop that reserved all its memory up front and */
+/* must not let a request trigger cudaMalloc, or a plug-in that only receives */
+/* buffers from a framework that owns all device memory).                    */
+/*   Y = (A + lambda I) V, the same product as krr_kmatvec with               */
+/*   KRR_PREC_FP64, computed with no allocation of any kind.                  */
+/* X (N x d), V and Y (N x m, column-major) must be device pointers on the    */
+/* current device; host pointers are rejected with KRR_EINVAL (staging them   */
+/* would allocate).  The split partial sums live in one 16 MiB static device  */
+/* array owned by the library (held by every GPU that loads the library until */
+/* the process exits), so N x padded(m) must be <= 2^21, padded(m) being m    */
+/* rounded up to 1, 2, 4, 8 or 16; larger sizes return KRR_EINVAL with a      */
+/* message.  The first call on each device looks up the array's device        */
+/* address and caches it; make that first call before any stream capture.    */
+/* Every call shares the one array and overwrites the partial sums it reads  */
+/* (nothing needs to start at zero), so calls that overlap on the GPU race:   */
+/* serialise them (one stream, or events).  Returns after the stream is       */
+/* synchronised.                                                              */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
+                                           krr_kernel kern, double sigma, double lambda,
+                                           const double *V, int m, double *Y, void *stream);
+
 /* Timing instrumentation: while on (non-zero), solves record CUDA events
  * around every fused-product launch on the caller's stream and report the
  * summed device time in krr_info.kmv_ms / kmv_launches. */

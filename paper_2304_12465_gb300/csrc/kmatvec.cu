@@ -194,6 +194,46 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
   return KRR_OK;
 }
 
+// Same product with caller-provided split scratch of `scratch_elems` doubles:
+// the column split count is reduced until the partial sums fit.  Launches
+// only the product and reduction kernels (no allocation).
+krr_status kmv_f64_with_scratch(const double *Xd, int64_t N, int d, int kern, double sigma,
+                                double lambda, const double *V, int64_t ldv, int m, double *Y,
+                                int64_t ldy, double *scratch, size_t scratch_elems,
+                                cudaStream_t s) {
+  if (N == 0 || m == 0) return KRR_OK;
+  const int dp = (d + 3) / 4 * 4;
+  double inv_scale = (kern == KGAUSS) ? 1.0 / (2.0 * sigma * sigma) : 1.0 / sigma;
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    if ((size_t)M * (size_t)N > scratch_elems) {
+      set_error("scratch of %zu doubles cannot hold N x %d = %lld partial sums", scratch_elems,
+                M, (long long)N * M);
+      return KRR_EINVAL;
+    }
+    const int64_t row_tiles = (N + KMV64_THREADS - 1) / KMV64_THREADS;
+    int splits = choose_splits(row_tiles, N, KMV64_TJ, 4, 4);
+    const int64_t fit = (int64_t)(scratch_elems / ((size_t)M * (size_t)N));
+    if (splits > fit) splits = (int)fit;
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV64_TJ - 1) / KMV64_TJ * KMV64_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    Kmv64Args a{Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, scratch};
+    cudaError_t e = launch_kmv64_any(kern, dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("float64 product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<double, 16><<<ceil_div(N, 256), 256, 0, s>>>(
+        scratch, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
+        Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
 // ------------------------------------------------------- conversions
 __global__ void f64_to_f32_kernel(const double *__restrict__ a, float *__restrict__ b,
                                   int64_t n) {

@@ -29,6 +29,13 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
                    double lambda, const double *V, int64_t ldv, int m, double *Y,
                    int64_t ldy, cudaStream_t s, DevBuf<double> &part);
 
+// kmv_f64 with caller-provided scratch for the split partial sums (no
+// allocation); KRR_EINVAL if N x padded(m) exceeds scratch_elems.
+krr_status kmv_f64_with_scratch(const double *Xd, int64_t N, int d, int kern, double sigma,
+                                double lambda, const double *V, int64_t ldv, int m, double *Y,
+                                int64_t ldy, double *scratch, size_t scratch_elems,
+                                cudaStream_t s);
+
 // Number of kernel entries one product evaluates (N^2).
 inline double kmv_entries(int64_t N) { return (double)N * (double)N; }
 
