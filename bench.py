@@ -196,6 +196,8 @@ def run_native(args):
     peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA units x clock
     kmv64_ms = sum(i["kmv64_ms"] for i in infos)
     kmv64_n = sum(i["kmv64_launches"] for i in infos)
+    kmvff_ms = sum(i["kmvff_ms"] for i in infos)
+    kmvff_n = sum(i["kmvff_launches"] for i in infos)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -219,7 +221,9 @@ def run_native(args):
                 "t_solve_s": [i["t_solve_s"] for i in infos],
                 "kmv32_ms_per_launch": per_launch_ms, "kmv32_launches": kmv_n,
                 "kmv64_ms_per_launch": kmv64_ms / max(kmv64_n, 1),
-                "kmv64_launches": kmv64_n},
+                "kmv64_launches": kmv64_n,
+                "kmvff_ms_per_launch": kmvff_ms / max(kmvff_n, 1),
+                "kmvff_launches": kmvff_n},
         "roofline": {"kernel": "kmv32_kernel (fused float32 product)", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,

@@ -63,8 +63,13 @@ typedef enum {
 
 typedef enum {
     KRR_PREC_FP64 = 0,   /* every step in float64                             */
-    KRR_PREC_MIXED = 1   /* float32 kernel tiles and inner PCG, float64 outer
-                            iterative refinement, CG scalars and k x k core    */
+    KRR_PREC_MIXED = 1,  /* float32 kernel tiles and inner PCG, float64-accurate
+                            outer iterative refinement, float64 CG scalars and
+                            k x k core                                         */
+    KRR_PREC_FLOAT_FLOAT = 2  /* krr_kmatvec only: float64-accurate product
+                            (about 2^-46 per entry) evaluated in float-float
+                            arithmetic on the float32 pipes; the product the
+                            mixed path uses for its refinement residuals       */
 } krr_precision;
 
 typedef struct krr_factor krr_factor;        /* RPCholesky factor F, pivots S */
@@ -87,6 +92,9 @@ typedef struct {
     int kmv_launches;        /* number of float32 fused-product launches      */
     int kmv64_launches;      /* number of float64 fused-product launches      */
     double kmv64_ms;         /* summed device time of the float64 product     */
+    double kmvff_ms;         /* summed device time of the float-float product */
+    int kmvff_launches;      /* number of float-float fused-product launches  */
+    int reserved3;
 } krr_info;
 
 /* ------------------------------------------------------------------------ */
@@ -94,7 +102,9 @@ typedef struct {
 /*   Y = (A + lambda I) V,  A_ij = kappa(x_i, x_j), never stored.            */
 /* precision KRR_PREC_FP64 evaluates in float64 with direct differences;     */
 /* KRR_PREC_MIXED evaluates kernel tiles in float32 (distances from row      */
-/* norms of centred points) and accumulates in float32.                      */
+/* norms of centred points) and accumulates in float32;                      */
+/* KRR_PREC_FLOAT_FLOAT evaluates entries and sums in float-float arithmetic */
+/* (error-free transformations on the float32 pipes, ~2^-46 per entry).     */
 /* V, Y: N x m column-major float64.  Y may not alias V.                     */
 /* ------------------------------------------------------------------------ */
 KRR_API krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern,
@@ -164,7 +174,8 @@ KRR_API krr_status krr_precond_apply(const krr_factor *F, double mu, const doubl
 /* ||r|| / ||y|| <= tol).                                                     */
 /*   KRR_PREC_FP64 : float64 throughout.                                      */
 /*   KRR_PREC_MIXED: iterative refinement -- an outer float64 loop x += d,    */
-/*     r = y - (A + lambda I) x recomputed with the float64 product, around   */
+/*     r = y - (A + lambda I) x recomputed with the float-float product       */
+/*     (KRR_PREC_FLOAT_FLOAT of krr_kmatvec, float64-accurate), around        */
 /*     an inner float32 PCG (float32 kernel tiles, float64 CG scalars) that   */
 /*     solves (A + lambda I) d = r to a loose tolerance; stops when the       */
 /*     float64 relative residual is <= tol.                                   */

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA",
                 4: "KRR_ECHOL", 5: "KRR_EBREAKDOWN", 6: "KRR_ENOCONV", 7: "KRR_ETIMEOUT"}
 
 GAUSSIAN, LAPLACE_L1, MATERN52 = 0, 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FLOAT_FLOAT = 0, 1, 2
 
 
 class KrrInfo(C.Structure):
@@ -26,10 +26,12 @@ class KrrInfo(C.Structure):
                 ("kernel_entries", C.c_double), ("t_build_s", C.c_double),
                 ("t_solve_s", C.c_double), ("kmv_ms", C.c_double),
                 ("kmv_launches", C.c_int), ("kmv64_launches", C.c_int),
-                ("kmv64_ms", C.c_double)]
+                ("kmv64_ms", C.c_double), ("kmvff_ms", C.c_double),
+                ("kmvff_launches", C.c_int), ("reserved3", C.c_int)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_
+                if not name.startswith("reserved")}
 
 
 class KrrError(RuntimeError):

@@ -24,7 +24,7 @@ except Exception:  # pragma: no cover
 
 _KERNELS = {"gaussian": N_.GAUSSIAN, "laplace": N_.LAPLACE_L1, "laplace_l1": N_.LAPLACE_L1,
             "matern52": N_.MATERN52, "matern": N_.MATERN52}
-_PRECS = {"fp64": N_.PREC_FP64, "mixed": N_.PREC_MIXED}
+_PRECS = {"fp64": N_.PREC_FP64, "mixed": N_.PREC_MIXED, "ff": N_.PREC_FLOAT_FLOAT}
 
 
 def _kern(k) -> int:

@@ -203,7 +203,8 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
   KRR_CHECK_POINTS(X, N, d, kern, sigma);
   KRR_REQUIRE(V && Y, "V and Y must not be NULL");
   KRR_REQUIRE(m >= 1 && m <= 16, "m must be in [1, 16]");
-  KRR_REQUIRE(prec == KRR_PREC_FP64 || prec == KRR_PREC_MIXED, "unknown precision");
+  KRR_REQUIRE(prec == KRR_PREC_FP64 || prec == KRR_PREC_MIXED || prec == KRR_PREC_FLOAT_FLOAT,
+              "unknown precision");
   KRR_REQUIRE(std::isfinite(lambda), "lambda must be finite");
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf<double> tx, tv;
@@ -215,6 +216,12 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
   if (prec == KRR_PREC_FP64) {
     DevBuf<double> part;
     KRR_TRY(kmv_f64(Xd, N, d, kern, sigma, lambda, Vd, N, m, out.dev, N, s, part));
+  } else if (prec == KRR_PREC_FLOAT_FLOAT) {
+    PointsFF P;
+    KRR_TRY(prepare_points_ff(Xd, N, d, kern, sigma, s, P));
+    DevBuf<double> part;
+    DevBuf<float> vsplit;
+    KRR_TRY(kmv_ff(P, lambda, Vd, N, m, out.dev, N, s, part, vsplit));
   } else {
     PointsF32 P;
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
@@ -374,6 +381,7 @@ krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel kern, dou
   if (info && prof) {
     kmv_profile_collect(0, &info->kmv_ms, &info->kmv_launches);
     kmv_profile_collect(1, &info->kmv64_ms, &info->kmv64_launches);
+    kmv_profile_collect(2, &info->kmvff_ms, &info->kmvff_launches);
   }
   return st;
 }

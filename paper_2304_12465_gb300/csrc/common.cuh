@@ -179,7 +179,7 @@ bool profiling_on();
 struct KmvTimer {
   cudaEvent_t a = nullptr, b = nullptr;
   bool on = false;
-  int tag = 0;               // 0: float32 product, 1: float64 product
+  int tag = 0;               // 0: float32, 1: float64, 2: float-float product
   explicit KmvTimer(int t = 0) : tag(t) {}
   void begin(cudaStream_t s);
   void end(cudaStream_t s);

@@ -9,6 +9,9 @@ cudaError_t launch_kmv32_gauss(int DP, int M, dim3 g, cudaStream_t s, const Kmv3
 cudaError_t launch_kmv32_laplace(int DP, int M, dim3 g, cudaStream_t s, const Kmv32Args &a);
 cudaError_t launch_kmv32_matern(int DP, int M, dim3 g, cudaStream_t s, const Kmv32Args &a);
 cudaError_t launch_kmv64_gauss(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
+cudaError_t launch_kmvff_gauss(int DP, int M, dim3 g, cudaStream_t s, const KmvFFArgs &a);
+cudaError_t launch_kmvff_laplace(int DP, int M, dim3 g, cudaStream_t s, const KmvFFArgs &a);
+cudaError_t launch_kmvff_matern(int DP, int M, dim3 g, cudaStream_t s, const KmvFFArgs &a);
 cudaError_t launch_kmv64_laplace(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
 cudaError_t launch_kmv64_matern(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
 
@@ -28,6 +31,16 @@ cudaError_t launch_kmv64_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
     case KGAUSS: return launch_kmv64_gauss(DP, M, g, s, a);
     case KLAPLACE: return launch_kmv64_laplace(DP, M, g, s, a);
     case KMATERN: return launch_kmv64_matern(DP, M, g, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kmvff_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
+                             const KmvFFArgs &a) {
+  switch (kern) {
+    case KGAUSS: return launch_kmvff_gauss(DP, M, g, s, a);
+    case KLAPLACE: return launch_kmvff_laplace(DP, M, g, s, a);
+    case KMATERN: return launch_kmvff_matern(DP, M, g, s, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -93,6 +106,92 @@ krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, doub
                                                       with_norm, P.xt.p, P.cn.p);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
+}
+
+// float-float split of centred, scaled points: x = xh + xl (float), and the
+// constant c = -|xh + xl|^2 / 2 split as ch + cl.
+__global__ void prepare_ff_kernel(const double *__restrict__ X, int64_t N, int d, int dp,
+                                  const double *__restrict__ mean, double scale, int with_norm,
+                                  float *__restrict__ xh, float *__restrict__ xl,
+                                  float *__restrict__ ch, float *__restrict__ cl) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double nrm = 0.0;
+  for (int k = 0; k < dp; ++k) {
+    double v = (k < d) ? (X[i * d + k] - mean[k]) * scale : 0.0;
+    const float h = (float)v;
+    const float l = (float)(v - (double)h);
+    xh[i * dp + k] = h;
+    xl[i * dp + k] = l;
+    const double e = (double)h + (double)l;
+    nrm = fma(e, e, nrm);
+  }
+  const double c = with_norm ? -0.5 * nrm : 0.0;
+  const float c_h = (float)c;
+  ch[i] = c_h;
+  cl[i] = (float)(c - (double)c_h);
+}
+
+krr_status prepare_points_ff(const double *Xd, int64_t N, int d, int kern, double sigma,
+                             cudaStream_t s, PointsFF &P) {
+  P.dp = (d + 3) / 4 * 4;
+  P.d = d;
+  P.N = N;
+  P.kern = kern;
+  KRR_TRY(P.xh.alloc((size_t)N * P.dp, s));
+  KRR_TRY(P.xl.alloc((size_t)N * P.dp, s));
+  KRR_TRY(P.ch.alloc((size_t)N, s));
+  KRR_TRY(P.cl.alloc((size_t)N, s));
+  DevBuf<double> mean;
+  KRR_TRY(mean.alloc(d, s));
+  column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, mean.p);
+  KRR_LAUNCH_CHECK();
+  const double scale = (kern == KMATERN) ? std::sqrt(5.0) / sigma : 1.0 / sigma;
+  const int with_norm = 0;   // the float-float distance uses direct differences
+  prepare_ff_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, mean.p, scale, with_norm,
+                                                     P.xh.p, P.xl.p, P.ch.p, P.cl.p);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+__global__ void split_ff_kernel(const double *__restrict__ V, int64_t ldv, int64_t N, int m,
+                                float *__restrict__ vh, float *__restrict__ vl) {
+  const int64_t total = N * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    const int64_t i = e % N;
+    const double v = V[(int64_t)c * ldv + i];
+    const float h = (float)v;
+    vh[e] = h;
+    vl[e] = (float)(v - (double)h);
+  }
+}
+
+// Host-side constants of the float-float exponential (see kmvff_kernels.cuh):
+// ln2/32 split into floats (the first with 8 significant bits) and the table
+// 2^(j/32), j < 32, as hi + lo floats.  Mathematical constants from the host
+// C library in double precision.
+static ExpFFConsts make_exp_consts() {
+  ExpFFConsts e;
+  const double ln2 = 0.69314718055994530942;
+  const double c = ln2 / 32.0;
+  e.c[0] = (float)(32.0 / ln2);
+  int ex = 0;
+  const double fr = std::frexp(c, &ex);
+  const double c1 = std::ldexp(std::nearbyint(std::ldexp(fr, 8)), ex - 8);
+  const double rem = c - c1;
+  const float c2 = (float)rem;
+  e.c[1] = (float)c1;
+  e.c[2] = c2;
+  e.c[3] = (float)(rem - (double)c2);
+  for (int j = 0; j < 32; ++j) {
+    const double t = std::exp2(j / 32.0);
+    const float h = (float)t;
+    e.tab[2 * j] = h;
+    e.tab[2 * j + 1] = (float)(t - (double)h);
+  }
+  return e;
 }
 
 // ---------------------------------------------------------- reduction
@@ -184,6 +283,50 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
     count_launch();
     if (e != cudaSuccess) {
       set_error("float64 product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<double, 16><<<ceil_div(N, 256), 256, 0, s>>>(
+        part.p, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
+        Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv, int m,
+                  double *Y, int64_t ldy, cudaStream_t s, DevBuf<double> &part,
+                  DevBuf<float> &vsplit) {
+  const int64_t N = P.N;
+  if (N == 0 || m == 0) return KRR_OK;
+  static const ExpFFConsts ec = make_exp_consts();
+  if (vsplit.n < (size_t)2 * N * m) KRR_TRY(vsplit.alloc((size_t)2 * N * m, s));
+  float *vh = vsplit.p, *vl = vsplit.p + (size_t)N * m;
+  {
+    int64_t g = (N * m + 255) / 256;
+    if (g > num_sms() * 16) g = num_sms() * 16;
+    split_ff_kernel<<<(unsigned)g, 256, 0, s>>>(V, ldv, N, m, vh, vl);
+    KRR_LAUNCH_CHECK();
+  }
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    const int rows = KFF_THREADS * kmvff_rows_per_thread(P.dp);
+    const int64_t row_tiles = (N + rows - 1) / rows;
+    const int splits = choose_splits(row_tiles, N, KFF_TJ, 4, 6);
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KFF_TJ - 1) / KFF_TJ * KFF_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * N;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    KmvFFArgs a{P.xh.p, P.xl.p, P.ch.p, P.cl.p, vh + (int64_t)c0 * N, vl + (int64_t)c0 * N,
+                N, mg, chunk, ec, part.p};
+    KmvTimer tm(2);
+    tm.begin(s);
+    cudaError_t e = launch_kmvff_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    tm.end(s);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("float-float product launch failed: %s", cudaGetErrorString(e));
       return KRR_ECUDA;
     }
     kmv_reduce_kernel<double, 16><<<ceil_div(N, 256), 256, 0, s>>>(

@@ -20,6 +20,26 @@ struct PointsF32 {
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
                               double sigma, cudaStream_t s, PointsF32 &P);
 
+// Points split for the float-float product: centred, scaled x = xh + xl and
+// c = -|x|^2/2 = ch + cl (unused for Laplace).
+struct PointsFF {
+  DevBuf<float> xh, xl;   // N x dp
+  DevBuf<float> ch, cl;   // N
+  int dp = 0;
+  int d = 0;
+  int64_t N = 0;
+  int kern = 0;
+};
+
+krr_status prepare_points_ff(const double *Xd, int64_t N, int d, int kern, double sigma,
+                             cudaStream_t s, PointsFF &P);
+
+// Y (float64) = (A + lambda I) V (float64) with float64-accurate kernel
+// entries computed in float-float arithmetic on the float32 pipes.
+krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv, int m,
+                  double *Y, int64_t ldy, cudaStream_t s, DevBuf<double> &part,
+                  DevBuf<float> &vsplit);
+
 // Y (m x ldy, float32) = (A + lambda I) V (m x ldv, float32).
 krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv,
                    int m, float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "kmv_kernels.cuh"
+#include "kmvff_kernels.cuh"
 
 namespace krr {
 
@@ -93,10 +94,54 @@ cudaError_t launch_kmv64(int DP, int M, dim3 grid, cudaStream_t s, const Kmv64Ar
   }
 }
 
-// Per-kernel entry points, defined in kmv_{gauss,laplace,matern}.cu.
+struct KmvFFArgs {
+  const float *xh, *xl, *ch, *cl, *Vh, *Vl;
+  int64_t N;
+  int m;
+  int64_t chunk;
+  ExpFFConsts ec;
+  double *part;
+};
+
+template <int KERN, int DP>
+cudaError_t launch_kmvff_m(int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a) {
+  switch (M) {
+#define KRR_CASE(MM)                                                                 \
+  case MM:                                                                           \
+    kmvff_kernel<KERN, DP, MM><<<grid, KFF_THREADS, 0, s>>>(a.xh, a.xl, a.ch, a.cl, a.Vh, \
+                                                            a.Vl, a.N, a.m, a.chunk,    \
+                                                            a.ec, a.part);              \
+    break;
+    KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
+#undef KRR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KERN>
+cudaError_t launch_kmvff(int DP, int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a) {
+  switch (DP) {
+    case 4: return launch_kmvff_m<KERN, 4>(M, grid, s, a);
+    case 8: return launch_kmvff_m<KERN, 8>(M, grid, s, a);
+    case 12: return launch_kmvff_m<KERN, 12>(M, grid, s, a);
+    case 16: return launch_kmvff_m<KERN, 16>(M, grid, s, a);
+    case 20: return launch_kmvff_m<KERN, 20>(M, grid, s, a);
+    case 24: return launch_kmvff_m<KERN, 24>(M, grid, s, a);
+    case 28: return launch_kmvff_m<KERN, 28>(M, grid, s, a);
+    case 32: return launch_kmvff_m<KERN, 32>(M, grid, s, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Per-kernel entry points, defined in kmv_{gauss,laplace,matern}.cu and
+// kmvff_{gauss,laplace,matern}.cu.
 cudaError_t launch_kmv32_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
                              const Kmv32Args &a);
 cudaError_t launch_kmv64_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
                              const Kmv64Args &a);
+cudaError_t launch_kmvff_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
+                             const KmvFFArgs &a);
 
 }  // namespace krr

@@ -1,0 +1,274 @@
+// Float64-accurate fused product on the float32 pipes ("double-float").
+//
+// The mixed-precision refinement needs its residual y - (A + lambda I)x with
+// kernel entries accurate far beyond float32, but this part's float64 pipe
+// runs at 1/73 of its float32 rate.  Here every value is an unevaluated sum
+// hi + lo of two floats (about 48 significant bits) and all arithmetic uses
+// error-free transformations: TwoSum (Knuth), TwoProd by FMA (Dekker's
+// product with a fused multiply-add), and renormalisation by FastTwoSum.
+// Intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) keep the compiler from
+// contracting or reassociating them.
+//
+// Per entry (i, j):
+//   distance   from direct coordinate differences of pre-scaled points split
+//              as x = xh + xl: xh_i - xh_j exactly by TwoSum, squares exactly
+//              by TwoProd, the sum compensated by TwoSum (Gaussian, Matern:
+//              S = |x_i - x_j|^2; Laplace: S = sum |x_i - x_j|).  Direct
+//              differences keep every intermediate the size of S, so the
+//              exponent is accurate to ~2^-48 S rather than 2^-48 |x|^2 (the
+//              norm expansion the float32 product uses loses that for near
+//              points).
+//   exp        arg -> k = round(arg 32 / ln 2), r = arg - k ln2/32 (Cody-Waite
+//              with a three-float ln2/32), exp(r) = 1 + r + r^2/2 + r^3 p(r)
+//              (Taylor; the cubic tail in float is below 2^-46 for
+//              |r| <= ln2/64), times the table value 2^(j/32) (hi + lo floats
+//              computed on the host) and 2^(k div 32).
+//   accumulate  acc_c += kappa v_jc with TwoProd + TwoSum per right-hand side.
+// Partial sums are written as float64 and reduced with lambda V in float64.
+#pragma once
+
+#include "common.cuh"
+
+namespace krr {
+
+struct FF {
+  float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.h, b.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  FF p = two_prod(a.h, b.h);
+  p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+  return fast_two_sum(p.h, p.l);
+}
+
+// Constants of the exponential (filled on the host, see kmv_ff.cu):
+//   c[0] = 32 / ln 2 (float), c[1..3] = ln2/32 split into three floats with
+//   c[1] carrying 8 significant bits (so k c[1] is exact for |k| < 2^16),
+//   tab[2 j], tab[2 j + 1] = hi, lo of 2^(j/32).
+struct ExpFFConsts {
+  float c[4];
+  float tab[64];
+};
+
+// exp(a) for a = a.h + a.l <= 0 (tiny positive values from rounding are fine).
+__device__ __forceinline__ FF exp_ff(FF a, const float *__restrict__ cst,
+                                     const float *__restrict__ tab) {
+  if (a.h < -87.0f) return {0.0f, 0.0f};
+  const float kf = rintf(__fmul_rn(a.h, cst[0]));
+  const int k = (int)kf;
+  // r = a - k ln2/32
+  const float t1 = __fmaf_rn(-kf, cst[1], a.h);           // exact (Sterbenz / few bits)
+  FF kc2 = two_prod(kf, cst[2]);
+  FF r = two_sum(t1, -kc2.h);
+  r.l = __fadd_rn(r.l, __fadd_rn(__fsub_rn(a.l, kc2.l), -__fmul_rn(kf, cst[3])));
+  r = fast_two_sum(r.h, r.l);
+  // exp(r) - 1 = r + r^2/2 + r^3 (1/6 + r/24 + r^2/120 + r^3/720)
+  const float rh = r.h;
+  float q = __fmaf_rn(rh, 1.0f / 720.0f, 1.0f / 120.0f);
+  q = __fmaf_rn(rh, q, 1.0f / 24.0f);
+  q = __fmaf_rn(rh, q, 1.0f / 6.0f);
+  q = __fmul_rn(q, __fmul_rn(rh, __fmul_rn(rh, rh)));
+  FF r2 = two_prod(rh, rh);
+  r2.l = __fmaf_rn(2.0f * rh, r.l, r2.l);
+  r2.h *= 0.5f;
+  r2.l *= 0.5f;
+  FF em1 = ff_add(r, r2);
+  em1.l = __fadd_rn(em1.l, q);
+  // kappa = T_j (1 + em1) = T_j + T_j em1
+  const int j = k & 31;
+  const int n = (k - j) / 32;  // exact: k - j is a multiple of 32
+  const FF T = {tab[2 * j], tab[2 * j + 1]};
+  FF v = ff_add(T, ff_mul(T, em1));
+  if (n < -125) {
+    const float s1 = __int_as_float((n + 64 + 127) << 23);   // 2^(n + 64)
+    const float s2 = __int_as_float((127 - 64) << 23);        // 2^-64
+    v.h = __fmul_rn(__fmul_rn(v.h, s1), s2);
+    v.l = __fmul_rn(__fmul_rn(v.l, s1), s2);
+  } else {
+    const float sc = __int_as_float((n + 127) << 23);
+    v.h = __fmul_rn(v.h, sc);
+    v.l = __fmul_rn(v.l, sc);
+  }
+  return v;
+}
+
+// ff square root of a positive ff value (one Newton correction).
+__device__ __forceinline__ FF sqrt_ff(FF a) {
+  if (!(a.h > 0.0f)) return {0.0f, 0.0f};
+  const float s = __fsqrt_rn(a.h);
+  const FF ss = two_prod(s, s);
+  const float corr = __fdiv_rn(__fadd_rn(__fsub_rn(a.h, ss.h), __fsub_rn(a.l, ss.l)),
+                               __fmul_rn(2.0f, s));
+  return fast_two_sum(s, corr);
+}
+
+constexpr int KFF_THREADS = 128;
+constexpr int KFF_TJ = 32;                // columns per shared tile
+
+// Rows per thread: two independent compensated chains while the split points
+// fit the register budget, one otherwise.
+__host__ __device__ constexpr int kmvff_rows_per_thread(int DP) { return DP <= 16 ? 2 : 1; }
+
+// xh, xl : N x DP  split prepared points; ch, cl: N split constants (not
+// used by the direct-difference distance).  Vh, Vl: m x N split RHS.
+// part: splits x M x N float64.
+template <int KERN, int DP, int M>
+__global__ void __launch_bounds__(KFF_THREADS, 4)
+kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
+             const float *__restrict__ ch, const float *__restrict__ cl,
+             const float *__restrict__ Vh, const float *__restrict__ Vl, int64_t N, int m,
+             int64_t chunk, ExpFFConsts ec, double *__restrict__ part) {
+  __shared__ float sxh[KFF_TJ][DP], sxl[KFF_TJ][DP];
+  __shared__ float sch[KFF_TJ], scl[KFF_TJ];
+  __shared__ float svh[KFF_TJ][M], svl[KFF_TJ][M];
+  __shared__ float s_cst[4], s_tab[64];
+  const int tid = threadIdx.x;
+  if (tid < 4) s_cst[tid] = ec.c[tid];
+  if (tid < 64) s_tab[tid] = ec.tab[tid];
+  constexpr int KFF_RI = kmvff_rows_per_thread(DP);
+  const int64_t row0 = (int64_t)blockIdx.x * KFF_THREADS * KFF_RI;
+  const int64_t j_begin = (int64_t)blockIdx.y * chunk;
+  const int64_t j_end = min(N, j_begin + chunk);
+
+  float ih[KFF_RI][DP], il[KFF_RI][DP];
+  FF ic[KFF_RI];
+  FF acc[KFF_RI][M];
+#pragma unroll
+  for (int r = 0; r < KFF_RI; ++r) {
+    const int64_t i = row0 + tid + (int64_t)r * KFF_THREADS;
+    const bool ok = i < N;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      ih[r][k] = ok ? xh[i * DP + k] : 0.0f;
+      il[r][k] = ok ? xl[i * DP + k] : 0.0f;
+    }
+    ic[r] = {ok ? ch[i] : 0.0f, ok ? cl[i] : 0.0f};
+#pragma unroll
+    for (int c = 0; c < M; ++c) acc[r][c] = {0.0f, 0.0f};
+  }
+
+  for (int64_t j0 = j_begin; j0 < j_end; j0 += KFF_TJ) {
+    __syncthreads();
+    for (int idx = tid; idx < KFF_TJ * DP; idx += KFF_THREADS) {
+      const int jj = idx / DP, k = idx % DP;
+      const int64_t j = j0 + jj;
+      const bool ok = j < j_end;
+      sxh[jj][k] = ok ? xh[j * DP + k] : 0.0f;
+      sxl[jj][k] = ok ? xl[j * DP + k] : 0.0f;
+    }
+    for (int idx = tid; idx < KFF_TJ * M; idx += KFF_THREADS) {
+      const int c = idx / KFF_TJ, jj = idx % KFF_TJ;
+      const int64_t j = j0 + jj;
+      const bool ok = (j < j_end) && (c < m);
+      svh[jj][c] = ok ? Vh[(int64_t)c * N + j] : 0.0f;
+      svl[jj][c] = ok ? Vl[(int64_t)c * N + j] : 0.0f;
+    }
+    if (tid < KFF_TJ) {
+      const int64_t j = j0 + tid;
+      const bool ok = j < j_end;
+      sch[tid] = ok ? ch[j] : 0.0f;
+      scl[tid] = ok ? cl[j] : 0.0f;
+    }
+    __syncthreads();
+    const int jn = (int)min((int64_t)KFF_TJ, j_end - j0);
+#pragma unroll 1
+    for (int jj = 0; jj < jn; ++jj) {
+#pragma unroll
+      for (int r = 0; r < KFF_RI; ++r) {
+        FF arg;
+        if constexpr (KERN == KLAPLACE) {
+          FF s = {0.0f, 0.0f};
+          float lo = 0.0f;
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            FF dd = two_sum(ih[r][k], -sxh[jj][k]);
+            dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
+            if (dd.h < 0.0f) {
+              dd.h = -dd.h;
+              dd.l = -dd.l;
+            }
+            const FF t = two_sum(s.h, dd.h);
+            s.h = t.h;
+            lo = __fadd_rn(lo, __fadd_rn(t.l, dd.l));
+          }
+          s = fast_two_sum(s.h, __fadd_rn(s.l, lo));
+          arg = {-s.h, -s.l};
+        } else {
+          // S = sum_k (x_ik - x_jk)^2 with exact differences (TwoSum) and
+          // exact squares (TwoProd): intermediates stay the size of S.
+          FF s = {0.0f, 0.0f};
+          float lo = 0.0f;
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            FF dd = two_sum(ih[r][k], -sxh[jj][k]);
+            dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
+            const FF p = two_prod(dd.h, dd.h);
+            const float cross = __fmaf_rn(__fadd_rn(dd.h, dd.h), dd.l, p.l);
+            const FF t = two_sum(s.h, p.h);
+            s.h = t.h;
+            lo = __fadd_rn(lo, __fadd_rn(t.l, cross));
+          }
+          s = fast_two_sum(s.h, lo);
+          if constexpr (KERN == KMATERN) {
+            // q = sqrt(S);  kappa = (1 + q + q^2/3) exp(-q)
+            const FF q = sqrt_ff(s);
+            arg = {-q.h, -q.l};
+          } else {
+            arg = {-0.5f * s.h, -0.5f * s.l};  // Gaussian: -|x - y|^2 / (2 sigma^2)
+          }
+        }
+        FF kv = exp_ff(arg, s_cst, s_tab);
+        if constexpr (KERN == KMATERN) {
+          const FF q = {-arg.h, -arg.l};
+          FF q2 = ff_mul(q, q);
+          const FF third = {0.3333333433f, -9.9341077e-09f};  // 1/3 = hi + lo
+          FF poly = ff_add({1.0f, 0.0f}, ff_add(q, ff_mul(q2, third)));
+          kv = ff_mul(poly, kv);
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          const FF p = two_prod(kv.h, svh[jj][c]);
+          const float cross = __fmaf_rn(kv.h, svl[jj][c], __fmaf_rn(kv.l, svh[jj][c], p.l));
+          const FF t = two_sum(acc[r][c].h, p.h);
+          acc[r][c].h = t.h;
+          acc[r][c].l = __fadd_rn(acc[r][c].l, __fadd_rn(t.l, cross));
+        }
+      }
+    }
+  }
+  double *out = part + (int64_t)blockIdx.y * M * N;
+#pragma unroll
+  for (int r = 0; r < KFF_RI; ++r) {
+    const int64_t i = row0 + tid + (int64_t)r * KFF_THREADS;
+    if (i < N) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        if (c < m) out[(int64_t)c * N + i] = (double)acc[r][c].h + (double)acc[r][c].l;
+    }
+  }
+}
+
+}  // namespace krr

@@ -1,0 +1,10 @@
+// Instantiates the float-float fused product for one kernel function.
+#include "kmv_dispatch.cuh"
+
+namespace krr {
+
+cudaError_t launch_kmvff_matern(int DP, int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a) {
+  return launch_kmvff<KMATERN>(DP, M, grid, s, a);
+}
+
+}  // namespace krr

@@ -85,7 +85,9 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     // iterative refinement: float64 outer loop around a float32 inner PCG
     PointsF32 P;
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
-    DevBuf<float> part32, b32, d32;
+    PointsFF Pff;
+    KRR_TRY(prepare_points_ff(Xd, N, d, kern, sigma, s, Pff));
+    DevBuf<float> part32, b32, d32, vsplit;
     DevBuf<double> part64, mx, r64;
     KRR_TRY(b32.alloc((size_t)N * m, s));
     KRR_TRY(d32.alloc((size_t)N * m, s));
@@ -136,7 +138,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
       budget -= st.iters_max;
       entries += kmv_entries(N) * st.products;
       KRR_TRY(add_f32_to_f64(alpha, d32.p, N * m, s));
-      KRR_TRY(kmv_f64(Xd, N, d, kern, sigma, lambda, alpha, N, m, mx.p, N, s, part64));
+      KRR_TRY(kmv_ff(Pff, lambda, alpha, N, m, mx.p, N, s, part64, vsplit));
       entries += kmv_entries(N);
       KRR_TRY(residual_f64(Y, mx.p, r64.p, N * m, s));
       KRR_TRY(column_norms(r64.p, N, m, rn.data(), s));

@@ -5,6 +5,9 @@ rtol 1e-12.  float32 path: errors are bounded by the float32 unit roundoff
 times the condition of the sum; each entry must satisfy
 |Y32 - Y| <= 2e-5 (A|V| + lambda|V|) -- the kernel value carries ~1e-6
 relative error from the argument and ex2, the accumulation a few 1e-6.
+float-float path (the refinement residual): about 48-bit entries and sums,
+|Yff - Y| <= 5e-13 (A|V| + lambda|V|) at these sizes (the oracle's own
+sequential float64 sums contribute up to N x 2^-53 of the same scale).
 """
 import numpy as np
 import pytest
@@ -48,6 +51,36 @@ def test_fp32_product(K, kern, N, d, m):
     assert np.all(np.abs(got - ref) <= 2e-5 * bound)
 
 
+@pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,d,m", [(1, 1, 1), (65, 3, 1), (700, 8, 4), (2500, 16, 4),
+                                   (1029, 20, 16), (513, 32, 2), (300, 5, 9)])
+def test_float_float_product(K, kern, N, d, m):
+    rng = np.random.default_rng(N * 13 + d + kern)
+    X = rng.standard_normal((N, d))
+    V = rng.standard_normal((m, N))
+    ref = O.kmatvec(X, kern, 0.9, 0.3, V)
+    bound = f32_product_bound(X, kern, 0.9, 0.3, V)
+    got = K.krr_kmatvec(X, kern, 0.9, 0.3, V, prec="ff")
+    assert np.all(np.abs(got - ref) <= 5e-13 * bound)
+
+
+def test_float_float_near_duplicates_and_far_points(K):
+    """Twins at 1e-7 and a far cluster whose cross entries underflow.  The
+    split x = xh + xl represents each centred, scaled coordinate to about
+    2^-48 |x|, so the exponent error is ~2^-47 |x| |x_i - x_j| per coordinate:
+    float64-level for standardised data (|x| / sigma up to ~20 here)."""
+    rng = np.random.default_rng(3)
+    X = rng.random((800, 16))
+    X[400:] = X[:400] + 1e-7 * rng.standard_normal((400, 16))
+    X[:50] += 8.0
+    V = rng.standard_normal((2, 800))
+    for kern in KERNS:
+        ref = O.kmatvec(X, kern, 0.5, 0.01, V)
+        bound = f32_product_bound(X, kern, 0.5, 0.01, V)
+        got = K.krr_kmatvec(X, kern, 0.5, 0.01, V, prec="ff")
+        assert np.all(np.abs(got - ref) <= 5e-13 * bound), kern
+
+
 def test_device_and_host_pointers_agree(K):
     w = make_c1_plain_fp64(n=777)
     V = np.random.default_rng(0).standard_normal((2, w.N))
@@ -64,7 +97,7 @@ def test_deterministic(K):
     np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_full_size_sampled_rows(K, prec):
     """The 100000-point, d = 16 ill-conditioned workload with 4 right-hand
     sides: GPU product on all rows, oracle on 48 sampled rows."""
@@ -77,6 +110,9 @@ def test_full_size_sampled_rows(K, prec):
     ref = O.kmatvec(w.X, w.kernel, w.sigma, w.lam, V, rows)
     if prec == "fp64":
         np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    elif prec == "ff":
+        bound = f32_product_bound(w.X, w.kernel, w.sigma, w.lam, V, rows)
+        assert np.all(np.abs(got - ref) <= 2e-12 * bound)
     else:
         bound = f32_product_bound(w.X, w.kernel, w.sigma, w.lam, V, rows)
         assert np.all(np.abs(got - ref) <= 2e-5 * bound)
