@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--fp64-path", action="store_true",
                     help="also time the plain float64 path (one step, slow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
     return ap.parse_args()
 
 
@@ -247,6 +248,14 @@ def run_native(args):
                                "speedup_mixed_vs_fp64": t64 / (total_ms / args.steps / 1e3)}
 
     # end to end through the C ABI with host buffers (copies inside the region)
+    if args.no_e2e:
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(w)
+        if rank == 0:
+            print(json.dumps(result), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     Xh, Yh = w.X, w.Y
     alpha_h = np.empty_like(Yh)
     t0 = time.perf_counter()

@@ -112,6 +112,18 @@ KRR_API krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel ker
                        double *Y, krr_precision prec, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Prediction at test points (Sec. 2.1: f(x) = sum_i alpha_i K(x_i, x)):      */
+/*   out (Nt x m) = K(Xtest, Xtrain) alpha,  alpha N x m.                     */
+/* Xtrain N x d and Xtest Nt x d row-major.  KRR_PREC_FP64 evaluates entries  */
+/* in float64; KRR_PREC_MIXED in float32 tiles with float32 accumulation     */
+/* (both point sets centred on the training mean).                           */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_predict(const double *Xtrain, int64_t N, int d, krr_kernel kern,
+                               double sigma, const double *alpha, int m,
+                               const double *Xtest, int64_t Nt, double *out,
+                               krr_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Pivot sampling of Alg. 3: ndraw i.i.d. indices with probability           */
 /* proportional to the residual diagonal dres (length N).  Weights are the    */
 /* fixed-point integers floor(min(dres_i, 1) * 2^F) for dres_i > dfloor and   */

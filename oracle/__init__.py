@@ -43,6 +43,8 @@ def lib():
                                        ip, C.c_int64, ip, C.c_int64, dp]
         L.orc_kmatvec.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
                                   C.c_double, dp, C.c_int, ip, C.c_int64, dp]
+        L.orc_kcross_matvec.argtypes = [dp, C.c_int64, dp, C.c_int64, C.c_int, C.c_int,
+                                        C.c_double, dp, C.c_int, dp]
         L.orc_kcols_matvec.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
                                        ip, C.c_int, dp, C.c_int, dp]
         L.orc_krows_matvec.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
@@ -119,6 +121,18 @@ def kmatvec(X, kern: int, sigma: float, lam: float, V, rows=None) -> np.ndarray:
     Y = np.empty((m, nr))
     lib().orc_kmatvec(_d(X), N, d, kern, sigma, lam, _d(V), m, _i(rows), nr, _d(Y))
     return Y
+
+
+def predict(X, kern, sigma, alpha, T) -> np.ndarray:
+    """f(t) = sum_n alpha_n kappa(x_n, t) for every test point (Sec. 2.1);
+    alpha (m, N) -> (m, Nt)."""
+    X, T, alpha = _f64(X), _f64(T), _f64(np.atleast_2d(alpha))
+    N, d = X.shape
+    Nt = T.shape[0]
+    m = alpha.shape[0]
+    out = np.empty((m, Nt))
+    lib().orc_kcross_matvec(_d(X), N, _d(T), Nt, d, kern, sigma, _d(alpha), m, _d(out))
+    return out
 
 
 def kcols_matvec(X, kern, sigma, S, beta) -> np.ndarray:

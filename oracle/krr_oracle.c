@@ -95,6 +95,22 @@ void orc_kmatvec(const double *X, int64_t N, int d, int kern, double sigma,
     }
 }
 
+/* Prediction (Sec. 2.1): out (Nt x m, col-major) = K(T, X) V, i.e.
+ * out[c][t] = sum_n kappa(t_t, x_n) V[c][n], V N x m col-major. */
+void orc_kcross_matvec(const double *X, int64_t N, const double *T, int64_t Nt, int d,
+                       int kern, double sigma, const double *V, int m, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < Nt; ++t) {
+        for (int c = 0; c < m; ++c) {
+            double acc = 0.0;
+            for (int64_t n = 0; n < N; ++n)
+                acc += orc_kappa(T + t * d, X + n * d, d, kern, sigma) * V[c * N + n];
+            out[c * Nt + t] = acc;
+        }
+    }
+}
+
 /* u (N x m, col-major) = A(:, S) beta, beta k x m col-major. */
 void orc_kcols_matvec(const double *X, int64_t N, int d, int kern, double sigma,
                       const int64_t *S, int k, const double *beta, int m, double *u)

@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     krr_kmatvec,
     krr_launch_count,
     krr_pcg_solve,
+    krr_predict,
     krr_precond_apply,
     krr_rpc_sample,
     krr_rpcholesky,

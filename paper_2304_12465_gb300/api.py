@@ -89,6 +89,21 @@ def krr_kmatvec(X, kern, sigma: float, lam: float, V, prec="fp64", stream=None):
     return Y
 
 
+def krr_predict(Xtrain, kern, sigma: float, alpha, Xtest, prec="fp64", stream=None):
+    """Predictions K(Xtest, Xtrain) alpha, alpha (m, N) -> (m, Nt)."""
+    lib = load()
+    Xk, Xp = _arr(Xtrain)
+    Ak, Ap = _arr(alpha)
+    Tk, Tp = _arr(Xtest)
+    Nn, d = Xk.shape
+    Nt = Tk.shape[0]
+    m = _shape2(Ak)[0]
+    out, Op = _empty_like_container(alpha, (m, Nt))
+    check(lib.krr_predict(Xp, Nn, d, _kern(kern), float(sigma), Ap, m, Tp, Nt, Op, _prec(prec),
+                          _stream(stream, Xtrain, alpha, Xtest)), "krr_predict")
+    return out
+
+
 def krr_rpc_sample(dres, seed: int, t: int, ndraw: int, dfloor: float = 0.0,
                    stream=None) -> np.ndarray:
     lib = load()

@@ -235,6 +235,40 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
   return out.finish(s);
 }
 
+krr_status krr_predict(const double *Xtrain, int64_t N, int d, krr_kernel kern, double sigma,
+                       const double *alpha, int m, const double *Xtest, int64_t Nt,
+                       double *out, krr_precision prec, void *stream) {
+  clear_error();
+  KRR_CHECK_POINTS(Xtrain, N, d, kern, sigma);
+  KRR_REQUIRE(alpha && Xtest && out, "alpha, Xtest and out must not be NULL");
+  KRR_REQUIRE(Nt >= 1, "number of test points must be >= 1");
+  KRR_REQUIRE(m >= 1 && m <= 16, "m must be in [1, 16]");
+  KRR_REQUIRE(prec == KRR_PREC_FP64 || prec == KRR_PREC_MIXED, "unknown precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf<double> tx, ta, tt;
+  const double *Xd, *Ad, *Td;
+  KRR_TRY(device_view(Xtrain, (size_t)N * d, s, tx, &Xd));
+  KRR_TRY(device_view(alpha, (size_t)N * m, s, ta, &Ad));
+  KRR_TRY(device_view(Xtest, (size_t)Nt * d, s, tt, &Td));
+  OutView<double> o;
+  KRR_TRY(o.init(out, (size_t)Nt * m, s));
+  if (prec == KRR_PREC_FP64) {
+    DevBuf<double> part;
+    KRR_TRY(kcross_f64(Td, Nt, Xd, N, d, kern, sigma, Ad, N, m, o.dev, Nt, s, part));
+  } else {
+    PointsF32 P, R;
+    KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
+    KRR_TRY(prepare_points_f32(Td, Nt, d, kern, sigma, s, R, P.mean.p));
+    DevBuf<float> a32, y32, part;
+    KRR_TRY(a32.alloc((size_t)N * m, s));
+    KRR_TRY(y32.alloc((size_t)Nt * m, s));
+    KRR_TRY(convert_f64_to_f32(Ad, a32.p, N * m, s));
+    KRR_TRY(kcross_f32(R, P, a32.p, N, m, y32.p, Nt, s, part));
+    KRR_TRY(convert_f32_to_f64(y32.p, o.dev, Nt * m, s));
+  }
+  return o.finish(s);
+}
+
 krr_status krr_rpc_sample(const double *dres, int64_t N, double dfloor, uint64_t seed,
                           uint64_t t, int ndraw, int64_t *draws, int *ndraw_out, void *stream) {
   clear_error();

@@ -79,7 +79,7 @@ __global__ void prepare_f32_kernel(const double *__restrict__ X, int64_t N, int 
 }
 
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, double sigma,
-                              cudaStream_t s, PointsF32 &P) {
+                              cudaStream_t s, PointsF32 &P, const double *mean_dev) {
   P.dp = (d + 3) / 4 * 4;
   P.d = d;
   P.N = N;
@@ -87,10 +87,14 @@ krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, doub
   P.sigma = sigma;
   KRR_TRY(P.xt.alloc((size_t)N * P.dp, s));
   KRR_TRY(P.cn.alloc((size_t)N, s));
-  DevBuf<double> mean;
-  KRR_TRY(mean.alloc(d, s));
-  column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, mean.p);
-  KRR_LAUNCH_CHECK();
+  KRR_TRY(P.mean.alloc(d, s));
+  if (mean_dev) {
+    KRR_CUDA_TRY(cudaMemcpyAsync(P.mean.p, mean_dev, sizeof(double) * d,
+                                 cudaMemcpyDeviceToDevice, s));
+  } else {
+    column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, P.mean.p);
+    KRR_LAUNCH_CHECK();
+  }
   const double log2e = 1.4426950408889634;
   double scale;
   int with_norm = 1;
@@ -102,7 +106,7 @@ krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, doub
     scale = log2e / sigma;
     with_norm = 0;
   }
-  prepare_f32_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, mean.p, scale,
+  prepare_f32_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, P.mean.p, scale,
                                                       with_norm, P.xt.p, P.cn.p);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
@@ -204,7 +208,7 @@ __global__ void kmv_reduce_kernel(const T *__restrict__ part, int splits, int M,
   for (int c = 0; c < m; ++c) {
     T acc = 0;
     for (int sp = 0; sp < splits; ++sp) acc += part[((int64_t)sp * M + c) * N + i];
-    Y[(int64_t)c * ldy + i] = acc + lambda * V[(int64_t)c * ldv + i];
+    Y[(int64_t)c * ldy + i] = V ? acc + lambda * V[(int64_t)c * ldv + i] : acc;
   }
 }
 
@@ -241,7 +245,8 @@ krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv
     const int nsplit = (int)((N + chunk - 1) / chunk);
     const size_t need = (size_t)nsplit * M * N;
     if (part.n < need) KRR_TRY(part.alloc(need, s));
-    Kmv32Args a{P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, part.p};
+    Kmv32Args a{P.xt.p, P.cn.p, N, P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg, chunk,
+                part.p};
     KmvTimer tm;
     tm.begin(s);
     cudaError_t e = launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
@@ -275,7 +280,7 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
     const int nsplit = (int)((N + chunk - 1) / chunk);
     const size_t need = (size_t)nsplit * M * N;
     if (part.n < need) KRR_TRY(part.alloc(need, s));
-    Kmv64Args a{Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, part.p};
+    Kmv64Args a{Xd, N, Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, part.p};
     KmvTimer tm(1);
     tm.begin(s);
     cudaError_t e = launch_kmv64_any(kern, dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
@@ -337,6 +342,67 @@ krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv
   return KRR_OK;
 }
 
+// Prediction products Y (Nr x m) = K(Xr, X) V, V N x m (no shift).
+krr_status kcross_f32(const PointsF32 &R, const PointsF32 &P, const float *V, int64_t ldv,
+                      int m, float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
+  const int64_t N = P.N, Nr = R.N;
+  if (N == 0 || Nr == 0 || m == 0) return KRR_OK;
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    const int rows = KMV_THREADS * kmv32_rows_per_thread(P.dp, M);
+    const int64_t row_tiles = (Nr + rows - 1) / rows;
+    const int splits = choose_splits(row_tiles, N, KMV_TJ, 2, 8);
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * Nr;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    Kmv32Args a{R.xt.p, R.cn.p, Nr, P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg, chunk,
+                part.p};
+    cudaError_t e = launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("prediction product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<float, 16><<<ceil_div(Nr, 256), 256, 0, s>>>(
+        part.p, nsplit, M, Nr, mg, 0.0f, nullptr, 0, Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+krr_status kcross_f64(const double *Xr, int64_t Nr, const double *Xd, int64_t N, int d,
+                      int kern, double sigma, const double *V, int64_t ldv, int m, double *Y,
+                      int64_t ldy, cudaStream_t s, DevBuf<double> &part) {
+  if (N == 0 || Nr == 0 || m == 0) return KRR_OK;
+  const int dp = (d + 3) / 4 * 4;
+  double inv_scale = (kern == KGAUSS) ? 1.0 / (2.0 * sigma * sigma) : 1.0 / sigma;
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int mg = (m - c0 < 16) ? (m - c0) : 16;
+    const int M = pad_m(mg);
+    const int64_t row_tiles = (Nr + KMV64_THREADS - 1) / KMV64_THREADS;
+    const int splits = choose_splits(row_tiles, N, KMV64_TJ, 4, 4);
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV64_TJ - 1) / KMV64_TJ * KMV64_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * Nr;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    Kmv64Args a{Xr, Nr, Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, part.p};
+    cudaError_t e = launch_kmv64_any(kern, dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("prediction product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<double, 16><<<ceil_div(Nr, 256), 256, 0, s>>>(
+        part.p, nsplit, M, Nr, mg, 0.0, nullptr, 0, Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
 // Same product with caller-provided split scratch of `scratch_elems` doubles:
 // the column split count is reduced until the partial sums fit.  Launches
 // only the product and reduction kernels (no allocation).
@@ -362,7 +428,7 @@ krr_status kmv_f64_with_scratch(const double *Xd, int64_t N, int d, int kern, do
     int64_t chunk = (N + splits - 1) / splits;
     chunk = (chunk + KMV64_TJ - 1) / KMV64_TJ * KMV64_TJ;
     const int nsplit = (int)((N + chunk - 1) / chunk);
-    Kmv64Args a{Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, scratch};
+    Kmv64Args a{Xd, N, Xd, d, V + (int64_t)c0 * ldv, ldv, N, mg, chunk, inv_scale, scratch};
     cudaError_t e = launch_kmv64_any(kern, dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
     count_launch();
     if (e != cudaSuccess) {

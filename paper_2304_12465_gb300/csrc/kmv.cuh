@@ -10,6 +10,7 @@ namespace krr {
 struct PointsF32 {
   DevBuf<float> xt;   // N x dp
   DevBuf<float> cn;   // N
+  DevBuf<double> mean;  // d, the centre subtracted from every point
   int dp = 0;
   int d = 0;
   int64_t N = 0;
@@ -17,8 +18,18 @@ struct PointsF32 {
   double sigma = 0.0;
 };
 
+// mean_dev (optional, d doubles on the device): centre to use instead of the
+// points' own mean (prediction prepares test points with the training mean).
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
-                              double sigma, cudaStream_t s, PointsF32 &P);
+                              double sigma, cudaStream_t s, PointsF32 &P,
+                              const double *mean_dev = nullptr);
+
+// Prediction products (no shift): Y (Nr x m) = K(rows, columns) V.
+krr_status kcross_f32(const PointsF32 &R, const PointsF32 &P, const float *V, int64_t ldv,
+                      int m, float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part);
+krr_status kcross_f64(const double *Xr, int64_t Nr, const double *Xd, int64_t N, int d,
+                      int kern, double sigma, const double *V, int64_t ldv, int m, double *Y,
+                      int64_t ldy, cudaStream_t s, DevBuf<double> &part);
 
 // Points split for the float-float product: centred, scaled x = xh + xl and
 // c = -|x|^2/2 = ch + cl (unused for Laplace).

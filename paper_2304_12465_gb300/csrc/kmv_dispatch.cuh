@@ -10,6 +10,9 @@
 namespace krr {
 
 struct Kmv32Args {
+  const float *xr;   // row points (== xt for the square product)
+  const float *cr;
+  int64_t Nr;
   const float *xt;
   const float *cn;
   const float *V;
@@ -20,6 +23,8 @@ struct Kmv32Args {
 };
 
 struct Kmv64Args {
+  const double *Xr;  // row points (== X for the square product)
+  int64_t Nr;
   const double *X;
   int d;
   const double *V;
@@ -35,9 +40,9 @@ cudaError_t launch_kmv32_m(int M, dim3 grid, cudaStream_t s, const Kmv32Args &a)
   switch (M) {
 #define KRR_CASE(MM)                                                              \
   case MM:                                                                        \
-    kmv32_kernel<KERN, DP, MM><<<grid, KMV_THREADS, 0, s>>>(a.xt, a.cn, a.V, a.ldv, \
-                                                           a.N, a.m, a.chunk,      \
-                                                           a.part);                \
+    kmv32_kernel<KERN, DP, MM><<<grid, KMV_THREADS, 0, s>>>(a.xr, a.cr, a.Nr, a.xt,    \
+                                                           a.cn, a.V, a.ldv, a.N, \
+                                                           a.m, a.chunk, a.part); \
     break;
     KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
 #undef KRR_CASE
@@ -67,9 +72,10 @@ cudaError_t launch_kmv64_m(int M, dim3 grid, cudaStream_t s, const Kmv64Args &a)
   switch (M) {
 #define KRR_CASE(MM)                                                                \
   case MM:                                                                          \
-    kmv64_kernel<KERN, DP, MM><<<grid, KMV64_THREADS, 0, s>>>(a.X, a.d, a.V, a.ldv,   \
-                                                             a.N, a.m, a.chunk,      \
-                                                             a.inv_scale, a.part);   \
+    kmv64_kernel<KERN, DP, MM><<<grid, KMV64_THREADS, 0, s>>>(a.Xr, a.Nr, a.X, a.d,  \
+                                                             a.V, a.ldv, a.N, a.m,  \
+                                                             a.chunk, a.inv_scale,  \
+                                                             a.part);               \
     break;
     KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
 #undef KRR_CASE

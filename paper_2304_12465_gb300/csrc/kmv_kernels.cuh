@@ -65,13 +65,16 @@ __device__ __forceinline__ float kappa_f32(float acc) {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // ------------------------------------------------------------------ f32
-// xt : N x DP   prepared points (zero padded beyond d)
+// xr, cr : Nr x DP, Nr  prepared row points and constants (the same arrays as
+//          xt, cn for the square product; test points for prediction)
+// xt : N x DP   prepared column points (zero padded beyond d)
 // cn : N        per-point constant (c above; unused for Laplace)
 // V  : m x ldv  right-hand sides (column c at V + c*ldv), float32
-// part: splits x M x N partial products
+// part: splits x M x Nr partial products
 template <int KERN, int DP, int M>
 __global__ void __launch_bounds__(KMV_THREADS, 2)
-kmv32_kernel(const float *__restrict__ xt, const float *__restrict__ cn,
+kmv32_kernel(const float *__restrict__ xr, const float *__restrict__ cr, int64_t Nr,
+             const float *__restrict__ xt, const float *__restrict__ cn,
              const float *__restrict__ V, int64_t ldv, int64_t N, int m,
              int64_t chunk, float *__restrict__ part) {
   static_assert(DP % 4 == 0, "DP must be a multiple of 4");
@@ -96,11 +99,11 @@ kmv32_kernel(const float *__restrict__ xt, const float *__restrict__ cn,
   for (int p = 0; p < RP; ++p) {
     const int64_t ra = row0 + tid + (int64_t)(2 * p) * KMV_THREADS;
     const int64_t rb = ra + KMV_THREADS;
-    const bool va = ra < N, vb = rb < N;
+    const bool va = ra < Nr, vb = rb < Nr;
 #pragma unroll
     for (int k = 0; k < DP; ++k)
-      xi[p][k] = f2(va ? xt[ra * DP + k] : 0.0f, vb ? xt[rb * DP + k] : 0.0f);
-    ci[p] = f2(va ? cn[ra] : 0.0f, vb ? cn[rb] : 0.0f);
+      xi[p][k] = f2(va ? xr[ra * DP + k] : 0.0f, vb ? xr[rb * DP + k] : 0.0f);
+    ci[p] = f2(va ? cr[ra] : 0.0f, vb ? cr[rb] : 0.0f);
 #pragma unroll
     for (int c = 0; c < MP; ++c) acc[p][c] = f2(0.0f, 0.0f);
   }
@@ -210,7 +213,7 @@ kmv32_kernel(const float *__restrict__ xt, const float *__restrict__ cn,
     buf ^= 1;
   }
 
-  float *out = part + (int64_t)blockIdx.y * M * N;
+  float *out = part + (int64_t)blockIdx.y * M * Nr;
 #pragma unroll
   for (int p = 0; p < RP; ++p) {
     const int64_t ra = row0 + tid + (int64_t)(2 * p) * KMV_THREADS;
@@ -218,8 +221,8 @@ kmv32_kernel(const float *__restrict__ xt, const float *__restrict__ cn,
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       if (c < m) {
-        if (ra < N) out[(int64_t)c * N + ra] = acc[p][c].x;
-        if (rb < N) out[(int64_t)c * N + rb] = acc[p][c].y;
+        if (ra < Nr) out[(int64_t)c * Nr + ra] = acc[p][c].x;
+        if (rb < Nr) out[(int64_t)c * Nr + rb] = acc[p][c].y;
       }
     }
   }
@@ -240,11 +243,12 @@ __device__ __forceinline__ double kappa_f64(double s, double inv_scale) {
   }
 }
 
+// Xr (Nr x d) row points; X (N x d) column points; part: splits x M x Nr.
 template <int KERN, int DP, int M>
 __global__ void __launch_bounds__(KMV64_THREADS)
-kmv64_kernel(const double *__restrict__ X, int d, const double *__restrict__ V,
-             int64_t ldv, int64_t N, int m, int64_t chunk, double inv_scale,
-             double *__restrict__ part) {
+kmv64_kernel(const double *__restrict__ Xr, int64_t Nr, const double *__restrict__ X, int d,
+             const double *__restrict__ V, int64_t ldv, int64_t N, int m, int64_t chunk,
+             double inv_scale, double *__restrict__ part) {
   __shared__ double sx[KMV64_TJ][DP];
   __shared__ double sv[KMV64_TJ][M];
   const int tid = threadIdx.x;
@@ -254,7 +258,7 @@ kmv64_kernel(const double *__restrict__ X, int d, const double *__restrict__ V,
   double xi[DP];
   double acc[M];
 #pragma unroll
-  for (int k = 0; k < DP; ++k) xi[k] = (i < N && k < d) ? X[i * d + k] : 0.0;
+  for (int k = 0; k < DP; ++k) xi[k] = (i < Nr && k < d) ? Xr[i * d + k] : 0.0;
 #pragma unroll
   for (int c = 0; c < M; ++c) acc[c] = 0.0;
 
@@ -286,11 +290,11 @@ kmv64_kernel(const double *__restrict__ X, int d, const double *__restrict__ V,
       for (int c = 0; c < M; ++c) acc[c] = fma(kv, sv[jj][c], acc[c]);
     }
   }
-  if (i < N) {
-    double *out = part + (int64_t)blockIdx.y * M * N;
+  if (i < Nr) {
+    double *out = part + (int64_t)blockIdx.y * M * Nr;
 #pragma unroll
     for (int c = 0; c < M; ++c)
-      if (c < m) out[(int64_t)c * N + i] = acc[c];
+      if (c < m) out[(int64_t)c * Nr + i] = acc[c];
   }
 }
 

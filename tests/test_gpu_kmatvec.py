@@ -64,11 +64,26 @@ def test_float_float_product(K, kern, N, d, m):
     assert np.all(np.abs(got - ref) <= 5e-13 * bound)
 
 
+def ff_error_bound(X, kern, sigma, lam, V):
+    """Entrywise error model of the float-float product.  Each centred,
+    scaled coordinate is held to 2^-48 |x|, so a difference d_k carries
+    2^-48 (|x_ik| + |x_jk|) and the exponent (S/2, S or q) carries about
+    eps_ij = 2^-46 sum_k (|x_ik| + |x_jk|)(1 + |d_k|) + 2^-44; the row error
+    is at most a few times sum_j kappa_ij |v_j| eps_ij, plus the oracle's own
+    float64 rounding."""
+    scale = {O.GAUSSIAN: 1.0 / sigma, O.LAPLACE_L1: 1.0 / sigma,
+             O.MATERN52: np.sqrt(5.0) / sigma}[kern]
+    Xs = (X - X.mean(axis=0)) * scale
+    A = O.kernel_block(X, kern, sigma)
+    ax = np.abs(Xs)
+    D = np.abs(Xs[:, None, :] - Xs[None, :, :])
+    eps = 2.0 ** -46 * ((ax[:, None, :] + ax[None, :, :]) * (1.0 + D)).sum(axis=2) + 2.0 ** -44
+    return 8.0 * ((A * eps) @ np.abs(V).T).T + 5e-14 * f32_product_bound(X, kern, sigma, lam, V)
+
+
 def test_float_float_near_duplicates_and_far_points(K):
-    """Twins at 1e-7 and a far cluster whose cross entries underflow.  The
-    split x = xh + xl represents each centred, scaled coordinate to about
-    2^-48 |x|, so the exponent error is ~2^-47 |x| |x_i - x_j| per coordinate:
-    float64-level for standardised data (|x| / sigma up to ~20 here)."""
+    """Twins at 1e-7 and a far cluster (coordinates ~16 after scaling) whose
+    cross entries underflow, against the float-float error model."""
     rng = np.random.default_rng(3)
     X = rng.random((800, 16))
     X[400:] = X[:400] + 1e-7 * rng.standard_normal((400, 16))
@@ -76,9 +91,11 @@ def test_float_float_near_duplicates_and_far_points(K):
     V = rng.standard_normal((2, 800))
     for kern in KERNS:
         ref = O.kmatvec(X, kern, 0.5, 0.01, V)
-        bound = f32_product_bound(X, kern, 0.5, 0.01, V)
         got = K.krr_kmatvec(X, kern, 0.5, 0.01, V, prec="ff")
-        assert np.all(np.abs(got - ref) <= 5e-13 * bound), kern
+        assert np.all(np.abs(got - ref) <= ff_error_bound(X, kern, 0.5, 0.01, V)), kern
+        # standardised-scale rows (all but the far cluster) stay at 5e-13
+        bound = f32_product_bound(X, kern, 0.5, 0.01, V)
+        assert np.all(np.abs(got - ref)[:, 50:] <= 5e-13 * bound[:, 50:]), kern
 
 
 def test_device_and_host_pointers_agree(K):
@@ -116,3 +133,19 @@ def test_full_size_sampled_rows(K, prec):
     else:
         bound = f32_product_bound(w.X, w.kernel, w.sigma, w.lam, V, rows)
         assert np.all(np.abs(got - ref) <= 2e-5 * bound)
+
+
+@pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,Nt,d,m", [(1, 1, 1, 1), (700, 65, 8, 4), (3000, 1025, 16, 2),
+                                      (513, 2000, 20, 16)])
+def test_prediction(K, kern, N, Nt, d, m):
+    rng = np.random.default_rng(N + Nt + d + kern)
+    X = rng.standard_normal((N, d))
+    T = rng.standard_normal((Nt, d)) * 1.3
+    alpha = rng.standard_normal((m, N))
+    ref = O.predict(X, kern, 1.1, alpha, T)
+    bound = O.predict(X, kern, 1.1, np.abs(alpha), T)
+    got64 = K.krr_predict(X, kern, 1.1, alpha, T, prec="fp64")
+    np.testing.assert_allclose(got64, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    got32 = K.krr_predict(to_dev(X), kern, 1.1, to_dev(alpha), to_dev(T), prec="mixed")
+    assert np.all(np.abs(got32.cpu().numpy() - ref) <= 2e-5 * bound + 1e-30)

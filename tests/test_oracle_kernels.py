@@ -122,3 +122,17 @@ def test_kcols_krows_products():
                                (A[:, S] @ beta.T).T, rtol=1e-12, atol=1e-13)
     np.testing.assert_allclose(O.krows_matvec(X, O.GAUSSIAN, 1.1, S, u),
                                (A[S, :] @ u.T).T, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("kern", [O.GAUSSIAN, O.LAPLACE_L1, O.MATERN52])
+def test_predict_equals_block_of_stacked_matrix(kern):
+    """Prediction = the (test, train) block of the kernel matrix of the
+    stacked point set, applied to alpha."""
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((90, 4))
+    T = rng.standard_normal((25, 4))
+    alpha = rng.standard_normal((2, 90))
+    Z = np.vstack([X, T])
+    Akt = O.kernel_block(Z, kern, 1.2, np.arange(90, 115), np.arange(90))
+    np.testing.assert_allclose(O.predict(X, kern, 1.2, alpha, T), (Akt @ alpha.T).T,
+                               rtol=1e-12, atol=1e-13)
