@@ -112,6 +112,24 @@ KRR_API krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel ker
                        double *Y, krr_precision prec, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched fused product over several hyperparameter settings sharing one     */
+/* tile generation (the paper applies its solvers across bandwidths and      */
+/* regularisations, Sec. 2.1.2, Sec. 2.2.2, Sec. 5; batching them is this   */
+/* library's design):                                                         */
+/*   Y_{s,c} = (A_s + lambda_{s,c} I) V_{s,c},  s < S, c < ms,                */
+/* A_s the kernel matrix of (kerns[s], sigmas[s]).  V, Y: N x (S ms)          */
+/* column-major, column s*ms + c; lambdas: S*ms.  Per point pair the          */
+/* coordinate differences are formed once (l2 and/or l1 distance), then each  */
+/* setting costs one kernel evaluation.  float32 tiles, float32 accumulation. */
+/* 1 <= S <= KRR_MAX_SETTINGS, ms in {1, 2}.                                  */
+/* ------------------------------------------------------------------------ */
+#define KRR_MAX_SETTINGS 8
+KRR_API krr_status krr_kmatvec_batched(const double *X, int64_t N, int d, int S,
+                                       const int *kerns, const double *sigmas, int ms,
+                                       const double *lambdas, const double *V, double *Y,
+                                       void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Prediction at test points (Sec. 2.1: f(x) = sum_i alpha_i K(x_i, x)):      */
 /*   out (Nt x m) = K(Xtest, Xtrain) alpha,  alpha N x m.                     */
 /* Xtrain N x d and Xtest Nt x d row-major.  KRR_PREC_FP64 evaluates entries  */
@@ -202,6 +220,24 @@ KRR_API krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel k
                          const krr_factor *F, double tol, int maxit,
                          krr_precision prec, double *alpha_out, void *stream,
                          krr_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* Batched RPCholesky-preconditioned CG over S hyperparameter settings x ms   */
+/* regularisations (mixed precision with float64-accurate refinement, as     */
+/* krr_pcg_solve with KRR_PREC_MIXED).  System q*ms + c solves                */
+/*   (A_q + mus[c] N I) alpha = Y(:, q*ms + c),                               */
+/* A_q the kernel matrix of (kerns[q], sigmas[q]), preconditioned by the      */
+/* Alg. 1 preconditioner of factors[q] and mus[c] (factors or factors[q] may  */
+/* be NULL: lambda^{-1} I).  All systems advance together: one batched fused  */
+/* product (krr_kmatvec_batched) per iteration; each column keeps its own CG  */
+/* scalars and stops at its own tolerance.  Y, alpha_out: N x (S ms).        */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_pcg_solve_batched(const double *X, int64_t N, int d, int S,
+                                         const int *kerns, const double *sigmas,
+                                         const krr_factor *const *factors, int ms,
+                                         const double *mus, const double *Y, double tol,
+                                         int maxit, double *alpha_out, void *stream,
+                                         krr_info *info);
 
 /* ------------------------------------------------------------------------ */
 /* Sparse sign embedding of Alg. 2 (Sec. 2.2.1): Phi is s x N; column n has   */

@@ -12,8 +12,10 @@ from .api import (  # noqa: F401
     krill_build,
     krill_solve,
     krr_kmatvec,
+    krr_kmatvec_batched,
     krr_launch_count,
     krr_pcg_solve,
+    krr_pcg_solve_batched,
     krr_predict,
     krr_precond_apply,
     krr_rpc_sample,

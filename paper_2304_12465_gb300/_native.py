@@ -47,6 +47,7 @@ SIGNATURES = {
     "krr_kmatvec": (_int, [_vp, _i64, _int, _int, _dbl, _dbl, _vp, _int, _vp, _int, _vp]),
     "krr_kmatvec_f64_noalloc": (_int, [_vp, _i64, _int, _int, _dbl, _dbl, _vp, _int, _vp,
                                        _vp]),
+    "krr_kmatvec_batched": (_int, [_vp, _i64, _int, _int, _vp, _vp, _int, _vp, _vp, _vp, _vp]),
     "krr_predict": (_int, [_vp, _i64, _int, _int, _dbl, _vp, _int, _vp, _i64, _vp, _int, _vp]),
     "krr_rpc_sample": (_int, [_vp, _i64, _dbl, _u64, _u64, _int, _vp, C.POINTER(_int), _vp]),
     "krr_rpcholesky": (_int, [_vp, _i64, _int, _int, _dbl, _int, _int, _u64, _vp,
@@ -57,6 +58,8 @@ SIGNATURES = {
     "krr_precond_apply": (_int, [_vp, _dbl, _vp, _int, _vp, _int, _vp]),
     "krr_pcg_solve": (_int, [_vp, _i64, _int, _int, _dbl, _vp, _int, _dbl, _vp, _dbl, _int,
                              _int, _vp, _vp, C.POINTER(KrrInfo)]),
+    "krr_pcg_solve_batched": (_int, [_vp, _i64, _int, _int, _vp, _vp, _vp, _int, _vp, _vp, _dbl,
+                                     _int, _vp, _vp, C.POINTER(KrrInfo)]),
     "krr_sparse_sign": (_int, [_i64, _int, _int, _u64, _vp, _vp, _vp]),
     "krill_build": (_int, [_vp, _i64, _int, _int, _dbl, _vp, _int, _dbl, _int, _int, _u64, _vp,
                            C.POINTER(_vp)]),

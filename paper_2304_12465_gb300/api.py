@@ -89,6 +89,27 @@ def krr_kmatvec(X, kern, sigma: float, lam: float, V, prec="fp64", stream=None):
     return Y
 
 
+def krr_kmatvec_batched(X, kerns, sigmas, lambdas, V, stream=None):
+    """Batched product: settings s (kerns[s], sigmas[s]) with ms = len(V) // S
+    columns each; V (S*ms, N), lambdas (S*ms,).  Returns Y like V."""
+    lib = load()
+    Xk, Xp = _arr(X)
+    Vk, Vp = _arr(V)
+    Nn, d = Xk.shape
+    S = len(kerns)
+    mt = _shape2(Vk)[0]
+    ms = mt // S
+    assert ms * S == mt
+    kk = np.ascontiguousarray([_kern(k) for k in kerns], dtype=np.int32)
+    ss = np.ascontiguousarray(sigmas, dtype=np.float64)
+    ll = np.ascontiguousarray(lambdas, dtype=np.float64)
+    Y, Yp = _empty_like_container(V, (mt, Nn))
+    check(lib.krr_kmatvec_batched(Xp, Nn, d, S, C.c_void_p(kk.ctypes.data),
+                                  C.c_void_p(ss.ctypes.data), ms, C.c_void_p(ll.ctypes.data),
+                                  Vp, Yp, _stream(stream, X, V)), "krr_kmatvec_batched")
+    return Y
+
+
 def krr_predict(Xtrain, kern, sigma: float, alpha, Xtest, prec="fp64", stream=None):
     """Predictions K(Xtest, Xtrain) alpha, alpha (m, N) -> (m, Nt)."""
     lib = load()
@@ -213,6 +234,40 @@ def krr_pcg_solve(X, kern, sigma: float, Y, mu: float, F: Optional[Factor], tol:
                                  F.handle if F is not None else None, float(tol), int(maxit),
                                  _prec(prec), Ap, _stream(stream, X, Y), C.byref(info)),
                "krr_pcg_solve", allow)
+    res = info.as_dict()
+    res["status"] = N_.STATUS_NAMES[st]
+    return A, res
+
+
+def krr_pcg_solve_batched(X, kerns, sigmas, factors, mus, Y, tol: float, maxit: int = 0,
+                          stream=None, out=None, raise_on_noconv=False):
+    """Batched Alg. 1 PCG: settings (kerns[q], sigmas[q], factors[q]) x
+    regularisations mus; Y (S*len(mus), N), column q*ms + c.  Returns
+    (alpha like Y, info dict)."""
+    lib = load()
+    Xk, Xp = _arr(X)
+    Yk, Yp = _arr(Y)
+    Nn, d = Xk.shape
+    S, ms = len(kerns), len(mus)
+    mt = S * ms
+    assert _shape2(Yk)[0] == mt
+    kk = np.ascontiguousarray([_kern(k) for k in kerns], dtype=np.int32)
+    ss = np.ascontiguousarray(sigmas, dtype=np.float64)
+    mm = np.ascontiguousarray(mus, dtype=np.float64)
+    handles = (C.c_void_p * S)(*[(f.handle if f is not None else None) for f in factors]) \
+        if factors is not None else None
+    if out is None:
+        A, Ap = _empty_like_container(Y, (mt, Nn))
+    else:
+        A, Ap = out, C.c_void_p(out.data_ptr() if _is_torch(out) else out.ctypes.data)
+    info = KrrInfo()
+    allow = () if raise_on_noconv else (N_.KRR_ENOCONV,)
+    st = check(lib.krr_pcg_solve_batched(Xp, Nn, d, S, C.c_void_p(kk.ctypes.data),
+                                         C.c_void_p(ss.ctypes.data),
+                                         C.cast(handles, C.c_void_p) if handles else None, ms,
+                                         C.c_void_p(mm.ctypes.data), Yp, float(tol), int(maxit),
+                                         Ap, _stream(stream, X, Y), C.byref(info)),
+               "krr_pcg_solve_batched", allow)
     res = info.as_dict()
     res["status"] = N_.STATUS_NAMES[st]
     return A, res

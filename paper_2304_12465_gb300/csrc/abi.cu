@@ -235,6 +235,44 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
   return out.finish(s);
 }
 
+krr_status krr_kmatvec_batched(const double *X, int64_t N, int d, int S, const int *kerns,
+                               const double *sigmas, int ms, const double *lambdas,
+                               const double *V, double *Y, void *stream) {
+  clear_error();
+  KRR_REQUIRE(X && kerns && sigmas && lambdas && V && Y, "NULL argument");
+  KRR_REQUIRE(N >= 1, "N must be >= 1");
+  KRR_REQUIRE(d >= 1 && d <= 32, "d must be in [1, 32]");
+  KRR_REQUIRE(S >= 1 && S <= KRR_MAX_SETTINGS, "S must be in [1, %d]", KRR_MAX_SETTINGS);
+  KRR_REQUIRE(ms == 1 || ms == 2, "ms must be 1 or 2");
+  for (int q = 0; q < S; ++q) {
+    KRR_REQUIRE(valid_kernel(kerns[q]), "unknown kernel %d in setting %d", kerns[q], q);
+    KRR_REQUIRE(sigmas[q] > 0 && std::isfinite(sigmas[q]), "sigma of setting %d invalid", q);
+  }
+  for (int c = 0; c < S * ms; ++c)
+    KRR_REQUIRE(std::isfinite(lambdas[c]), "lambda %d is not finite", c);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int mt = S * ms;
+  DevBuf<double> tx, tv;
+  const double *Xd, *Vd;
+  KRR_TRY(device_view(X, (size_t)N * d, s, tx, &Xd));
+  KRR_TRY(device_view(V, (size_t)N * mt, s, tv, &Vd));
+  OutView<double> out;
+  KRR_TRY(out.init(Y, (size_t)N * mt, s));
+  PointsF32 P;
+  KRR_TRY(kmvb_prepare(Xd, N, d, s, P));
+  std::vector<float> lam32(mt);
+  for (int c = 0; c < mt; ++c) lam32[c] = (float)lambdas[c];
+  DevBuf<float> lam, v32, y32, part;
+  KRR_TRY(lam.alloc(mt, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(lam.p, lam32.data(), sizeof(float) * mt, cudaMemcpyHostToDevice, s));
+  KRR_TRY(v32.alloc((size_t)N * mt, s));
+  KRR_TRY(y32.alloc((size_t)N * mt, s));
+  KRR_TRY(convert_f64_to_f32(Vd, v32.p, N * mt, s));
+  KRR_TRY(kmv_batched_f32(P, S, kerns, sigmas, ms, lam.p, v32.p, y32.p, s, part));
+  KRR_TRY(convert_f32_to_f64(y32.p, out.dev, N * mt, s));
+  return out.finish(s);
+}
+
 krr_status krr_predict(const double *Xtrain, int64_t N, int d, krr_kernel kern, double sigma,
                        const double *alpha, int m, const double *Xtest, int64_t Nt,
                        double *out, krr_precision prec, void *stream) {
@@ -415,6 +453,48 @@ krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel kern, dou
   if (info && prof) {
     kmv_profile_collect(0, &info->kmv_ms, &info->kmv_launches);
     kmv_profile_collect(1, &info->kmv64_ms, &info->kmv64_launches);
+    kmv_profile_collect(2, &info->kmvff_ms, &info->kmvff_launches);
+  }
+  return st;
+}
+
+krr_status krr_pcg_solve_batched(const double *X, int64_t N, int d, int S, const int *kerns,
+                                 const double *sigmas, const krr_factor *const *factors,
+                                 int ms, const double *mus, const double *Y, double tol,
+                                 int maxit, double *alpha_out, void *stream, krr_info *info) {
+  clear_error();
+  KRR_REQUIRE(X && kerns && sigmas && mus && Y && alpha_out, "NULL argument");
+  KRR_REQUIRE(N >= 1, "N must be >= 1");
+  KRR_REQUIRE(d >= 1 && d <= 32, "d must be in [1, 32]");
+  KRR_REQUIRE(S >= 1 && S <= KRR_MAX_SETTINGS, "S must be in [1, %d]", KRR_MAX_SETTINGS);
+  KRR_REQUIRE(ms == 1 || ms == 2, "ms must be 1 or 2");
+  KRR_REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+  for (int q = 0; q < S; ++q) {
+    KRR_REQUIRE(valid_kernel(kerns[q]), "unknown kernel %d in setting %d", kerns[q], q);
+    KRR_REQUIRE(sigmas[q] > 0 && std::isfinite(sigmas[q]), "sigma of setting %d invalid", q);
+    KRR_REQUIRE(!factors || !factors[q] || factors[q]->N == N, "factor %d has the wrong N", q);
+  }
+  for (int c = 0; c < ms; ++c)
+    KRR_REQUIRE(mus[c] > 0 && std::isfinite(mus[c]), "mu %d must be positive", c);
+  if (maxit <= 0) maxit = 1000;
+  const int mt = S * ms;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf<double> tx, ty;
+  const double *Xd, *Yd;
+  KRR_TRY(device_view(X, (size_t)N * d, s, tx, &Xd));
+  KRR_TRY(device_view(Y, (size_t)N * mt, s, ty, &Yd));
+  OutView<double> out;
+  KRR_TRY(out.init(alpha_out, (size_t)N * mt, s));
+  if (info) std::memset(info, 0, sizeof(*info));
+  const bool prof = profiling_on();
+  if (prof) kmv_profile_reset();
+  krr_status st = pcg_solve_batched_device(Xd, N, d, S, kerns, sigmas, factors, ms, mus, Yd, tol,
+                                           maxit, out.dev, s, info);
+  if (st != KRR_OK && st != KRR_ENOCONV) return st;
+  krr_status st2 = out.finish(s);
+  if (st2 != KRR_OK) return st2;
+  if (info && prof) {
+    kmv_profile_collect(0, &info->kmv_ms, &info->kmv_launches);
     kmv_profile_collect(2, &info->kmvff_ms, &info->kmvff_launches);
   }
   return st;

@@ -140,6 +140,112 @@ krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k) {
   return KRR_OK;
 }
 
+// ------------------------------------------------------------ Gram (F^T F)
+// Lower-triangular output tiles only.  float input: each K tile of GB_K
+// products is summed in float32, then added to float64 accumulators (one
+// float64 add per GB_K float32 FMAs); double input: float64 throughout.
+template <typename T>
+__global__ void __launch_bounds__(G_THREADS)
+gram_lower_kernel(const T *__restrict__ F, int64_t N, int r, int kslice,
+                  double *__restrict__ part) {
+  __shared__ T As[GB_K][GB_M + 1];
+  __shared__ T Bs[GB_K][GB_N + 1];
+  // map blockIdx.x to a lower-triangular (ti, tj) tile pair, tj <= ti
+  int t = blockIdx.x, ti = 0;
+  while (t > ti) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = ti * GB_M, j0 = tj * GB_N;
+  const int64_t kb = (int64_t)blockIdx.y * kslice;
+  const int64_t ke = min(N, kb + kslice);
+  double acc[4][4];
+  T acc32[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
+#pragma unroll
+    for (int e = 0; e < (GB_M * GB_K) / G_THREADS; ++e) {
+      const int idx = tid + e * G_THREADS;
+      const int kk = idx % GB_K, ii = idx / GB_K;
+      const int64_t gk = k0 + kk;
+      As[kk][ii] = (i0 + ii < r && gk < ke) ? F[gk + (int64_t)(i0 + ii) * N] : T(0);
+      Bs[kk][ii] = (j0 + ii < r && gk < ke) ? F[gk + (int64_t)(j0 + ii) * N] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc32[a][b] = T(0);
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc32[a][b] = fma(av[a], bv[b], acc32[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += (double)acc32[a][b];
+    __syncthreads();
+  }
+  double *o = part + (int64_t)blockIdx.y * r * r;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+      if (gi < r && gj <= gi) o[(int64_t)gi + (int64_t)gj * r] = acc[a][b];
+    }
+}
+
+__global__ void gram_combine_kernel(const double *__restrict__ part, int slices, int r,
+                                    double *__restrict__ C) {
+  const int64_t total = (int64_t)r * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % r), j = (int)(e / r);
+    if (j > i) continue;
+    double acc = 0.0;
+    for (int z = 0; z < slices; ++z) acc += part[(int64_t)z * total + e];
+    C[e] = acc;
+  }
+}
+
+template <typename T>
+krr_status gram_lower(const T *F, int64_t N, int r, double *C, cudaStream_t s) {
+  if (r <= 0) return KRR_OK;
+  const int tiles = (r + GB_M - 1) / GB_M;
+  const int ntri = tiles * (tiles + 1) / 2;
+  int64_t slices = ((int64_t)num_sms() * 4 + ntri - 1) / ntri;
+  const int64_t maxs = (N + 1023) / 1024;
+  if (slices > maxs) slices = maxs;
+  if (slices < 1) slices = 1;
+  int64_t kslice = (N + slices - 1) / slices;
+  kslice = (kslice + GB_K - 1) / GB_K * GB_K;
+  slices = (N + kslice - 1) / kslice;
+  DevBuf<double> part;
+  KRR_TRY(part.alloc((size_t)slices * r * r, s));
+  gram_lower_kernel<T><<<dim3(ntri, (unsigned)slices), G_THREADS, 0, s>>>(F, N, r, (int)kslice,
+                                                                         part.p);
+  KRR_LAUNCH_CHECK();
+  int blocks = ceil_div((int64_t)r * r, 256);
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+  gram_combine_kernel<<<blocks, 256, 0, s>>>(part.p, (int)slices, r, C);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+template krr_status gram_lower<float>(const float *, int64_t, int, double *, cudaStream_t);
+template krr_status gram_lower<double>(const double *, int64_t, int, double *, cudaStream_t);
+
 template krr_status gemm<double>(const Gemm<double> &, cudaStream_t, int);
 template krr_status gemm<float>(const Gemm<float> &, cudaStream_t, int);
 

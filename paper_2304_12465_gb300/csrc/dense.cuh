@@ -25,6 +25,12 @@ struct Gemm {
 template <typename T>
 krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k = 1);
 
+// Lower triangle of C (r x r, column-major) = F^T F for F N x r column-major.
+// float F: float32 products summed in float32 over 16-term chunks, then in
+// float64; double F: float64.  The strict upper triangle of C is untouched.
+template <typename T>
+krr_status gram_lower(const T *F, int64_t N, int r, double *C, cudaStream_t s);
+
 // Picks a split-K count that fills the machine for a long, thin reduction.
 int gemm_auto_split(int M, int N, int K);
 

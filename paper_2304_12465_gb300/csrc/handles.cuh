@@ -1,6 +1,7 @@
 // Library-owned handle layouts shared by the translation units.
 #pragma once
 
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -37,7 +38,9 @@ struct krr_factor {
   int64_t *S = nullptr;     // pivots, column order
   double *dres = nullptr;   // residual diagonal
   mutable std::mutex mtx;
-  mutable std::vector<krr::NystromCore> cores;
+  // a deque keeps the address of every core stable while more are added, so
+  // pointers handed out by nystrom_core stay valid for the factor's lifetime
+  mutable std::deque<krr::NystromCore> cores;
 };
 
 struct krill_precond {

@@ -67,6 +67,14 @@ krr_status kmv_f64_with_scratch(const double *Xd, int64_t N, int d, int kern, do
                                 int64_t ldy, double *scratch, size_t scratch_elems,
                                 cudaStream_t s);
 
+// Batched multi-setting float32 product (kmvb.cu): S settings (kernel type,
+// sigma) with ms columns each, column s*ms + c shifted by lambda_dev[s*ms+c];
+// V, Y: (S ms) x N.  Points prepared by kmvb_prepare (centred, unscaled).
+krr_status kmvb_prepare(const double *Xd, int64_t N, int d, cudaStream_t s, PointsF32 &P);
+krr_status kmv_batched_f32(const PointsF32 &P, int S, const int *kerns, const double *sigmas,
+                           int ms, const float *lambda_dev, const float *V, float *Y,
+                           cudaStream_t s, DevBuf<float> &part);
+
 // Number of kernel entries one product evaluates (N^2).
 inline double kmv_entries(int64_t N) { return (double)N * (double)N; }
 

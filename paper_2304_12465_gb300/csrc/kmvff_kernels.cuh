@@ -206,7 +206,8 @@ kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
           for (int k = 0; k < DP; ++k) {
             FF dd = two_sum(ih[r][k], -sxh[jj][k]);
             dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
-            if (dd.h < 0.0f) {
+            // sign of the unevaluated sum (dd.h is 0 when the high parts agree)
+            if (__fadd_rn(dd.h, dd.l) < 0.0f) {
               dd.h = -dd.h;
               dd.l = -dd.l;
             }
@@ -226,7 +227,9 @@ kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
             FF dd = two_sum(ih[r][k], -sxh[jj][k]);
             dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
             const FF p = two_prod(dd.h, dd.h);
-            const float cross = __fmaf_rn(__fadd_rn(dd.h, dd.h), dd.l, p.l);
+            // d^2 = dh^2 + 2 dh dl + dl^2 (dl^2 matters when dh is 0 or tiny)
+            const float cross =
+                __fmaf_rn(__fadd_rn(dd.h, dd.h), dd.l, __fmaf_rn(dd.l, dd.l, p.l));
             const FF t = two_sum(s.h, p.h);
             s.h = t.h;
             lo = __fadd_rn(lo, __fadd_rn(t.l, cross));

@@ -15,15 +15,19 @@ namespace krr {
 // Both are HBM-bound; products and in-block sums use the precision of the
 // data (float32 in the mixed path, float64 otherwise), sums across blocks are
 // float64, in a fixed order.
-constexpr int TT_ROWS = 256;   // rows per block of the transposed product
+constexpr int TT_ROWS = 512;   // rows per block of the transposed product
 constexpr int RED_BLOCKS = 512;
 
 // part[b][l][c] = sum_{n in block b} F[n + l N] R[c][n]
+// One warp per column l; each lane holds TT_ROWS/32 rows, all loaded before
+// any arithmetic so that many loads are in flight.
 template <typename T>
 __global__ void __launch_bounds__(256)
 tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict__ R, int m,
               double *__restrict__ part) {
-  __shared__ T sR[16][TT_ROWS];
+  constexpr int PER_LANE = TT_ROWS / 32;
+  extern __shared__ __align__(16) unsigned char tall_t_smem[];
+  T(*sR)[TT_ROWS] = reinterpret_cast<T(*)[TT_ROWS]>(tall_t_smem);   // m x TT_ROWS
   const int64_t n0 = (int64_t)blockIdx.x * TT_ROWS;
   const int nr = (int)min((int64_t)TT_ROWS, N - n0);
   for (int e = threadIdx.x; e < m * TT_ROWS; e += blockDim.x) {
@@ -33,16 +37,21 @@ tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict_
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = warp; l < rank; l += blockDim.x >> 5) {
+    const T *col = F + (int64_t)l * N + n0;
+    T f[PER_LANE];
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
+      const int n = lane + 32 * q;
+      f[q] = (n < nr) ? col[n] : T(0);
+    }
     T acc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = T(0);
-    const T *col = F + (int64_t)l * N + n0;
-#pragma unroll 4
-    for (int n = lane; n < nr; n += 32) {
-      const T f = col[n];
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
 #pragma unroll
       for (int c = 0; c < 16; ++c)
-        if (c < m) acc[c] = fma(f, sR[c][n], acc[c]);
+        if (c < m) acc[c] = fma(f[q], sR[c][lane + 32 * q], acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -54,15 +63,19 @@ tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict_
   }
 }
 
-// t[c][l] = sum_b part[b][l][c]
+// t[c][l] = sum_b part[b][l][c], one warp per (l, c), blocks summed in a
+// fixed lane-strided order then a fixed shuffle tree.
 __global__ void tall_t_reduce_kernel(const double *__restrict__ part, int nb, int rank, int m,
                                      double *__restrict__ t) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warps = blockDim.x >> 5;
+  const int e = blockIdx.x * warps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (e >= rank * m) return;
   const int l = e / m, c = e % m;
   double acc = 0.0;
-  for (int b = 0; b < nb; ++b) acc += part[((int64_t)b * rank + l) * m + c];
-  t[(int64_t)c * rank + l] = acc;
+  for (int b = lane; b < nb; b += 32) acc += part[((int64_t)b * rank + l) * m + c];
+  acc = warp_sum(acc);
+  if (lane == 0) t[(int64_t)c * rank + l] = acc;
 }
 
 // Triangular products with one warp per output row, reading contiguous
@@ -99,13 +112,17 @@ __global__ void tri_gemv_kernel(const double *__restrict__ Mt, int rank,
 }
 
 // Z[c][n] = (R[c][n] - sum_l F[n + l N] v[c][l]) / lambda
+// One thread per row; the column loop loads LU values of F before using them
+// so that enough loads are in flight to stream F at HBM speed.
 template <typename T>
 __global__ void __launch_bounds__(256)
 tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
               int m, const T *__restrict__ R, double inv_lambda, T *__restrict__ Z) {
   constexpr int LCH = 256;
+  constexpr int LU = 16;
   __shared__ T sv[LCH][16];
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = n < N;
   T acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = T(0);
@@ -117,17 +134,20 @@ tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__rest
       sv[l][c] = (l < nl) ? (T)v[(int64_t)c * rank + l0 + l] : T(0);
     }
     __syncthreads();
-    if (n < N) {
-#pragma unroll 4
-      for (int l = 0; l < nl; ++l) {
-        const T f = F[n + (int64_t)(l0 + l) * N];
+    for (int lb = 0; lb < nl; lb += LU) {
+      T f[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u)
+        f[u] = (ok && lb + u < nl) ? F[n + (int64_t)(l0 + lb + u) * N] : T(0);
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-          if (c < m) acc[c] = fma(f, sv[l][c], acc[c]);
+          if (c < m) acc[c] = fma(f[u], sv[lb + u][c], acc[c]);
       }
     }
   }
-  if (n < N) {
+  if (ok) {
     for (int c = 0; c < m; ++c)
       Z[(int64_t)c * N + n] = (T)(((double)R[(int64_t)c * N + n] - (double)acc[c]) * inv_lambda);
   }
@@ -152,10 +172,13 @@ static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const doub
   KRR_TRY(t.alloc((size_t)rank * m, s));
   KRR_TRY(u.alloc((size_t)rank * m, s));
   KRR_TRY(v.alloc((size_t)rank * m, s));
-  tall_t_kernel<T><<<nb, 256, 0, s>>>(F, N, rank, R, m, part.p);
+  const size_t smem = (size_t)m * TT_ROWS * sizeof(T);
+  KRR_CUDA_TRY(cudaFuncSetAttribute(tall_t_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+  tall_t_kernel<T><<<nb, 256, smem, s>>>(F, N, rank, R, m, part.p);
   KRR_LAUNCH_CHECK();
-  tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 256), 256, 0, s>>>(part.p, nb, rank, m,
-                                                                      t.p);
+  tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 8), 256, 0, s>>>(part.p, nb, rank, m,
+                                                                    t.p);
   KRR_LAUNCH_CHECK();
   KRR_TRY(tri_apply_lower(Wt, rank, t.p, m, u.p, s));
   KRR_TRY(tri_apply_lower_t(W, rank, u.p, m, v.p, s));
@@ -192,23 +215,17 @@ krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s
   const int r = f->rank;
   const int64_t N = f->N;
   if (r > 0) {
-    const double *Fp = f->F;
-    DevBuf<double> Fround;
-    if (prec == KRR_PREC_MIXED) {
-      KRR_TRY(dev_alloc(&c.F32, (size_t)N * r));
-      KRR_TRY(convert_f64_to_f32(f->F, c.F32, N * r, s));
-      KRR_TRY(Fround.alloc((size_t)N * r, s));
-      KRR_TRY(convert_f32_to_f64(c.F32, Fround.p, N * r, s));
-      Fp = Fround.p;
-    }
     DevBuf<double> Gm;
     KRR_TRY(Gm.alloc((size_t)r * r, s));
-    Gemm<double> g;
-    g.M = r; g.N = r; g.K = (int)N;
-    g.A = Fp; g.sai = N; g.sak = 1;
-    g.B = Fp; g.sbk = 1; g.sbj = N;
-    g.alpha = 1.0; g.beta = 0.0; g.C = Gm.p; g.ldc = r;
-    KRR_TRY(gemm(g, s, gemm_auto_split(r, r, (int)N)));
+    if (prec == KRR_PREC_MIXED) {
+      // the mixed preconditioner is built from F rounded to float32, so that
+      // it is exactly P^{-1} for that factor (up to the Gram accumulation)
+      KRR_TRY(dev_alloc(&c.F32, (size_t)N * r));
+      KRR_TRY(convert_f64_to_f32(f->F, c.F32, N * r, s));
+      KRR_TRY(gram_lower<float>(c.F32, N, r, Gm.p, s));
+    } else {
+      KRR_TRY(gram_lower<double>(f->F, N, r, Gm.p, s));
+    }
     KRR_TRY(add_diagonal(Gm.p, r, r, c.lambda, s));
     krr_status st = potrf_lower(Gm.p, r, r, s);
     if (st != KRR_OK) {

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <functional>
 #include <vector>
 
 #include "dense.cuh"
@@ -32,6 +33,18 @@ static krr_status scale(const T *in, T *out, int64_t n, double a, cudaStream_t s
 
 // Relative tolerance floor of one inner float32 PCG solve.
 constexpr double kInnerFloor = 1e-4;
+
+struct RefineStats {
+  int iters = 0, outer = 0, products32 = 0, products64 = 0;
+  double relres = 0.0;
+  krr_status status = KRR_OK;
+};
+
+krr_status refine_solve(const PcgOps<float> &ops,
+                        const std::function<krr_status(const double *, double *, cudaStream_t)>
+                            &product64,
+                        int64_t N, int m, const double *Y, double *alpha, double tol, int maxit,
+                        cudaStream_t s, RefineStats *rs);
 
 static double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -90,14 +103,8 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
     PointsFF Pff;
     KRR_TRY(prepare_points_ff(Xd, N, d, kern, sigma, s, Pff));
-    DevBuf<float> part32, b32, d32, vsplit;
-    DevBuf<double> part64, mx, r64;
-    KRR_TRY(b32.alloc((size_t)N * m, s));
-    KRR_TRY(d32.alloc((size_t)N * m, s));
-    KRR_TRY(mx.alloc((size_t)N * m, s));
-    KRR_TRY(r64.alloc((size_t)N * m, s));
-    KRR_CUDA_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * N * m, s));
-    KRR_CUDA_TRY(cudaMemcpyAsync(r64.p, Y, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, s));
+    DevBuf<float> part32, vsplit;
+    DevBuf<double> part64;
     PcgOps<float> ops;
     const float lam32 = (float)lambda;
     ops.product = [&](const float *in, float *out, cudaStream_t st) {
@@ -107,55 +114,16 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
       if (core) return nystrom_apply_f32(F, core, in, m, out, st);
       return scale<float>(in, out, N * m, 1.0 / lambda, st);
     };
-    std::vector<double> yn(m), rn(m);
-    KRR_TRY(column_norms(Y, N, m, yn.data(), s));
-    rn = yn;
-    const int max_outer = 12;
-    double prev_worst = 1e300;
-    final_status = KRR_ENOCONV;
-    int budget = maxit;
-    while (true) {
-      double worst = 0.0;
-      for (int c = 0; c < m; ++c) worst = std::max(worst, yn[c] > 0 ? rn[c] / yn[c] : 0.0);
-      relres = worst;
-      if (worst <= tol) { final_status = KRR_OK; break; }
-      if (outer >= max_outer || budget <= 0) break;
-      if (outer > 0 && worst > 0.5 * prev_worst) break;  // refinement stagnated
-      prev_worst = worst;
-      // inner tolerances: aim a little below what the outer test needs, but
-      // stop each float32 solve at 1e-4 -- below that its recursive residual
-      // keeps falling while the true residual is held up by float32 products,
-      // so the iterations are better spent after the next float64 residual
-      std::vector<double> inner_tol(m);
-      for (int c = 0; c < m; ++c) {
-        const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
-        inner_tol[c] = (rel > tol) ? std::max(0.3 * tol / rel, kInnerFloor) : 1.0;
-      }
-      // columns already converged get a zero right-hand side (no work)
-      KRR_TRY(convert_f64_to_f32(r64.p, b32.p, N * m, s));
-      for (int c = 0; c < m; ++c) {
-        const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
-        if (!(rel > tol)) KRR_CUDA_TRY(cudaMemsetAsync(b32.p + (int64_t)c * N, 0, sizeof(float) * N, s));
-      }
-      PcgStats st;
-      KRR_TRY(pcg_run<float>(ops, N, m, b32.p, d32.p, inner_tol.data(), budget, s, &st));
-      iters_total += st.iters_max;
-      budget -= st.iters_max;
-      entries += kmv_entries(N) * st.products;
-      KRR_TRY(add_f32_to_f64(alpha, d32.p, N * m, s));
-      KRR_TRY(kmv_ff(Pff, lambda, alpha, N, m, mx.p, N, s, part64, vsplit));
-      entries += kmv_entries(N);
-      KRR_TRY(residual_f64(Y, mx.p, r64.p, N * m, s));
-      KRR_TRY(column_norms(r64.p, N, m, rn.data(), s));
-      ++outer;
-      if (st.breakdown) { final_status = KRR_EBREAKDOWN; break; }
-    }
-    if (final_status != KRR_OK && final_status != KRR_EBREAKDOWN) {
-      double worst = 0.0;
-      for (int c = 0; c < m; ++c) worst = std::max(worst, yn[c] > 0 ? rn[c] / yn[c] : 0.0);
-      relres = worst;
-      if (worst <= tol) final_status = KRR_OK;
-    }
+    auto product64 = [&](const double *in, double *out, cudaStream_t st) {
+      return kmv_ff(Pff, lambda, in, N, m, out, N, st, part64, vsplit);
+    };
+    RefineStats rs;
+    KRR_TRY(refine_solve(ops, product64, N, m, Y, alpha, tol, maxit, s, &rs));
+    iters_total = rs.iters;
+    outer = rs.outer;
+    relres = rs.relres;
+    final_status = rs.status;
+    entries += kmv_entries(N) * (rs.products32 + rs.products64);
   }
   KRR_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) {
@@ -171,6 +139,171 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     set_error("PCG did not reach the tolerance (relative residual %.3e > %.3e)", relres, tol);
   if (final_status == KRR_EBREAKDOWN) set_error("PCG breakdown: p^T M p <= 0 or NaN");
   return final_status;
+}
+
+// Mixed-precision iterative refinement shared by the single and batched
+// solves: x = 0, r = y; repeat { solve M d = r with the float32 PCG to a
+// loose per-column tolerance; x += d; r = y - M x with the float64-accurate
+// product } until every column's float64 relative residual is <= tol.
+krr_status refine_solve(const PcgOps<float> &ops,
+                        const std::function<krr_status(const double *, double *, cudaStream_t)>
+                            &product64,
+                        int64_t N, int m, const double *Y, double *alpha, double tol, int maxit,
+                        cudaStream_t s, RefineStats *rs) {
+  DevBuf<float> b32, d32;
+  DevBuf<double> mx, r64;
+  KRR_TRY(b32.alloc((size_t)N * m, s));
+  KRR_TRY(d32.alloc((size_t)N * m, s));
+  KRR_TRY(mx.alloc((size_t)N * m, s));
+  KRR_TRY(r64.alloc((size_t)N * m, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * N * m, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(r64.p, Y, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> yn(m), rn(m);
+  KRR_TRY(column_norms(Y, N, m, yn.data(), s));
+  rn = yn;
+  const int max_outer = 12;
+  double prev_worst = 1e300;
+  krr_status final_status = KRR_ENOCONV;
+  int budget = maxit, outer = 0, iters = 0, prod32 = 0;
+  double relres = 0.0;
+  auto worst_rel = [&]() {
+    double w = 0.0;
+    for (int c = 0; c < m; ++c) w = std::max(w, yn[c] > 0 ? rn[c] / yn[c] : 0.0);
+    return w;
+  };
+  while (true) {
+    const double worst = worst_rel();
+    relres = worst;
+    if (worst <= tol) { final_status = KRR_OK; break; }
+    if (outer >= max_outer || budget <= 0) break;
+    if (outer > 0 && worst > 0.5 * prev_worst) break;  // refinement stagnated
+    prev_worst = worst;
+    // inner tolerances: aim a little below what the outer test needs, but
+    // stop each float32 solve at kInnerFloor -- below that its recursive
+    // residual keeps falling while the true residual is held up by float32
+    // products, so the iterations are better spent after the next float64
+    // residual
+    std::vector<double> inner_tol(m);
+    KRR_TRY(convert_f64_to_f32(r64.p, b32.p, N * m, s));
+    for (int c = 0; c < m; ++c) {
+      const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
+      inner_tol[c] = (rel > tol) ? std::max(0.3 * tol / rel, kInnerFloor) : 1.0;
+      // columns already converged get a zero right-hand side (no work)
+      if (!(rel > tol))
+        KRR_CUDA_TRY(cudaMemsetAsync(b32.p + (int64_t)c * N, 0, sizeof(float) * N, s));
+    }
+    PcgStats st;
+    KRR_TRY(pcg_run<float>(ops, N, m, b32.p, d32.p, inner_tol.data(), budget, s, &st));
+    iters += st.iters_max;
+    budget -= st.iters_max;
+    prod32 += st.products;
+    KRR_TRY(add_f32_to_f64(alpha, d32.p, N * m, s));
+    KRR_TRY(product64(alpha, mx.p, s));
+    KRR_TRY(residual_f64(Y, mx.p, r64.p, N * m, s));
+    KRR_TRY(column_norms(r64.p, N, m, rn.data(), s));
+    ++outer;
+    if (st.breakdown) { final_status = KRR_EBREAKDOWN; break; }
+  }
+  if (final_status != KRR_OK && final_status != KRR_EBREAKDOWN) {
+    relres = worst_rel();
+    if (relres <= tol) final_status = KRR_OK;
+  }
+  rs->iters = iters;
+  rs->outer = outer;
+  rs->relres = relres;
+  rs->status = final_status;
+  rs->products32 = prod32;
+  rs->products64 = outer;
+  return KRR_OK;
+}
+
+// --------------------------------------------------------------- batched
+__global__ void add_shift_kernel(double *__restrict__ out, const double *__restrict__ x,
+                                 int64_t N, int m, const double *__restrict__ lam) {
+  const int64_t total = N * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] += lam[e / N] * x[e];
+}
+
+krr_status pcg_solve_batched_device(const double *Xd, int64_t N, int d, int S,
+                                    const int *kerns, const double *sigmas,
+                                    const krr_factor *const *factors, int ms,
+                                    const double *mus, const double *Y, double tol, int maxit,
+                                    double *alpha, cudaStream_t s, krr_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int mt = S * ms;
+  std::vector<double> lam(mt);
+  std::vector<const NystromCore *> cores(mt, nullptr);
+  double t_build = 0.0;
+  for (int q = 0; q < S; ++q)
+    for (int c = 0; c < ms; ++c) {
+      lam[q * ms + c] = mus[c] * (double)N;
+      if (factors && factors[q] && factors[q]->rank > 0) {
+        KRR_TRY(nystrom_core(factors[q], mus[c], KRR_PREC_MIXED, s, &cores[q * ms + c]));
+        t_build += cores[q * ms + c]->build_s;
+      }
+    }
+  auto t1 = std::chrono::steady_clock::now();
+  (void)t0;
+  PointsF32 Pb;
+  KRR_TRY(kmvb_prepare(Xd, N, d, s, Pb));
+  std::vector<PointsFF> Pff(S);
+  for (int q = 0; q < S; ++q) KRR_TRY(prepare_points_ff(Xd, N, d, kerns[q], sigmas[q], s, Pff[q]));
+  std::vector<float> lam32(mt);
+  for (int c = 0; c < mt; ++c) lam32[c] = (float)lam[c];
+  DevBuf<float> lam_dev32, part32, vsplit;
+  DevBuf<double> lam_dev, part64;
+  KRR_TRY(lam_dev32.alloc(mt, s));
+  KRR_TRY(lam_dev.alloc(mt, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(lam_dev32.p, lam32.data(), sizeof(float) * mt,
+                               cudaMemcpyHostToDevice, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(lam_dev.p, lam.data(), sizeof(double) * mt,
+                               cudaMemcpyHostToDevice, s));
+  PcgOps<float> ops;
+  ops.product = [&](const float *in, float *out, cudaStream_t st) {
+    return kmv_batched_f32(Pb, S, kerns, sigmas, ms, lam_dev32.p, in, out, st, part32);
+  };
+  ops.precond = [&](const float *in, float *out, cudaStream_t st) {
+    for (int q = 0; q < S; ++q)
+      for (int c = 0; c < ms; ++c) {
+        const int col = q * ms + c;
+        const float *r = in + (int64_t)col * N;
+        float *z = out + (int64_t)col * N;
+        if (cores[col]) KRR_TRY(nystrom_apply_f32(factors[q], cores[col], r, 1, z, st));
+        else KRR_TRY(scale<float>(r, z, N, 1.0 / lam[col], st));
+      }
+    return KRR_OK;
+  };
+  auto product64 = [&](const double *in, double *out, cudaStream_t st) {
+    // A_s x without the shift, per setting, then + lambda x per column
+    for (int q = 0; q < S; ++q)
+      KRR_TRY(kmv_ff(Pff[q], 0.0, in + (int64_t)q * ms * N, N, ms, out + (int64_t)q * ms * N,
+                     N, st, part64, vsplit));
+    int64_t g = (N * mt + 255) / 256;
+    if (g > num_sms() * 8) g = num_sms() * 8;
+    add_shift_kernel<<<(unsigned)g, 256, 0, st>>>(out, in, N, mt, lam_dev.p);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  };
+  RefineStats rs;
+  KRR_TRY(refine_solve(ops, product64, N, mt, Y, alpha, tol, maxit, s, &rs));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = rs.iters;
+    info->outer_refinements = rs.outer;
+    info->rank = 0;
+    for (int q = 0; q < S; ++q)
+      if (factors && factors[q]) info->rank = std::max(info->rank, factors[q]->rank);
+    info->rel_residual = rs.relres;
+    info->kernel_entries = kmv_entries(N) * ((double)S * rs.products32 + (double)S * rs.products64);
+    info->t_build_s = t_build;
+    info->t_solve_s = seconds_since(t1);
+  }
+  if (rs.status == KRR_ENOCONV)
+    set_error("batched PCG did not reach the tolerance (%.3e > %.3e)", rs.relres, tol);
+  if (rs.status == KRR_EBREAKDOWN) set_error("batched PCG breakdown");
+  return rs.status;
 }
 
 // --------------------------------------------------------------- KRILL

@@ -149,3 +149,24 @@ def test_prediction(K, kern, N, Nt, d, m):
     np.testing.assert_allclose(got64, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
     got32 = K.krr_predict(to_dev(X), kern, 1.1, to_dev(alpha), to_dev(T), prec="mixed")
     assert np.all(np.abs(got32.cpu().numpy() - ref) <= 2e-5 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("N,d,ms", [(1, 2, 1), (777, 8, 2), (3001, 5, 2), (1500, 16, 1)])
+def test_batched_settings_product(K, N, d, ms):
+    """Eight (kernel, sigma) settings sharing the tile generation, each with
+    its own shifts; every block equals the single-setting oracle product."""
+    rng = np.random.default_rng(N + d)
+    means = 3.0 * rng.standard_normal((4, d))
+    X = means[rng.integers(0, 4, N)] + 0.5 * rng.standard_normal((N, d))
+    kerns = [O.MATERN52] * 4 + [O.LAPLACE_L1] * 3 + [O.GAUSSIAN]
+    sigmas = [0.5, 1.0, 2.0, 4.0, 0.5, 1.0, 2.0, 1.5]
+    S = len(kerns)
+    lams = rng.uniform(1e-3, 1.0, S * ms)
+    V = rng.standard_normal((S * ms, N))
+    got = K.krr_kmatvec_batched(X, kerns, sigmas, lams, V)
+    for q in range(S):
+        for c in range(ms):
+            col = q * ms + c
+            ref = O.kmatvec(X, kerns[q], sigmas[q], lams[col], V[col])
+            bound = O.kmatvec(X, kerns[q], sigmas[q], lams[col], np.abs(V[col]))
+            assert np.all(np.abs(got[col] - ref[0]) <= 2e-5 * bound[0]), (q, c)

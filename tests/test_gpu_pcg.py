@@ -125,3 +125,26 @@ def test_full_size_mixed_solve(K):
     assert info["status"] == "KRR_OK", info
     rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, alpha.cpu().numpy())
     assert rr.max() <= w.tol * 1.001
+
+
+def test_batched_settings_solve(K):
+    """Four (kernel, sigma) settings x two mu values on mixture data: every
+    one of the 8 systems meets the tolerance in the float64 residual the
+    oracle recomputes, and matches the single-setting solve."""
+    from inputs import make_c3_batched
+    w = make_c3_batched(n=4000, k=200)
+    settings = [(O.MATERN52, 1.0), (O.MATERN52, 2.0), (O.LAPLACE_L1, 1.0), (O.LAPLACE_L1, 4.0)]
+    mus = [1e-4, 1e-6]
+    kerns = [k for k, _ in settings]
+    sigmas = [s for _, s in settings]
+    factors = [K.krr_rpcholesky(w.X, k, s, w.k, 20, seed=q) for q, (k, s) in enumerate(settings)]
+    Y = np.repeat(w.Y, len(settings) * len(mus), axis=0)
+    alpha, info = K.krr_pcg_solve_batched(w.X, kerns, sigmas, factors, mus, Y, tol=1e-8)
+    assert info["status"] == "KRR_OK", info
+    for q, (k, sg) in enumerate(settings):
+        for c, mu in enumerate(mus):
+            col = q * len(mus) + c
+            rr = O.true_relres(w.X, k, sg, mu * w.N, Y[col:col + 1], alpha[col:col + 1])
+            assert rr.max() <= 1e-8, (q, c, rr)
+    one, _ = K.krr_pcg_solve(w.X, kerns[1], sigmas[1], Y[2:3], mus[0], factors[1], tol=1e-8)
+    assert rel_err(alpha[2], one[0]) < 1e-5
