@@ -137,7 +137,7 @@ __global__ void prepare_ff_kernel(const double *__restrict__ X, int64_t N, int d
 }
 
 krr_status prepare_points_ff(const double *Xd, int64_t N, int d, int kern, double sigma,
-                             cudaStream_t s, PointsFF &P) {
+                             cudaStream_t s, PointsFF &P, const double *mean_dev) {
   P.dp = (d + 3) / 4 * 4;
   P.d = d;
   P.N = N;
@@ -146,14 +146,18 @@ krr_status prepare_points_ff(const double *Xd, int64_t N, int d, int kern, doubl
   KRR_TRY(P.xl.alloc((size_t)N * P.dp, s));
   KRR_TRY(P.ch.alloc((size_t)N, s));
   KRR_TRY(P.cl.alloc((size_t)N, s));
-  DevBuf<double> mean;
-  KRR_TRY(mean.alloc(d, s));
-  column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, mean.p);
-  KRR_LAUNCH_CHECK();
+  KRR_TRY(P.mean.alloc(d, s));
+  if (mean_dev) {
+    KRR_CUDA_TRY(cudaMemcpyAsync(P.mean.p, mean_dev, sizeof(double) * d,
+                                 cudaMemcpyDeviceToDevice, s));
+  } else {
+    column_mean_kernel<<<d, 256, 0, s>>>(Xd, N, d, P.mean.p);
+    KRR_LAUNCH_CHECK();
+  }
   const double scale = (kern == KMATERN) ? std::sqrt(5.0) / sigma : 1.0 / sigma;
   const int with_norm = 0;   // the float-float distance uses direct differences
-  prepare_ff_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, mean.p, scale, with_norm,
-                                                     P.xh.p, P.xl.p, P.ch.p, P.cl.p);
+  prepare_ff_kernel<<<ceil_div(N, 256), 256, 0, s>>>(Xd, N, d, P.dp, P.mean.p, scale,
+                                                     with_norm, P.xh.p, P.xl.p, P.ch.p, P.cl.p);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
@@ -298,11 +302,14 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
   return KRR_OK;
 }
 
-krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv, int m,
-                  double *Y, int64_t ldy, cudaStream_t s, DevBuf<double> &part,
-                  DevBuf<float> &vsplit) {
-  const int64_t N = P.N;
-  if (N == 0 || m == 0) return KRR_OK;
+// Y (Nr x m) = K(R, P) V (+ lambda V when R is P and lambda != 0): the
+// float-float product between a row point set R and a column set P prepared
+// with the same centre and scale.
+krr_status kff_cross(const PointsFF &R, const PointsFF &P, double lambda, const double *V,
+                     int64_t ldv, int m, double *Y, int64_t ldy, cudaStream_t s,
+                     DevBuf<double> &part, DevBuf<float> &vsplit) {
+  const int64_t N = P.N, Nr = R.N;
+  if (N == 0 || Nr == 0 || m == 0) return KRR_OK;
   static const ExpFFConsts ec = make_exp_consts();
   if (vsplit.n < (size_t)2 * N * m) KRR_TRY(vsplit.alloc((size_t)2 * N * m, s));
   float *vh = vsplit.p, *vl = vsplit.p + (size_t)N * m;
@@ -312,19 +319,20 @@ krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv
     split_ff_kernel<<<(unsigned)g, 256, 0, s>>>(V, ldv, N, m, vh, vl);
     KRR_LAUNCH_CHECK();
   }
+  const bool square = (&R == &P);
   for (int c0 = 0; c0 < m; c0 += 16) {
     const int mg = (m - c0 < 16) ? (m - c0) : 16;
     const int M = pad_m(mg);
     const int rows = KFF_THREADS * kmvff_rows_per_thread(P.dp);
-    const int64_t row_tiles = (N + rows - 1) / rows;
+    const int64_t row_tiles = (Nr + rows - 1) / rows;
     const int splits = choose_splits(row_tiles, N, KFF_TJ, 4, 6);
     int64_t chunk = (N + splits - 1) / splits;
     chunk = (chunk + KFF_TJ - 1) / KFF_TJ * KFF_TJ;
     const int nsplit = (int)((N + chunk - 1) / chunk);
-    const size_t need = (size_t)nsplit * M * N;
+    const size_t need = (size_t)nsplit * M * Nr;
     if (part.n < need) KRR_TRY(part.alloc(need, s));
-    KmvFFArgs a{P.xh.p, P.xl.p, P.ch.p, P.cl.p, vh + (int64_t)c0 * N, vl + (int64_t)c0 * N,
-                N, mg, chunk, ec, part.p};
+    KmvFFArgs a{R.xh.p, R.xl.p, Nr, P.xh.p, P.xl.p, P.ch.p, P.cl.p, vh + (int64_t)c0 * N,
+                vl + (int64_t)c0 * N, N, mg, chunk, ec, part.p};
     KmvTimer tm(2);
     tm.begin(s);
     cudaError_t e = launch_kmvff_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
@@ -334,12 +342,18 @@ krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv
       set_error("float-float product launch failed: %s", cudaGetErrorString(e));
       return KRR_ECUDA;
     }
-    kmv_reduce_kernel<double, 16><<<ceil_div(N, 256), 256, 0, s>>>(
-        part.p, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
-        Y + (int64_t)c0 * ldy, ldy);
+    kmv_reduce_kernel<double, 16><<<ceil_div(Nr, 256), 256, 0, s>>>(
+        part.p, nsplit, M, Nr, mg, square ? lambda : 0.0,
+        square ? V + (int64_t)c0 * ldv : nullptr, ldv, Y + (int64_t)c0 * ldy, ldy);
     KRR_LAUNCH_CHECK();
   }
   return KRR_OK;
+}
+
+krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv, int m,
+                  double *Y, int64_t ldy, cudaStream_t s, DevBuf<double> &part,
+                  DevBuf<float> &vsplit) {
+  return kff_cross(P, P, lambda, V, ldv, m, Y, ldy, s, part, vsplit);
 }
 
 // Prediction products Y (Nr x m) = K(Xr, X) V, V N x m (no shift).

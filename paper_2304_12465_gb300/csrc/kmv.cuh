@@ -36,6 +36,7 @@ krr_status kcross_f64(const double *Xr, int64_t Nr, const double *Xd, int64_t N,
 struct PointsFF {
   DevBuf<float> xh, xl;   // N x dp
   DevBuf<float> ch, cl;   // N
+  DevBuf<double> mean;    // d
   int dp = 0;
   int d = 0;
   int64_t N = 0;
@@ -43,7 +44,13 @@ struct PointsFF {
 };
 
 krr_status prepare_points_ff(const double *Xd, int64_t N, int d, int kern, double sigma,
-                             cudaStream_t s, PointsFF &P);
+                             cudaStream_t s, PointsFF &P, const double *mean_dev = nullptr);
+
+// Rectangular float-float product Y (R.N x m) = K(R, P) V; when &R == &P the
+// shift lambda V is added (square product).
+krr_status kff_cross(const PointsFF &R, const PointsFF &P, double lambda, const double *V,
+                     int64_t ldv, int m, double *Y, int64_t ldy, cudaStream_t s,
+                     DevBuf<double> &part, DevBuf<float> &vsplit);
 
 // Y (float64) = (A + lambda I) V (float64) with float64-accurate kernel
 // entries computed in float-float arithmetic on the float32 pipes.

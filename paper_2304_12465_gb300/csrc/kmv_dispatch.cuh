@@ -101,6 +101,8 @@ cudaError_t launch_kmv64(int DP, int M, dim3 grid, cudaStream_t s, const Kmv64Ar
 }
 
 struct KmvFFArgs {
+  const float *rh, *rl;  // row points (== xh, xl for the square product)
+  int64_t Nr;
   const float *xh, *xl, *ch, *cl, *Vh, *Vl;
   int64_t N;
   int m;
@@ -114,9 +116,9 @@ cudaError_t launch_kmvff_m(int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a)
   switch (M) {
 #define KRR_CASE(MM)                                                                 \
   case MM:                                                                           \
-    kmvff_kernel<KERN, DP, MM><<<grid, KFF_THREADS, 0, s>>>(a.xh, a.xl, a.ch, a.cl, a.Vh, \
-                                                            a.Vl, a.N, a.m, a.chunk,    \
-                                                            a.ec, a.part);              \
+    kmvff_kernel<KERN, DP, MM><<<grid, KFF_THREADS, 0, s>>>(                             \
+        a.rh, a.rl, a.Nr, a.xh, a.xl, a.ch, a.cl, a.Vh, a.Vl, a.N, a.m, a.chunk, a.ec,  \
+        a.part);                                                                        \
     break;
     KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8) KRR_CASE(16)
 #undef KRR_CASE

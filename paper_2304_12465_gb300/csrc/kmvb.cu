@@ -81,7 +81,7 @@ krr_status kmv_batched_f32(const PointsF32 &P, int S, const int *kerns, const do
   const int MT = KMVB_MAX_SETTINGS * ms;
   const int rows = KMVB_THREADS * 2 * KMVB_RP;
   const int64_t row_tiles = (N + rows - 1) / rows;
-  int64_t target = (int64_t)num_sms() * 2 * 8;
+  int64_t target = (int64_t)num_sms() * 3 * 8;
   int64_t splits = (target + row_tiles - 1) / row_tiles;
   const int64_t maxs = (N + KMVB_TJ - 1) / KMVB_TJ;
   if (splits > maxs) splits = maxs;

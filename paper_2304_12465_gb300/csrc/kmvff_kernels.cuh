@@ -132,12 +132,14 @@ constexpr int KFF_TJ = 32;                // columns per shared tile
 // fit the register budget, one otherwise.
 __host__ __device__ constexpr int kmvff_rows_per_thread(int DP) { return DP <= 16 ? 2 : 1; }
 
-// xh, xl : N x DP  split prepared points; ch, cl: N split constants (not
-// used by the direct-difference distance).  Vh, Vl: m x N split RHS.
-// part: splits x M x N float64.
+// rh, rl : Nr x DP split row points (the column arrays for the square
+// product); xh, xl : N x DP split column points; ch, cl: N split constants
+// (not used by the direct-difference distance).  Vh, Vl: m x N split RHS.
+// part: splits x M x Nr float64.
 template <int KERN, int DP, int M>
 __global__ void __launch_bounds__(KFF_THREADS, 4)
-kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
+kmvff_kernel(const float *__restrict__ rh, const float *__restrict__ rl, int64_t Nr,
+             const float *__restrict__ xh, const float *__restrict__ xl,
              const float *__restrict__ ch, const float *__restrict__ cl,
              const float *__restrict__ Vh, const float *__restrict__ Vl, int64_t N, int m,
              int64_t chunk, ExpFFConsts ec, double *__restrict__ part) {
@@ -159,13 +161,13 @@ kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
 #pragma unroll
   for (int r = 0; r < KFF_RI; ++r) {
     const int64_t i = row0 + tid + (int64_t)r * KFF_THREADS;
-    const bool ok = i < N;
+    const bool ok = i < Nr;
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      ih[r][k] = ok ? xh[i * DP + k] : 0.0f;
-      il[r][k] = ok ? xl[i * DP + k] : 0.0f;
+      ih[r][k] = ok ? rh[i * DP + k] : 0.0f;
+      il[r][k] = ok ? rl[i * DP + k] : 0.0f;
     }
-    ic[r] = {ok ? ch[i] : 0.0f, ok ? cl[i] : 0.0f};
+    ic[r] = {0.0f, 0.0f};
 #pragma unroll
     for (int c = 0; c < M; ++c) acc[r][c] = {0.0f, 0.0f};
   }
@@ -262,14 +264,14 @@ kmvff_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
       }
     }
   }
-  double *out = part + (int64_t)blockIdx.y * M * N;
+  double *out = part + (int64_t)blockIdx.y * M * Nr;
 #pragma unroll
   for (int r = 0; r < KFF_RI; ++r) {
     const int64_t i = row0 + tid + (int64_t)r * KFF_THREADS;
-    if (i < N) {
+    if (i < Nr) {
 #pragma unroll
       for (int c = 0; c < M; ++c)
-        if (c < m) out[(int64_t)c * N + i] = (double)acc[r][c].h + (double)acc[r][c].l;
+        if (c < m) out[(int64_t)c * Nr + i] = (double)acc[r][c].h + (double)acc[r][c].l;
     }
   }
 }

@@ -6,7 +6,8 @@
 // sketch B = Phi A(:,S) gathered row by row with kernel entries regenerated
 // in float32; P = B^T B + H and its Cholesky factor in float64.
 // Solve: iterative refinement -- the right-hand side A(S,:) y and the outer
-// residuals use float64 kernel entries; the inner PCG on k-vectors (float64)
+// residuals use float64-accurate kernel entries (float-float arithmetic on the
+// float32 pipes); the inner PCG on k-vectors (float64)
 // uses a product that regenerates the N x k block A(:,S) twice per
 // application in float32 (u = A(:,S) beta, then A(S,:) u), with the
 // preconditioner W^T W, W = L^{-1}, P = L L^T.
@@ -352,80 +353,6 @@ __global__ void krows_reduce_kernel(const double *__restrict__ part, int nch, in
   out[e] = acc;
 }
 
-// float64 versions (direct differences, float64 exp) used for the right-hand
-// side and the refinement residual.
-// u[c][n] = sum_l kappa(x_n, x_{S_l}) beta[c][l]
-template <int M>
-__global__ void __launch_bounds__(128)
-kcols64_kernel(const double *__restrict__ X, int d, int64_t N, int kern, double sigma,
-               const int64_t *__restrict__ S, int k, const double *__restrict__ beta, int m,
-               double *__restrict__ u) {
-  constexpr int TL = 64;
-  __shared__ double sx[TL * 32];
-  __shared__ double sb[TL][M];
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double xn[32];
-  for (int q = 0; q < d; ++q) xn[q] = (n < N) ? X[n * d + q] : 0.0;
-  double acc[M];
-#pragma unroll
-  for (int c = 0; c < M; ++c) acc[c] = 0.0;
-  for (int l0 = 0; l0 < k; l0 += TL) {
-    const int nl = min(TL, k - l0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nl * d; idx += blockDim.x)
-      sx[idx] = X[S[l0 + idx / d] * d + idx % d];
-    for (int idx = threadIdx.x; idx < TL * M; idx += blockDim.x) {
-      const int l = idx / M, c = idx % M;
-      sb[l][c] = (l < nl && c < m) ? beta[(int64_t)c * k + l0 + l] : 0.0;
-    }
-    __syncthreads();
-    for (int l = 0; l < nl; ++l) {
-      const double kv = kappa_point_f64(xn, sx + l * d, d, kern, sigma);
-#pragma unroll
-      for (int c = 0; c < M; ++c) acc[c] = fma(kv, sb[l][c], acc[c]);
-    }
-  }
-  if (n < N)
-    for (int c = 0; c < m; ++c) u[(int64_t)c * N + n] = acc[c];
-}
-
-// part[ch][c][l] = sum_{n in chunk ch} kappa(x_{S_l}, x_n) u[c][n]
-template <int M>
-__global__ void __launch_bounds__(128)
-krows64_kernel(const double *__restrict__ X, int d, int64_t N, int kern, double sigma,
-               const int64_t *__restrict__ S, int k, const double *__restrict__ u, int m,
-               double *__restrict__ part) {
-  constexpr int TN = 64;
-  __shared__ double sx[TN * 32];
-  __shared__ double su[TN][M];
-  const int l = blockIdx.y * blockDim.x + threadIdx.x;
-  const int64_t n_begin = (int64_t)blockIdx.x * KR_CHUNK;
-  const int64_t n_end = min(N, n_begin + KR_CHUNK);
-  double xl[32];
-  for (int q = 0; q < d; ++q) xl[q] = (l < k) ? X[S[l] * d + q] : 0.0;
-  double acc[M];
-#pragma unroll
-  for (int c = 0; c < M; ++c) acc[c] = 0.0;
-  for (int64_t n0 = n_begin; n0 < n_end; n0 += TN) {
-    const int nn = (int)min((int64_t)TN, n_end - n0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nn * d; idx += blockDim.x)
-      sx[idx] = X[(n0 + idx / d) * d + idx % d];
-    for (int idx = threadIdx.x; idx < TN * M; idx += blockDim.x) {
-      const int e = idx % TN, c = idx / TN;
-      su[e][c] = (e < nn && c < m) ? u[(int64_t)c * N + n0 + e] : 0.0;
-    }
-    __syncthreads();
-    for (int e = 0; e < nn; ++e) {
-      const double kv = kappa_point_f64(xl, sx + e * d, d, kern, sigma);
-#pragma unroll
-      for (int c = 0; c < M; ++c) acc[c] = fma(kv, su[e][c], acc[c]);
-    }
-  }
-  if (l < k)
-    for (int c = 0; c < m; ++c) part[((int64_t)blockIdx.x * m + c) * k + l] = acc[c];
-}
-
 // y[c][i] = H[i, :] beta[c] + add[c][i]   (H symmetric, one warp per row)
 __global__ void sym_gemv_add_kernel(const double *__restrict__ H, int k,
                                     const double *__restrict__ beta, int m,
@@ -497,35 +424,6 @@ krr_status krill_krows(const krill_precond *P, const float *u, int m, double *ou
     krows_kernel<KERN, DP, M><<<grid, 256, 0, s>>>(P->xt, P->cn, P->N, P->S, P->k, u, m,
                                                    part.p);
   })));
-  KRR_LAUNCH_CHECK();
-  krows_reduce_kernel<<<ceil_div((int64_t)P->k * m, 256), 256, 0, s>>>(part.p, nch, P->k, m,
-                                                                     out);
-  KRR_LAUNCH_CHECK();
-  return KRR_OK;
-}
-
-krr_status krill_kcols64(const krill_precond *P, const double *beta, int m, double *u,
-                         cudaStream_t s) {
-  const int M = pad_m_krill(m);
-  KRR_M_SWITCH(M, {
-    kcols64_kernel<M><<<ceil_div(P->N, 128), 128, 0, s>>>(P->X, P->d, P->N, P->kern, P->sigma,
-                                                          P->S, P->k, beta, m, u);
-  });
-  KRR_LAUNCH_CHECK();
-  return KRR_OK;
-}
-
-krr_status krill_krows64(const krill_precond *P, const double *u, int m, double *out,
-                         cudaStream_t s) {
-  const int M = pad_m_krill(m);
-  const int nch = ceil_div(P->N, KR_CHUNK);
-  DevBuf<double> part;
-  KRR_TRY(part.alloc((size_t)nch * P->k * m, s));
-  dim3 grid(nch, ceil_div(P->k, 128));
-  KRR_M_SWITCH(M, {
-    krows64_kernel<M><<<grid, 128, 0, s>>>(P->X, P->d, P->N, P->kern, P->sigma, P->S, P->k, u,
-                                           m, part.p);
-  });
   KRR_LAUNCH_CHECK();
   krows_reduce_kernel<<<ceil_div((int64_t)P->k * m, 256), 256, 0, s>>>(part.p, nch, P->k, m,
                                                                      out);
@@ -640,18 +538,41 @@ krr_status krill_precond_apply(const krill_precond *P, const double *in, int m, 
   return KRR_OK;
 }
 
-// Right-hand side A(S,:) y, y N x m float64 (float64 kernel entries).
-krr_status krill_rhs(const krill_precond *P, const double *y, int m, double *b, cudaStream_t s) {
-  return krill_krows64(P, y, m, b, s);
+__global__ void gather_points_kernel(const double *__restrict__ X, int d,
+                                     const int64_t *__restrict__ S, int k,
+                                     double *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * d) return;
+  out[e] = X[S[e / d] * d + e % d];
 }
 
-// float64 product M beta = A(S,:)(A(:,S) beta) + H beta for the refinement.
-krr_status krill_product64(const krill_precond *P, const double *beta, int m, double *out,
-                           cudaStream_t s, DevBuf<double> &u, DevBuf<double> &v) {
+// float-float point sets of a solve: all points and the centers, split with
+// the same centre and scale.
+krr_status krill_points_ff(const krill_precond *P, cudaStream_t s, KrillFF &Q) {
+  KRR_TRY(prepare_points_ff(P->X, P->N, P->d, P->kern, P->sigma, s, Q.all));
+  DevBuf<double> xc;
+  KRR_TRY(xc.alloc((size_t)P->k * P->d, s));
+  gather_points_kernel<<<ceil_div((int64_t)P->k * P->d, 256), 256, 0, s>>>(P->X, P->d, P->S,
+                                                                          P->k, xc.p);
+  KRR_LAUNCH_CHECK();
+  KRR_TRY(prepare_points_ff(xc.p, P->k, P->d, P->kern, P->sigma, s, Q.centers, Q.all.mean.p));
+  return KRR_OK;
+}
+
+// Right-hand side A(S,:) y, y N x m float64, float64-accurate (float-float).
+krr_status krill_rhs(const krill_precond *P, KrillFF &Q, const double *y, int m, double *b,
+                     cudaStream_t s) {
+  return kff_cross(Q.centers, Q.all, 0.0, y, P->N, m, b, P->k, s, Q.part, Q.vsplit);
+}
+
+// float64-accurate product M beta = A(S,:)(A(:,S) beta) + H beta for the
+// refinement residual (float-float block products).
+krr_status krill_product64(const krill_precond *P, KrillFF &Q, const double *beta, int m,
+                           double *out, cudaStream_t s, DevBuf<double> &u, DevBuf<double> &v) {
   if (u.n < (size_t)P->N * m) KRR_TRY(u.alloc((size_t)P->N * m, s));
   if (v.n < (size_t)P->k * m) KRR_TRY(v.alloc((size_t)P->k * m, s));
-  KRR_TRY(krill_kcols64(P, beta, m, u.p, s));
-  KRR_TRY(krill_krows64(P, u.p, m, v.p, s));
+  KRR_TRY(kff_cross(Q.all, Q.centers, 0.0, beta, P->k, m, u.p, P->N, s, Q.part, Q.vsplit));
+  KRR_TRY(kff_cross(Q.centers, Q.all, 0.0, u.p, P->N, m, v.p, P->k, s, Q.part, Q.vsplit));
   sym_gemv_add_kernel<<<ceil_div(P->k, 8), 256, 0, s>>>(P->H, P->k, beta, m, v.p, out);
   KRR_LAUNCH_CHECK();
   return KRR_OK;

@@ -330,7 +330,9 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
   KRR_TRY(r.alloc((size_t)k * m, s));
   KRR_TRY(dx.alloc((size_t)k * m, s));
   KRR_TRY(mx.alloc((size_t)k * m, s));
-  KRR_TRY(krill_rhs(P, Y, m, b.p, s));
+  KrillFF Q;
+  KRR_TRY(krill_points_ff(P, s, Q));
+  KRR_TRY(krill_rhs(P, Q, Y, m, b.p, s));
   double entries = (double)P->N * k;
   DevBuf<float> u;
   DevBuf<double> v;
@@ -371,7 +373,7 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
     entries += 2.0 * (double)P->N * k * st.products;
     add_f64_kernel<<<ceil_div((int64_t)k * m, 256), 256, 0, s>>>(beta, dx.p, (int64_t)k * m);
     KRR_LAUNCH_CHECK();
-    KRR_TRY(krill_product64(P, beta, m, mx.p, s, u64, v64));
+    KRR_TRY(krill_product64(P, Q, beta, m, mx.p, s, u64, v64));
     entries += 2.0 * (double)P->N * k;
     axpy_sub_kernel<<<ceil_div((int64_t)k * m, 256), 256, 0, s>>>(b.p, mx.p, r.p, (int64_t)k * m);
     KRR_LAUNCH_CHECK();
