@@ -310,6 +310,109 @@ KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
                                            krr_kernel kern, double sigma, double lambda,
                                            const double *V, int m, double *Y, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving engine: continuous batching of Alg. 1 solves (the paper solves one */
+/* problem at a time; this is the serving layer around the same method).     */
+/*                                                                            */
+/* A request is one mixed-precision krr_pcg_solve with its own RPCholesky     */
+/* factor: (A + mu N I) alpha = Y for points X (N x d, row-major float64),    */
+/* kernel kern with bandwidth sigma, Y with m columns (m x N, column c at     */
+/* Y + c N), RPCholesky rank k (Alg. 3, block min(100, ceil(k/10)), seed),    */
+/* tolerance tol on the float64-accurate relative residual of every column    */
+/* and at most maxit inner PCG iterations over all refinements.               */
+/*                                                                            */
+/* Requests wait in a queue and are admitted in arrival order while a slot is */
+/* free and the sum of the admitted requests' estimated footprints           */
+/* (krr_server_footprint) stays within the server's HBM budget.  A builder    */
+/* thread with its own stream copies X and Y to the device and builds the     */
+/* factor, the Woodbury core and the prepared points; the solve then keeps    */
+/* them and its CG state resident.  Each krr_server_step advances the inner   */
+/* PCG iteration of every iterating request by iters_per_step iterations,     */
+/* one grouped launch per phase for all of them (replayed as one CUDA graph   */
+/* when use_graph is set), while inner-solve starts, float-float refinement   */
+/* residuals and result copies run on per-slot streams.  A result does not    */
+/* depend on which other requests are being served: every per-request work    */
+/* decomposition and sum order is fixed by that request alone.                */
+/*                                                                            */
+/* Ownership: X, Y and alpha_out (m x N float64, host or device memory) stay  */
+/* owned by the caller and must stay valid until the request is reported by   */
+/* krr_server_poll (or the server is destroyed, which abandons unfinished     */
+/* requests).  alpha_out is written once, when the request finishes.  Device */
+/* arrays must hold their data when submitted: the server reads them later   */
+/* on its own streams, without waiting on the caller's.                       */
+/* Threading: one host thread at a time may call a server's functions.        */
+/* ------------------------------------------------------------------------ */
+#define KRR_SERVE_MAX_SLOTS 64
+
+typedef struct krr_server krr_server;
+
+typedef struct {
+  int max_slots;            /* concurrent requests, 1..KRR_SERVE_MAX_SLOTS    */
+  int iters_per_step;       /* inner PCG iterations per step, 1..64           */
+  int use_graph;            /* replay each step as one CUDA graph launch      */
+  int reserved;             /* must be 0                                      */
+  double hbm_budget_bytes;  /* admission budget; 0: 90% of the free HBM at    */
+                            /* creation                                       */
+} krr_server_config;
+
+typedef struct {
+  int64_t id;               /* from krr_server_submit                         */
+  krr_status status;        /* KRR_OK, KRR_ENOCONV, KRR_EBREAKDOWN, or the    */
+                            /* error of a failed build (KRR_ENOMEM, ...)      */
+  int iters;                /* inner PCG iterations over all refinements      */
+  int outer_refinements;
+  int rank;                 /* RPCholesky rank                                */
+  int m;
+  double rel_residual;      /* worst column's relative residual, float64-     */
+                            /* accurate product                               */
+  double kernel_entries;    /* kernel entries evaluated by this request       */
+  double t_submit, t_admit, t_built, t_done;   /* seconds on krr_server_clock */
+} krr_request_result;
+
+typedef struct {
+  int64_t submitted, completed, queued, admitted;   /* request counts         */
+  int64_t steps;            /* steps launched                                 */
+  int64_t step_kernels;     /* kernels those steps launched                   */
+  int max_concurrent;       /* most requests iterating in one step            */
+  int reserved;
+  double reserved_bytes;    /* footprint of the admitted requests             */
+  double peak_reserved_bytes;
+  double budget_bytes;
+  double kernel_entries;    /* over the completed requests                    */
+} krr_server_stats;
+
+/* Estimated peak device bytes of one request (host-only; no GPU needed).     */
+KRR_API krr_status krr_server_footprint(int64_t N, int d, int m, int k, double *bytes);
+
+/* Creates a server on the current device (streams, a builder thread, the     */
+/* device tables).  KRR_EINVAL for a config outside the documented ranges.    */
+KRR_API krr_status krr_server_create(const krr_server_config *cfg, krr_server **out);
+
+/* Queues a request (see above); returns at once.  N <= 2^26, 1 <= d <= 32,   */
+/* 1 <= m <= 16, 0 <= k <= min(N, 4096), 0 < tol < 1, maxit >= 1.            */
+/* KRR_ENOMEM (not queued) when the request alone exceeds the budget.         */
+KRR_API krr_status krr_server_submit(krr_server *S, const double *X, int64_t N, int d,
+                                     krr_kernel kern, double sigma, const double *Y, int m,
+                                     double mu, int k, uint64_t seed, double tol, int maxit,
+                                     double *alpha_out, int64_t *id_out);
+
+/* Admits what fits, takes finished builds and slot events, and runs one step */
+/* for the iterating requests (returns when that step's status is back).      */
+/* *unfinished (optional): queued plus admitted requests not yet reported.    */
+KRR_API krr_status krr_server_step(krr_server *S, int64_t *unfinished);
+
+/* Copies up to max_results finished requests (each reported once).           */
+KRR_API krr_status krr_server_poll(krr_server *S, krr_request_result *out, int max_results,
+                                   int *n_out);
+
+KRR_API krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *out);
+
+/* Seconds since the server was created (the clock of the result times).      */
+KRR_API double krr_server_clock(const krr_server *S);
+
+/* Waits for the device, stops the builder and frees everything.              */
+KRR_API void krr_server_destroy(krr_server *S);
+
 /* Timing instrumentation: while on (non-zero), solves record CUDA events
  * around every fused-product launch on the caller's stream and report the
  * summed device time in krr_info.kmv_ms / kmv_launches. */

@@ -10,6 +10,7 @@ from .synthetic import (  # noqa: F401
     make_c2_mixed,
     make_c3_batched,
     make_c4_krill,
+    make_serving_request,
     make_serving_stream,
     uniform_centers,
     WORKLOADS,

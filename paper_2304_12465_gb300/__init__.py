@@ -9,6 +9,7 @@ implementation: without the built library (and a GPU) every call fails.
 from .api import (  # noqa: F401
     Factor,
     KrillPreconditioner,
+    KrrServer,
     krill_build,
     krill_solve,
     krr_kmatvec,
@@ -20,6 +21,7 @@ from .api import (  # noqa: F401
     krr_precond_apply,
     krr_rpc_sample,
     krr_rpcholesky,
+    krr_server_footprint,
     krr_set_profiling,
     krr_sparse_sign,
     krr_version,

@@ -34,6 +34,33 @@ class KrrInfo(C.Structure):
                 if not name.startswith("reserved")}
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("iters_per_step", C.c_int), ("use_graph", C.c_int),
+                ("reserved", C.c_int), ("hbm_budget_bytes", C.c_double)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("iters", C.c_int),
+                ("outer_refinements", C.c_int), ("rank", C.c_int), ("m", C.c_int),
+                ("rel_residual", C.c_double), ("kernel_entries", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_built", C.c_double),
+                ("t_done", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
+                ("admitted", C.c_int64), ("steps", C.c_int64), ("step_kernels", C.c_int64),
+                ("max_concurrent", C.c_int), ("reserved", C.c_int),
+                ("reserved_bytes", C.c_double), ("peak_reserved_bytes", C.c_double),
+                ("budget_bytes", C.c_double), ("kernel_entries", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
 class KrrError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -66,6 +93,15 @@ SIGNATURES = {
     "krill_export": (_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(_int)]),
     "krill_solve": (_int, [_vp, _vp, _int, _dbl, _int, _vp, _vp, C.POINTER(KrrInfo)]),
     "krill_free": (None, [_vp]),
+    "krr_server_footprint": (_int, [_i64, _int, _int, _int, C.POINTER(_dbl)]),
+    "krr_server_create": (_int, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
+    "krr_server_submit": (_int, [_vp, _vp, _i64, _int, _int, _dbl, _vp, _int, _dbl, _int, _u64,
+                                 _dbl, _int, _vp, C.POINTER(_i64)]),
+    "krr_server_step": (_int, [_vp, C.POINTER(_i64)]),
+    "krr_server_poll": (_int, [_vp, C.POINTER(RequestResult), _int, C.POINTER(_int)]),
+    "krr_server_get_stats": (_int, [_vp, C.POINTER(ServerStats)]),
+    "krr_server_clock": (_dbl, [_vp]),
+    "krr_server_destroy": (None, [_vp]),
     "krr_set_profiling": (None, [_int]),
     "krr_last_error": (C.c_char_p, []),
     "krr_version": (C.c_char_p, []),

@@ -362,3 +362,112 @@ def krr_version() -> str:
 
 def krr_launch_count() -> int:
     return int(load().krr_launch_count())
+
+
+# --------------------------------------------------------------- serving
+def krr_server_footprint(N: int, d: int, m: int, k: int) -> float:
+    """Estimated peak device bytes of one served request (host-only)."""
+    b = C.c_double()
+    check(load().krr_server_footprint(int(N), int(d), int(m), int(k), C.byref(b)),
+          "krr_server_footprint")
+    return b.value
+
+
+class KrrServer:
+    """The krr_server_* calls: continuous batching of Alg. 1 solves.
+
+    submit() queues a request and returns its id; step() advances the engine
+    once; poll() returns finished requests as dicts holding the result fields
+    of krr_request_result plus 'alpha' (m, N) and the status name.  The
+    binding keeps each request's arrays alive until poll() reports it.
+    """
+
+    def __init__(self, max_slots: int = 16, iters_per_step: int = 4, use_graph: bool = True,
+                 hbm_budget_bytes: float = 0.0):
+        lib = load()
+        cfg = N_.ServerConfig(int(max_slots), int(iters_per_step), 1 if use_graph else 0, 0,
+                              float(hbm_budget_bytes))
+        h = C.c_void_p()
+        check(lib.krr_server_create(C.byref(cfg), C.byref(h)), "krr_server_create")
+        self._h = h
+        self._keep = {}
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server destroyed")
+        return self._h
+
+    def submit(self, X, kern, sigma: float, Y, mu: float, k: int, tol: float = 1e-6,
+               maxit: int = 1000, seed: int = 0, out=None) -> int:
+        lib = load()
+        Xk, Xp = _arr(X)
+        Yk, Yp = _arr(Y)
+        Nn, d = Xk.shape
+        m = _shape2(Yk)[0]
+        if out is None:
+            A, Ap = _empty_like_container(Y, (m, Nn))
+        else:
+            A, Ap = out, C.c_void_p(out.data_ptr() if _is_torch(out) else out.ctypes.data)
+        rid = C.c_int64()
+        check(lib.krr_server_submit(self.handle, Xp, Nn, d, _kern(kern), float(sigma), Yp, m,
+                                    float(mu), int(k), int(seed), float(tol), int(maxit), Ap,
+                                    C.byref(rid)), "krr_server_submit")
+        self._keep[rid.value] = (Xk, Yk, A)
+        return rid.value
+
+    def step(self) -> int:
+        """One engine step; returns the number of unfinished requests."""
+        n = C.c_int64()
+        check(load().krr_server_step(self.handle, C.byref(n)), "krr_server_step")
+        return n.value
+
+    def poll(self):
+        lib = load()
+        out = []
+        buf = (N_.RequestResult * 64)()
+        while True:
+            n = C.c_int()
+            check(lib.krr_server_poll(self.handle, buf, 64, C.byref(n)), "krr_server_poll")
+            for i in range(n.value):
+                r = buf[i].as_dict()
+                r["status_name"] = N_.STATUS_NAMES[r["status"]]
+                r["alpha"] = self._keep.pop(r["id"])[2]
+                out.append(r)
+            if n.value < 64:
+                return out
+
+    def drain(self):
+        """Steps until every submitted request has finished; returns them."""
+        done = []
+        while True:
+            left = self.step()
+            done += self.poll()
+            if left == 0:
+                return done + self.poll()
+
+    def stats(self) -> dict:
+        st = N_.ServerStats()
+        check(load().krr_server_get_stats(self.handle, C.byref(st)), "krr_server_get_stats")
+        return st.as_dict()
+
+    def clock(self) -> float:
+        return float(load().krr_server_clock(self.handle))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().krr_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -29,6 +29,10 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_error.clear(); }
 
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
+cudaStream_t alloc_stream() { return g_alloc_stream; }
+
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -42,6 +46,7 @@ bool is_device_ptr(const void *p) {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int num_sms() {
   static int cached = 0;
@@ -153,13 +158,13 @@ static bool valid_kernel(int kern) {
 
 void free_factor(krr_factor *f) {
   if (!f) return;
-  cudaFree(f->F);
-  cudaFree(f->S);
-  cudaFree(f->dres);
+  dev_free(f->F, f->free_stream);
+  dev_free(f->S, f->free_stream);
+  dev_free(f->dres, f->free_stream);
   for (auto &c : f->cores) {
-    cudaFree(c.W);
-    cudaFree(c.Wt);
-    cudaFree(c.F32);
+    dev_free(c.W, f->free_stream);
+    dev_free(c.Wt, f->free_stream);
+    dev_free(c.F32, f->free_stream);
   }
   delete f;
 }

@@ -28,6 +28,7 @@ void clear_error();
 
 // Counts this library's kernel launches (reported by krr_launch_count).
 void count_launch();
+void count_launches(unsigned long long n);
 
 #define KRR_LAUNCH_CHECK()          \
   do {                              \
@@ -76,13 +77,31 @@ struct DevBuf {
   T *get() const { return p; }
 };
 
+// Stream for the persistent allocations made by this host thread (null:
+// plain cudaMalloc).  A thread that builds handles while other streams keep
+// the device busy (the serving engine's builder) sets it, so that neither the
+// allocations nor the later frees synchronise the device.
+void set_alloc_stream(cudaStream_t s);
+cudaStream_t alloc_stream();
+
 // Persistent device memory owned by a handle.
 template <typename T>
 krr_status dev_alloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) return KRR_OK;
-  KRR_CUDA_TRY(cudaMalloc((void **)p, count * sizeof(T)));
+  cudaStream_t s = alloc_stream();
+  if (s) KRR_CUDA_TRY(cudaMallocAsync((void **)p, count * sizeof(T), s));
+  else KRR_CUDA_TRY(cudaMalloc((void **)p, count * sizeof(T)));
   return KRR_OK;
+}
+
+// Frees handle memory: stream-ordered on free_stream when the handle was
+// built with an allocation stream (the owner has already seen every use
+// complete), otherwise cudaFree.
+inline void dev_free(void *p, cudaStream_t free_stream) {
+  if (!p) return;
+  if (free_stream) cudaFreeAsync(p, free_stream);
+  else cudaFree(p);
 }
 
 bool is_device_ptr(const void *p);

@@ -37,6 +37,9 @@ struct krr_factor {
   double *F = nullptr;      // N x k column-major (first `rank` columns valid)
   int64_t *S = nullptr;     // pivots, column order
   double *dres = nullptr;   // residual diagonal
+  // non-null when the factor was built with a thread allocation stream: its
+  // memory is then released with cudaFreeAsync on this stream
+  cudaStream_t free_stream = nullptr;
   mutable std::mutex mtx;
   // a deque keeps the address of every core stable while more are added, so
   // pointers handed out by nystrom_core stay valid for the factor's lifetime

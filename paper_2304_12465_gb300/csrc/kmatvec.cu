@@ -79,8 +79,9 @@ __global__ void prepare_f32_kernel(const double *__restrict__ X, int64_t N, int 
 }
 
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern, double sigma,
-                              cudaStream_t s, PointsF32 &P, const double *mean_dev) {
-  P.dp = (d + 3) / 4 * 4;
+                              cudaStream_t s, PointsF32 &P, const double *mean_dev, int dp) {
+  P.dp = dp > 0 ? dp : (d + 3) / 4 * 4;
+  KRR_REQUIRE(P.dp >= d && P.dp % 4 == 0 && P.dp <= 32, "bad padded dimension %d", P.dp);
   P.d = d;
   P.N = N;
   P.kern = kern;

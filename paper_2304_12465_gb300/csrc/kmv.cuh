@@ -20,9 +20,11 @@ struct PointsF32 {
 
 // mean_dev (optional, d doubles on the device): centre to use instead of the
 // points' own mean (prediction prepares test points with the training mean).
+// dp (optional): padded dimension (a multiple of 4 in [d, 32]) instead of the
+// smallest multiple of 4 >= d.
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
                               double sigma, cudaStream_t s, PointsF32 &P,
-                              const double *mean_dev = nullptr);
+                              const double *mean_dev = nullptr, int dp = 0);
 
 // Prediction products (no shift): Y (Nr x m) = K(rows, columns) V.
 krr_status kcross_f32(const PointsF32 &R, const PointsF32 &P, const float *V, int64_t ldv,

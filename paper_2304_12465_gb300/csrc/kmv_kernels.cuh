@@ -64,6 +64,12 @@ __device__ __forceinline__ float kappa_f32(float acc) {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Shared memory of one float32 product tile: two column tiles of points
+// (DP), right-hand sides (M rounded up to even) and per-point constants.
+__host__ __device__ constexpr int kmv32_smem_bytes(int DP, int M) {
+  return 2 * KMV_TJ * (DP + (M + 1) / 2 * 2 + 1) * (int)sizeof(float2);
+}
+
 // ------------------------------------------------------------------ f32
 // xr, cr : Nr x DP, Nr  prepared row points and constants (the same arrays as
 //          xt, cn for the square product; test points for prediction)
@@ -71,24 +77,30 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // cn : N        per-point constant (c above; unused for Laplace)
 // V  : m x ldv  right-hand sides (column c at V + c*ldv), float32
 // part: splits x M x Nr partial products
+// One (row tile, column split) work item of the float32 product; the
+// single-problem kernel maps it from blockIdx, the grouped serving kernel
+// from its work list.
 template <int KERN, int DP, int M>
-__global__ void __launch_bounds__(KMV_THREADS, 2)
-kmv32_kernel(const float *__restrict__ xr, const float *__restrict__ cr, int64_t Nr,
-             const float *__restrict__ xt, const float *__restrict__ cn,
-             const float *__restrict__ V, int64_t ldv, int64_t N, int m,
-             int64_t chunk, float *__restrict__ part) {
+__device__ __forceinline__ void
+kmv32_tile(const float *__restrict__ xr, const float *__restrict__ cr, int64_t Nr,
+           const float *__restrict__ xt, const float *__restrict__ cn,
+           const float *__restrict__ V, int64_t ldv, int64_t N, int m, int64_t chunk,
+           float *__restrict__ part, int64_t row_tile, int64_t split,
+           unsigned char *__restrict__ smem) {
   static_assert(DP % 4 == 0, "DP must be a multiple of 4");
   constexpr int RI = kmv32_rows_per_thread(DP, M);
   constexpr int RP = RI / 2;                      // row pairs per thread
   constexpr int MP = (M + 1) / 2 * 2;             // even number of columns
   constexpr int ROWS = KMV_THREADS * RI;          // rows per CTA
-  __shared__ __align__(16) float2 sx[2][KMV_TJ][DP];   // {x_jk, x_jk} (Laplace: -x_jk)
-  __shared__ __align__(16) float2 sv[2][KMV_TJ][MP];   // {v_jc, v_jc}
-  __shared__ __align__(16) float2 sc[2][KMV_TJ];       // {c_j, c_j}
+  // double-buffered column tiles, carved from the caller's shared buffer of
+  // kmv32_smem_bytes(DP, M) bytes (16-byte aligned)
+  auto sx = reinterpret_cast<float2 (*)[KMV_TJ][DP]>(smem);   // {x_jk, x_jk} (Laplace: -x_jk)
+  auto sv = reinterpret_cast<float2 (*)[KMV_TJ][MP]>(smem + 2 * KMV_TJ * DP * sizeof(float2));
+  auto sc = reinterpret_cast<float2 (*)[KMV_TJ]>(smem + 2 * KMV_TJ * (DP + MP) * sizeof(float2));
 
   const int tid = threadIdx.x;
-  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
-  const int64_t j_begin = (int64_t)blockIdx.y * chunk;
+  const int64_t row0 = row_tile * ROWS;
+  const int64_t j_begin = split * chunk;
   const int64_t j_end = min(N, j_begin + chunk);
 
   // rows of this thread: row0 + tid + 256 r, paired (r = 2p, 2p + 1)
@@ -213,7 +225,7 @@ kmv32_kernel(const float *__restrict__ xr, const float *__restrict__ cr, int64_t
     buf ^= 1;
   }
 
-  float *out = part + (int64_t)blockIdx.y * M * Nr;
+  float *out = part + split * M * Nr;
 #pragma unroll
   for (int p = 0; p < RP; ++p) {
     const int64_t ra = row0 + tid + (int64_t)(2 * p) * KMV_THREADS;
@@ -227,6 +239,18 @@ kmv32_kernel(const float *__restrict__ xr, const float *__restrict__ cr, int64_t
     }
   }
 }
+
+template <int KERN, int DP, int M>
+__global__ void __launch_bounds__(KMV_THREADS, 2)
+kmv32_kernel(const float *__restrict__ xr, const float *__restrict__ cr, int64_t Nr,
+             const float *__restrict__ xt, const float *__restrict__ cn,
+             const float *__restrict__ V, int64_t ldv, int64_t N, int m,
+             int64_t chunk, float *__restrict__ part) {
+  __shared__ __align__(16) unsigned char smem[kmv32_smem_bytes(DP, M)];
+  kmv32_tile<KERN, DP, M>(xr, cr, Nr, xt, cn, V, ldv, N, m, chunk, part, blockIdx.x,
+                          blockIdx.y, smem);
+}
+
 
 // ------------------------------------------------------------------ f64
 // Direct coordinate differences and the CUDA float64 exp, as in the

@@ -229,7 +229,7 @@ krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s
     KRR_TRY(add_diagonal(Gm.p, r, r, c.lambda, s));
     krr_status st = potrf_lower(Gm.p, r, r, s);
     if (st != KRR_OK) {
-      if (c.F32) cudaFree(c.F32);
+      dev_free(c.F32, f->free_stream);
       return st;
     }
     KRR_TRY(dev_alloc(&c.W, (size_t)r * r));

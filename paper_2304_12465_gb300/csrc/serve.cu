@@ -1,0 +1,1297 @@
+// Serving engine: continuous batching of Alg. 1 solves on one GPU.
+//
+// Requests are admitted in arrival order while their estimated device
+// footprint fits the HBM budget and a slot is free.  A builder thread (its own
+// low-priority stream) copies X and Y to the device, runs RPCholesky (Alg. 3),
+// factors the mixed-precision Woodbury core and prepares the points.  The solve
+// then follows the mixed-precision refinement of the single-solve driver:
+// x = 0, r = y; repeat { float32 PCG on M d = r to a loose per-column
+// tolerance; x += d; r = y - M x with the float-float product } until every
+// column's relative residual is <= tol.  The inner PCG iterations of all
+// iterating slots advance together, one grouped launch per phase (serve.cuh);
+// inner-solve set-up and refinement residuals run on each slot's own stream,
+// so they overlap with the other slots' iterations.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstddef>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kmv.cuh"
+#include "kmv_kernels.cuh"
+#include "pcg.cuh"
+#include "rpc.cuh"
+#include "serve.cuh"
+
+namespace krr {
+
+// ======================================================= device kernels
+constexpr int SERVE_COL_THREADS = 1024;   // single-CTA per-column kernels
+constexpr int SERVE_KERNELS_PER_ITER = 12;
+
+// Fixed-order sum of a column's block partials by one warp (lane-strided,
+// then a butterfly whose result is the same in every lane).
+__device__ __forceinline__ double serve_col_sum(const double *part, int nbv, int c,
+                                                int lane) {
+  double acc = 0.0;
+  for (int b = lane; b < nbv; b += 32) acc += part[(int64_t)c * nbv + b];
+  return warp_sum(acc);
+}
+
+// Block partial of one column: every thread passes its value, the warp sums
+// go to red[warp][c]; serve_block_flush then writes out[c * nbv + b].
+__device__ __forceinline__ void serve_block_put(double (*red)[SERVE_MAX_M], int c, double v) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+}
+
+__device__ __forceinline__ void serve_block_flush(double (*red)[SERVE_MAX_M], int m,
+                                                  double *out, int nbv, int b) {
+  __syncthreads();
+  if ((int)threadIdx.x < m) {
+    double t = 0.0;
+    for (int w = 0; w < SERVE_VB / 32; ++w) t += red[w][threadIdx.x];
+    out[(int64_t)threadIdx.x * nbv + b] = t;
+  }
+  __syncthreads();
+}
+
+// q = sum of the product's split partials + lambda p; block partials of p.q
+__global__ void __launch_bounds__(SERVE_VB) serve_reduce_kernel(const ServeTable *__restrict__ T) {
+  __shared__ double red[SERVE_VB / 32][SERVE_MAX_M];
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int b = item - T->vec_off[s];
+    const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
+    for (int c = 0; c < d.m; ++c) {
+      double pq = 0.0;
+      if (i < N) {
+        float acc = 0.0f;
+        for (int sp = 0; sp < d.splits; ++sp) acc += d.part[((int64_t)sp * d.M + c) * N + i];
+        const float pv = d.p[(int64_t)c * N + i];
+        const float qv = acc + d.lam32 * pv;
+        d.q[(int64_t)c * N + i] = qv;
+        pq = (double)pv * (double)qv;
+      }
+      serve_block_put(red, c, pq);
+    }
+    serve_block_flush(red, d.m, d.dpart0, d.nbv, b);
+  }
+}
+
+// alpha_c = rz_c / (p_c . q_c) for active columns; breakdown otherwise.
+__global__ void __launch_bounds__(SERVE_COL_THREADS)
+serve_alpha_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->col_off[n];
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int g = threadIdx.x >> 5; g < total; g += warps) {
+    const int s = serve_find_slot(T->col_off, n, g);
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    if (!sc->live) continue;
+    const int c = g - T->col_off[s];
+    const double pq = serve_col_sum(d.dpart0, d.nbv, c, lane);
+    if (lane == 0) {
+      double a = 0.0;
+      if (sc->active[c]) {
+        if (!(pq > 0.0)) {
+          sc->breakdown = 1;
+          sc->active[c] = 0;
+        } else {
+          a = sc->rz[c] / pq;
+        }
+      }
+      sc->alpha[c] = a;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q; block partials of r.r
+__global__ void __launch_bounds__(SERVE_VB) serve_update_kernel(const ServeTable *__restrict__ T) {
+  __shared__ double red[SERVE_VB / 32][SERVE_MAX_M];
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int b = item - T->vec_off[s];
+    const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
+    for (int c = 0; c < d.m; ++c) {
+      double rr = 0.0;
+      if (i < N) {
+        const int64_t e = (int64_t)c * N + i;
+        const double a = d.sc->alpha[c];
+        float rv = d.r[e];
+        if (a != 0.0) {
+          d.x[e] = (float)((double)d.x[e] + a * (double)d.p[e]);
+          rv = (float)((double)rv - a * (double)d.q[e]);
+          d.r[e] = rv;
+        }
+        rr = (double)rv * (double)rv;
+      }
+      serve_block_put(red, c, rr);
+    }
+    serve_block_flush(red, d.m, d.dpart0, d.nbv, b);
+  }
+}
+
+// Convergence test on the recursive residual and the iteration limit; then
+// the slot flags (one thread per slot) and the host-visible status.
+__global__ void __launch_bounds__(SERVE_COL_THREADS)
+serve_resid_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->col_off[n];
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int g = threadIdx.x >> 5; g < total; g += warps) {
+    const int s = serve_find_slot(T->col_off, n, g);
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    if (!sc->live) continue;
+    const int c = g - T->col_off[s];
+    const double rr = serve_col_sum(d.dpart0, d.nbv, c, lane);
+    if (lane == 0 && sc->active[c]) {
+      const double rel = sqrt(rr / sc->bb[c]);
+      sc->relres[c] = rel;
+      sc->iters[c] += 1;
+      if (rel <= sc->ctl.tol[c] || sc->iters[c] >= sc->ctl.limit) sc->active[c] = 0;
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    if (!sc->live) continue;
+    int live = 0, imax = 0;
+    for (int c = 0; c < d.m; ++c) {
+      live |= sc->active[c];
+      imax = max(imax, sc->iters[c]);
+    }
+    sc->live = live;
+    d.status->live = live;
+    d.status->breakdown = sc->breakdown;
+    d.status->iters_max = imax;
+  }
+}
+
+// part[b][l][c] = sum over the block's rows n of F[n + l N] r[c][n]
+__global__ void __launch_bounds__(256) serve_tt_kernel(const ServeTable *__restrict__ T) {
+  constexpr int PER_LANE = SERVE_TT_ROWS / 32;
+  __shared__ float sR[SERVE_MAX_M][SERVE_TT_ROWS];
+  const int n = T->nslots, total = T->tt_off[n];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->tt_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int b = item - T->tt_off[s];
+    const int64_t N = d.N, n0 = (int64_t)b * SERVE_TT_ROWS;
+    const int nr = (int)min((int64_t)SERVE_TT_ROWS, N - n0);
+    const int m = d.m, rank = d.rank;
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * SERVE_TT_ROWS; e += blockDim.x) {
+      const int c = e / SERVE_TT_ROWS, r = e % SERVE_TT_ROWS;
+      sR[c][r] = (r < nr) ? d.r[(int64_t)c * N + n0 + r] : 0.0f;
+    }
+    __syncthreads();
+    for (int l = warp; l < rank; l += blockDim.x >> 5) {
+      const float *col = d.F + (int64_t)l * N + n0;
+      float f[PER_LANE];
+#pragma unroll
+      for (int q = 0; q < PER_LANE; ++q) {
+        const int r = lane + 32 * q;
+        f[q] = (r < nr) ? col[r] : 0.0f;
+      }
+      float acc[SERVE_MAX_M];
+#pragma unroll
+      for (int c = 0; c < SERVE_MAX_M; ++c) acc[c] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < PER_LANE; ++q) {
+#pragma unroll
+        for (int c = 0; c < SERVE_MAX_M; ++c)
+          if (c < m) acc[c] = fmaf(f[q], sR[c][lane + 32 * q], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < SERVE_MAX_M; ++c) {
+        if (c < m) {
+          const float v = warp_sum(acc[c]);
+          if (lane == 0) d.ttpart[((int64_t)b * rank + l) * m + c] = (double)v;
+        }
+      }
+    }
+  }
+}
+
+// t[c][l] = sum over blocks of part[b][l][c] (one warp per (l, c))
+__global__ void __launch_bounds__(256) serve_ttred_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->ttr_off[n];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < total; w += gridDim.x * wpb) {
+    const int s = serve_find_slot(T->ttr_off, n, w);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int e = w - T->ttr_off[s];
+    const int l = e / d.m, c = e % d.m;
+    double acc = 0.0;
+    for (int b = lane; b < d.nbt; b += 32) acc += d.ttpart[((int64_t)b * d.rank + l) * d.m + c];
+    acc = warp_sum(acc);
+    if (lane == 0) d.t[(int64_t)c * d.rank + l] = acc;
+  }
+}
+
+// UPPER == false: u = W t (rows of W read from Wt); UPPER == true: v = W^T u.
+template <bool UPPER>
+__global__ void __launch_bounds__(256) serve_tri_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->tri_off[n];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < total; w += gridDim.x * wpb) {
+    const int s = serve_find_slot(T->tri_off, n, w);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int i = w - T->tri_off[s];
+    const int rank = d.rank, m = d.m;
+    const double *Mt = UPPER ? d.W : d.Wt;
+    const double *x = UPPER ? d.u : d.t;
+    double *out = UPPER ? d.v : d.u;
+    double acc[SERVE_MAX_M];
+#pragma unroll
+    for (int c = 0; c < SERVE_MAX_M; ++c) acc[c] = 0.0;
+    const double *col = Mt + (int64_t)i * rank;
+    const int lo = UPPER ? i : 0, hi = UPPER ? rank : i + 1;
+    for (int l = lo + lane; l < hi; l += 32) {
+      const double wv = col[l];
+#pragma unroll
+      for (int c = 0; c < SERVE_MAX_M; ++c)
+        if (c < m) acc[c] = fma(wv, x[(int64_t)c * rank + l], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < SERVE_MAX_M; ++c) {
+      if (c < m) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) out[(int64_t)c * rank + i] = v;
+      }
+    }
+  }
+}
+
+// z = (r - F v) / lambda; block partials of r.z
+__global__ void __launch_bounds__(SERVE_VB) serve_tn_kernel(const ServeTable *__restrict__ T) {
+  constexpr int LCH = 256;
+  constexpr int LU = 16;
+  __shared__ float sv[LCH][SERVE_MAX_M];
+  __shared__ double red[SERVE_VB / 32][SERVE_MAX_M];
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    if (!d.sc->live) continue;
+    const int b = item - T->vec_off[s];
+    const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
+    const bool ok = i < N;
+    const int m = d.m, rank = d.rank;
+    float acc[SERVE_MAX_M];
+#pragma unroll
+    for (int c = 0; c < SERVE_MAX_M; ++c) acc[c] = 0.0f;
+    for (int l0 = 0; l0 < rank; l0 += LCH) {
+      const int nl = min(LCH, rank - l0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < m * LCH; e += blockDim.x) {
+        const int c = e / LCH, l = e % LCH;
+        sv[l][c] = (l < nl) ? (float)d.v[(int64_t)c * rank + l0 + l] : 0.0f;
+      }
+      __syncthreads();
+      for (int lb = 0; lb < nl; lb += LU) {
+        float f[LU];
+#pragma unroll
+        for (int u = 0; u < LU; ++u)
+          f[u] = (ok && lb + u < nl) ? d.F[i + (int64_t)(l0 + lb + u) * N] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+#pragma unroll
+          for (int c = 0; c < SERVE_MAX_M; ++c)
+            if (c < m) acc[c] = fmaf(f[u], sv[lb + u][c], acc[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < SERVE_MAX_M; ++c) {
+      if (c < m) {
+        double rz = 0.0;
+        if (ok) {
+          const int64_t e = (int64_t)c * N + i;
+          const float rv = d.r[e];
+          const float zv = (float)(((double)rv - (double)acc[c]) * d.inv_lam);
+          d.z[e] = zv;
+          rz = (double)rv * (double)zv;
+        }
+        serve_block_put(red, c, rz);
+      }
+    }
+    serve_block_flush(red, m, d.dpart1, d.nbv, b);
+  }
+}
+
+// beta_c = rz_new / rz for active columns
+__global__ void __launch_bounds__(SERVE_COL_THREADS)
+serve_beta_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->col_off[n];
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int g = threadIdx.x >> 5; g < total; g += warps) {
+    const int s = serve_find_slot(T->col_off, n, g);
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    if (!sc->live) continue;
+    const int c = g - T->col_off[s];
+    const double rz = serve_col_sum(d.dpart1, d.nbv, c, lane);
+    if (lane == 0) {
+      double bt = 0.0;
+      if (sc->active[c]) {
+        bt = rz / sc->rz[c];
+        sc->rz[c] = rz;
+      }
+      sc->beta[c] = bt;
+    }
+  }
+}
+
+// p = z + beta p for active columns
+__global__ void __launch_bounds__(SERVE_VB) serve_dir_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    const ServeScalars *sc = d.sc;
+    if (!sc->live) continue;
+    const int64_t N = d.N, i = (int64_t)(item - T->vec_off[s]) * SERVE_VB + threadIdx.x;
+    if (i >= N) continue;
+    for (int c = 0; c < d.m; ++c) {
+      if (sc->active[c]) {
+        const int64_t e = (int64_t)c * N + i;
+        d.p[e] = (float)((double)d.z[e] + sc->beta[c] * (double)d.p[e]);
+      }
+    }
+  }
+}
+
+// Inner-solve start (one-slot table): x = 0, r = float32(r64) on the columns
+// that take part (zero elsewhere), block partials of r.r; marks the slot live
+// for the preconditioner launches that follow.
+__global__ void __launch_bounds__(SERVE_VB) serve_init_vec_kernel(const ServeTable *__restrict__ T) {
+  __shared__ double red[SERVE_VB / 32][SERVE_MAX_M];
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    if (item == T->vec_off[s] && threadIdx.x == 0) sc->live = 1;
+    const int b = item - T->vec_off[s];
+    const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
+    for (int c = 0; c < d.m; ++c) {
+      double rr = 0.0;
+      if (i < N) {
+        const int64_t e = (int64_t)c * N + i;
+        const float rv = sc->ctl.need[c] ? (float)d.r64[e] : 0.0f;
+        d.r[e] = rv;
+        d.x[e] = 0.0f;
+        rr = (double)rv * (double)rv;
+      }
+      serve_block_put(red, c, rr);
+    }
+    serve_block_flush(red, d.m, d.dpart0, d.nbv, b);
+  }
+}
+
+__global__ void __launch_bounds__(SERVE_COL_THREADS)
+serve_init_scalars_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->col_off[n];
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int g = threadIdx.x >> 5; g < total; g += warps) {
+    const int s = serve_find_slot(T->col_off, n, g);
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    const int c = g - T->col_off[s];
+    const double bb = serve_col_sum(d.dpart0, d.nbv, c, lane);
+    const double rz = serve_col_sum(d.dpart1, d.nbv, c, lane);
+    if (lane == 0) {
+      sc->bb[c] = bb;
+      sc->rz[c] = rz;
+      sc->iters[c] = 0;
+      sc->alpha[c] = 0.0;
+      sc->beta[c] = 0.0;
+      sc->relres[c] = (bb > 0.0) ? 1.0 : 0.0;
+      sc->active[c] = (sc->ctl.need[c] && bb > 0.0) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const ServeSlotDesc &d = T->slot[s];
+    ServeScalars *sc = d.sc;
+    int live = 0;
+    for (int c = 0; c < d.m; ++c) live |= sc->active[c];
+    sc->breakdown = 0;
+    sc->live = live;
+    d.status->live = live;
+    d.status->breakdown = 0;
+    d.status->iters_max = 0;
+  }
+}
+
+// p = z (all columns)
+__global__ void __launch_bounds__(SERVE_VB) serve_pinit_kernel(const ServeTable *__restrict__ T) {
+  const int n = T->nslots, total = T->vec_off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = serve_find_slot(T->vec_off, n, item);
+    const ServeSlotDesc &d = T->slot[s];
+    const int64_t N = d.N, i = (int64_t)(item - T->vec_off[s]) * SERVE_VB + threadIdx.x;
+    if (i >= N) continue;
+    for (int c = 0; c < d.m; ++c) d.p[(int64_t)c * N + i] = d.z[(int64_t)c * N + i];
+  }
+}
+
+// out[c] = sum_n a[c][n]^2 (one CTA per column, fixed order)
+__global__ void __launch_bounds__(1024) serve_sumsq_kernel(const double *__restrict__ a, int64_t N,
+                                                           double *__restrict__ out) {
+  __shared__ double red[32];
+  const double *col = a + (int64_t)blockIdx.x * N;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) acc = fma(col[i], col[i], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+static unsigned serve_vec_grid() { return (unsigned)(num_sms() * 4); }
+
+static krr_status serve_launch_precond(const ServeTable *T, cudaStream_t s) {
+  const unsigned g = serve_vec_grid();
+  serve_tt_kernel<<<g, 256, 0, s>>>(T);
+  KRR_LAUNCH_CHECK();
+  serve_ttred_kernel<<<g, 256, 0, s>>>(T);
+  KRR_LAUNCH_CHECK();
+  serve_tri_kernel<false><<<g, 256, 0, s>>>(T);
+  KRR_LAUNCH_CHECK();
+  serve_tri_kernel<true><<<g, 256, 0, s>>>(T);
+  KRR_LAUNCH_CHECK();
+  serve_tn_kernel<<<g, SERVE_VB, 0, s>>>(T);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+// U inner PCG iterations of every slot in T (SERVE_KERNELS_PER_ITER kernels
+// each), in the order of the single-solve loop: product, alpha, update,
+// convergence test, preconditioner, beta, direction.
+static krr_status serve_launch_iterations(const ServeTable *T, int *counters, int U,
+                                          cudaStream_t s) {
+  const unsigned g = serve_vec_grid();
+  KRR_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int) * U, s));
+  for (int it = 0; it < U; ++it) {
+    KRR_TRY(serve_launch_product(T, counters + it, s));
+    serve_reduce_kernel<<<g, SERVE_VB, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+    serve_alpha_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+    serve_update_kernel<<<g, SERVE_VB, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+    serve_resid_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+    KRR_TRY(serve_launch_precond(T, s));
+    serve_beta_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+    serve_dir_kernel<<<g, SERVE_VB, 0, s>>>(T);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
+static krr_status serve_launch_inner_start(const ServeTable *T1, cudaStream_t s) {
+  const unsigned g = serve_vec_grid();
+  serve_init_vec_kernel<<<g, SERVE_VB, 0, s>>>(T1);
+  KRR_LAUNCH_CHECK();
+  KRR_TRY(serve_launch_precond(T1, s));
+  serve_init_scalars_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T1);
+  KRR_LAUNCH_CHECK();
+  serve_pinit_kernel<<<g, SERVE_VB, 0, s>>>(T1);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+// ============================================================ host side
+static int serve_pad_m(int m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16; }
+
+// Columns per split of a slot's product: at least SERVE_MIN_CHUNK, at most
+// SERVE_MAX_SPLITS splits, a multiple of the column tile.
+static int64_t serve_chunk(int64_t N) {
+  int64_t chunk = (N + SERVE_MAX_SPLITS - 1) / SERVE_MAX_SPLITS;
+  if (chunk < SERVE_MIN_CHUNK) chunk = SERVE_MIN_CHUNK;
+  return (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
+}
+
+// Estimated peak device bytes of one solve (build and solve phases together).
+double serve_footprint(int64_t N, int d, int m, int k) {
+  const double n = (double)N;
+  const int M = serve_pad_m(m);
+  const int dp = serve_dp_class(d), dpff = (d + 3) / 4 * 4;
+  const int B = std::min(100, std::max(1, (k + 9) / 10));
+  const int64_t chunk = serve_chunk(N);
+  const double splits = (double)((N + chunk - 1) / chunk);
+  const double nbt = (double)((N + SERVE_TT_ROWS - 1) / SERVE_TT_ROWS);
+  const double nbv = (double)((N + SERVE_VB - 1) / SERVE_VB);
+  double b = 0.0;
+  // build: X, the float64 factor and its scratch, float32 factor, core
+  b += n * d * 8 + n * k * 8 + n * k * 4 + n * 8 + k * 8.0;
+  b += 2.0 * n * B * 8 + (double)B * k * 8 + 3.0 * k * k * 8;
+  // prepared points (float32 and float-float)
+  b += n * dp * 4 + n * 4 + 2.0 * n * dpff * 4 + 2.0 * n * 4;
+  // float64 blocks (y, x, r, M x) and float32 CG vectors
+  b += 4.0 * n * m * 8 + 5.0 * n * m * 4;
+  // product partials, preconditioner partials, reductions
+  b += splits * M * n * 4 + nbt * k * m * 8 + 3.0 * k * m * 8 + 2.0 * nbv * m * 8;
+  // float-float residual product: split partials and split right-hand sides
+  const double rows_ff = 128.0 * (dpff <= 16 ? 2 : 1);
+  const double tiles_ff = std::ceil(n / rows_ff);
+  const double ffsplits = std::min(std::ceil(3648.0 / tiles_ff) + 1.0, std::ceil(n / 32.0));
+  b += ffsplits * M * n * 8 + 2.0 * n * m * 4;
+  return b * 1.05 + 16.0 * 1024 * 1024;
+}
+
+}  // namespace krr
+
+using krr::ServeControl;
+using krr::ServeScalars;
+using krr::ServeSlotDesc;
+using krr::ServeStatus;
+using krr::ServeTable;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+enum class Phase { Queued, Building, Norms, Init, Inner, Refine, Final };
+
+struct Slot {
+  // request
+  int64_t req_id = 0;
+  const double *X = nullptr;
+  const double *Y = nullptr;
+  double *alpha_out = nullptr;
+  int64_t N = 0;
+  int d = 0, kern = 0, m = 0, k = 0, maxit = 0;
+  double sigma = 0, mu = 0, tol = 0, bytes = 0;
+  uint64_t seed = 0;
+  double t_submit = 0, t_admit = 0, t_built = 0;
+  // engine state
+  int id = -1;
+  Phase phase = Phase::Queued;
+  krr_status build_status = KRR_OK;
+  std::string error;
+  krr_factor *f = nullptr;
+  const krr::NystromCore *core = nullptr;
+  krr::PointsF32 P32;
+  krr::PointsFF Pff;
+  void *arena = nullptr;
+  krr::DevBuf<double> ffpart;
+  krr::DevBuf<float> ffvsplit;
+  double *Y64 = nullptr, *alpha64 = nullptr, *r64 = nullptr, *mx64 = nullptr;
+  ServeSlotDesc desc{};
+  // refinement bookkeeping (as the single-solve driver)
+  std::vector<double> yn, rn;
+  int outer = 0, iters = 0, budget = 0;
+  double prev_worst = 1e300, relres = 1.0, entries = 0.0;
+  bool breakdown = false, first_norms = true;
+  krr_status status = KRR_OK;
+};
+
+}  // namespace
+
+struct krr_server {
+  krr_server_config cfg{};
+  int device = 0;
+  Clock::time_point t0;
+  cudaStream_t s_iter = nullptr, s_build = nullptr, s_free = nullptr;
+  cudaStream_t s_slot[krr::SERVE_MAX_SLOTS] = {};
+  cudaEvent_t ev_slot[krr::SERVE_MAX_SLOTS] = {};
+  cudaEvent_t ev_step = nullptr;
+  // device
+  ServeTable *table_dev = nullptr;
+  ServeTable *init_dev = nullptr;      // one single-slot table per slot index
+  ServeScalars *scalars_dev = nullptr;
+  ServeStatus *status_dev = nullptr;
+  int *counters_dev = nullptr;
+  // pinned host
+  ServeTable *table_host = nullptr;
+  ServeTable *init_host = nullptr;
+  ServeStatus *status_host = nullptr;
+  ServeControl *ctl_host = nullptr;
+  double *sumsq_host = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  // slots
+  std::unique_ptr<Slot> slots[krr::SERVE_MAX_SLOTS];
+  std::deque<std::unique_ptr<Slot>> queue;
+  std::vector<krr_request_result> done;
+  bool table_dirty = true;
+  // builder
+  std::thread builder;
+  std::mutex mtx;
+  std::condition_variable cv;
+  std::deque<Slot *> build_q;
+  std::vector<Slot *> built;
+  bool stop = false;
+  // accounting
+  double budget = 0, reserved = 0, peak_reserved = 0, entries_total = 0;
+  int64_t next_id = 0, submitted = 0, completed = 0, steps = 0, step_kernels = 0;
+  int max_concurrent = 0;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace krr {
+
+static size_t table_bytes(int nslots) {
+  return offsetof(ServeTable, slot) + sizeof(ServeSlotDesc) * (size_t)(nslots > 0 ? nslots : 0);
+}
+
+static void table_add(ServeTable *T, const ServeSlotDesc &d) {
+  const int s = T->nslots;
+  if (s == 0) {
+    T->prod_off[0] = T->vec_off[0] = T->tt_off[0] = T->ttr_off[0] = T->tri_off[0] =
+        T->col_off[0] = 0;
+  }
+  T->slot[s] = d;
+  T->prod_off[s + 1] = T->prod_off[s] + d.row_tiles * d.splits;
+  T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
+  T->tt_off[s + 1] = T->tt_off[s] + d.nbt;
+  T->ttr_off[s + 1] = T->ttr_off[s] + (d.rank > 0 ? d.rank * d.m : 0);
+  T->tri_off[s + 1] = T->tri_off[s] + d.rank;
+  T->col_off[s + 1] = T->col_off[s] + d.m;
+  T->nslots = s + 1;
+}
+
+template <typename T>
+static void rebind(DevBuf<T> &b, cudaStream_t s) { b.s = s; }
+
+// ------------------------------------------------------------- build
+static krr_status build_slot(krr_server *S, Slot *sl) {
+  cudaStream_t s = S->s_build;
+  const int64_t N = sl->N;
+  const int d = sl->d, m = sl->m;
+  DevBuf<double> xtmp;
+  const double *Xd = nullptr;
+  KRR_TRY(device_view(sl->X, (size_t)N * d, s, xtmp, &Xd));
+  sl->f = new (std::nothrow) krr_factor();
+  if (!sl->f) return KRR_ENOMEM;
+  sl->f->free_stream = S->s_free;
+  sl->f->N = N;
+  sl->f->d = d;
+  sl->f->kern = sl->kern;
+  sl->f->sigma = sl->sigma;
+  if (sl->k > 0) {
+    const int B = std::min(100, (sl->k + 9) / 10);
+    KRR_TRY(rpcholesky_device(Xd, N, d, sl->kern, sl->sigma, sl->k, B, sl->seed, s, sl->f));
+  }
+  if (sl->f->rank > 0) KRR_TRY(nystrom_core(sl->f, sl->mu, KRR_PREC_MIXED, s, &sl->core));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  // the float64 factor only served the core; the solve uses its float32 copy
+  dev_free(sl->f->F, S->s_free);
+  sl->f->F = nullptr;
+  const int dp = serve_dp_class(d);
+  KRR_TRY(prepare_points_f32(Xd, N, d, sl->kern, sl->sigma, s, sl->P32, nullptr, dp));
+  KRR_TRY(prepare_points_ff(Xd, N, d, sl->kern, sl->sigma, s, sl->Pff));
+
+  ServeSlotDesc &D = sl->desc;
+  const int M = serve_pad_m(m);
+  const int rank = sl->core ? sl->core->rank : 0;
+  const int64_t chunk = serve_chunk(N);
+  const int rows = KMV_THREADS * kmv32_rows_per_thread(dp, M);
+  D.xt = sl->P32.xt.p;
+  D.cn = sl->P32.cn.p;
+  D.N = N;
+  D.chunk = chunk;
+  D.m = m;
+  D.M = M;
+  D.dp = dp;
+  D.kern = sl->kern;
+  D.variant = serve_variant(sl->kern, dp, M);
+  D.row_tiles = (int)((N + rows - 1) / rows);
+  D.splits = (int)((N + chunk - 1) / chunk);
+  const double lambda = sl->mu * (double)N;
+  D.lam32 = (float)lambda;
+  D.inv_lam = 1.0 / lambda;
+  D.rank = rank;
+  D.nbt = rank > 0 ? (int)((N + SERVE_TT_ROWS - 1) / SERVE_TT_ROWS) : 0;
+  D.nbv = (int)((N + SERVE_VB - 1) / SERVE_VB);
+  D.F = sl->core ? sl->core->F32 : nullptr;
+  D.W = sl->core ? sl->core->W : nullptr;
+  D.Wt = sl->core ? sl->core->Wt : nullptr;
+  D.sc = S->scalars_dev + sl->id;
+  D.status = S->status_dev + sl->id;
+
+  // one arena for the slot's solve state, 256-byte aligned pieces
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t nm = (size_t)N * m;
+  const size_t oY = take(nm * 8), oA = take(nm * 8), oR = take(nm * 8), oMx = take(nm * 8);
+  const size_t ox = take(nm * 4), orr = take(nm * 4), oz = take(nm * 4), op = take(nm * 4),
+               oq = take(nm * 4);
+  const size_t opart = take((size_t)D.splits * M * N * 4);
+  const size_t ott = take((size_t)D.nbt * rank * m * 8);
+  const size_t ot = take((size_t)rank * m * 8), ou = take((size_t)rank * m * 8),
+               ov = take((size_t)rank * m * 8);
+  const size_t od0 = take((size_t)D.nbv * m * 8), od1 = take((size_t)D.nbv * m * 8);
+  KRR_CUDA_TRY(cudaMallocAsync(&sl->arena, off, s));
+  char *base = (char *)sl->arena;
+  sl->Y64 = (double *)(base + oY);
+  sl->alpha64 = (double *)(base + oA);
+  sl->r64 = (double *)(base + oR);
+  sl->mx64 = (double *)(base + oMx);
+  D.x = (float *)(base + ox);
+  D.r = (float *)(base + orr);
+  D.z = (float *)(base + oz);
+  D.p = (float *)(base + op);
+  D.q = (float *)(base + oq);
+  D.part = (float *)(base + opart);
+  D.ttpart = (double *)(base + ott);
+  D.t = (double *)(base + ot);
+  D.u = (double *)(base + ou);
+  D.v = (double *)(base + ov);
+  D.dpart0 = (double *)(base + od0);
+  D.dpart1 = (double *)(base + od1);
+  D.r64 = sl->r64;
+  KRR_CUDA_TRY(cudaMemcpyAsync(sl->Y64, sl->Y, nm * 8, cudaMemcpyDefault, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(sl->alpha64, 0, nm * 8, s));
+  KRR_CUDA_TRY(cudaMemcpyAsync(sl->r64, sl->Y64, nm * 8, cudaMemcpyDeviceToDevice, s));
+  KRR_CUDA_TRY(cudaMemsetAsync(D.p, 0, nm * 4, s));
+  KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  // from here on the slot's memory is released on the free stream
+  rebind(sl->P32.xt, S->s_free);
+  rebind(sl->P32.cn, S->s_free);
+  rebind(sl->P32.mean, S->s_free);
+  rebind(sl->Pff.xh, S->s_free);
+  rebind(sl->Pff.xl, S->s_free);
+  rebind(sl->Pff.ch, S->s_free);
+  rebind(sl->Pff.cl, S->s_free);
+  rebind(sl->Pff.mean, S->s_free);
+  return KRR_OK;
+}
+
+static void builder_main(krr_server *S) {
+  cudaSetDevice(S->device);
+  set_alloc_stream(S->s_build);
+  for (;;) {
+    Slot *sl = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mtx);
+      S->cv.wait(lk, [&] { return S->stop || !S->build_q.empty(); });
+      if (S->stop) break;
+      sl = S->build_q.front();
+      S->build_q.pop_front();
+    }
+    clear_error();
+    const krr_status st = build_slot(S, sl);
+    if (st != KRR_OK) cudaStreamSynchronize(S->s_build);
+    {
+      std::lock_guard<std::mutex> lk(S->mtx);
+      sl->build_status = st;
+      if (st != KRR_OK) sl->error = krr_last_error();
+      S->built.push_back(sl);
+    }
+  }
+  set_alloc_stream(nullptr);
+}
+
+// ------------------------------------------------------------ phases
+static void complete(krr_server *S, Slot *sl, krr_status st) {
+  krr_request_result r{};
+  r.id = sl->req_id;
+  r.status = st;
+  r.iters = sl->iters;
+  r.outer_refinements = sl->outer;
+  r.rank = sl->desc.rank;
+  r.m = sl->m;
+  r.rel_residual = sl->relres;
+  r.kernel_entries = sl->entries;
+  r.t_submit = sl->t_submit;
+  r.t_admit = sl->t_admit;
+  r.t_built = sl->t_built;
+  r.t_done = S->now();
+  S->done.push_back(r);
+  S->completed += 1;
+  S->entries_total += sl->entries;
+  S->reserved -= sl->bytes;
+  // every use of the slot's memory has completed (its last event was seen)
+  free_factor(sl->f);
+  sl->f = nullptr;
+  if (sl->arena) cudaFreeAsync(sl->arena, S->s_free);
+  sl->arena = nullptr;
+  const int id = sl->id;
+  if (id >= 0) S->slots[id].reset();
+}
+
+static krr_status start_norms(krr_server *S, Slot *sl) {
+  cudaStream_t ss = S->s_slot[sl->id];
+  ServeScalars *sc = S->scalars_dev + sl->id;
+  serve_sumsq_kernel<<<sl->m, 1024, 0, ss>>>(sl->r64, sl->N, sc->resid_sq);
+  KRR_LAUNCH_CHECK();
+  KRR_CUDA_TRY(cudaMemcpyAsync(S->sumsq_host + (size_t)sl->id * SERVE_MAX_M, sc->resid_sq,
+                               sizeof(double) * sl->m, cudaMemcpyDeviceToHost, ss));
+  KRR_CUDA_TRY(cudaEventRecord(S->ev_slot[sl->id], ss));
+  return KRR_OK;
+}
+
+static krr_status finalize(krr_server *S, Slot *sl, krr_status st) {
+  sl->status = st;
+  cudaStream_t ss = S->s_slot[sl->id];
+  KRR_CUDA_TRY(cudaMemcpyAsync(sl->alpha_out, sl->alpha64, sizeof(double) * sl->N * sl->m,
+                               cudaMemcpyDefault, ss));
+  KRR_CUDA_TRY(cudaEventRecord(S->ev_slot[sl->id], ss));
+  sl->phase = Phase::Final;
+  return KRR_OK;
+}
+
+static double worst_rel(const Slot *sl) {
+  double w = 0.0;
+  for (int c = 0; c < sl->m; ++c)
+    w = std::max(w, sl->yn[c] > 0 ? sl->rn[c] / sl->yn[c] : 0.0);
+  return w;
+}
+
+// One decision of the refinement loop after a float64 residual is known.
+static krr_status decide(krr_server *S, Slot *sl) {
+  constexpr int kMaxOuter = 12;
+  constexpr double kInnerFloor = 1e-4;
+  const double worst = worst_rel(sl);
+  sl->relres = worst;
+  if (worst <= sl->tol) return finalize(S, sl, KRR_OK);
+  if (sl->breakdown) return finalize(S, sl, KRR_EBREAKDOWN);
+  if (sl->outer >= kMaxOuter || sl->budget <= 0) return finalize(S, sl, KRR_ENOCONV);
+  if (sl->outer > 0 && worst > 0.5 * sl->prev_worst) return finalize(S, sl, KRR_ENOCONV);
+  sl->prev_worst = worst;
+  ServeControl &ctl = S->ctl_host[sl->id];
+  std::memset(&ctl, 0, sizeof(ctl));
+  for (int c = 0; c < sl->m; ++c) {
+    const double rel = sl->yn[c] > 0 ? sl->rn[c] / sl->yn[c] : 0.0;
+    ctl.need[c] = rel > sl->tol ? 1 : 0;
+    ctl.tol[c] = ctl.need[c] ? std::max(0.3 * sl->tol / rel, kInnerFloor) : 1.0;
+  }
+  ctl.limit = sl->budget;
+  cudaStream_t ss = S->s_slot[sl->id];
+  KRR_CUDA_TRY(cudaMemcpyAsync(&S->scalars_dev[sl->id].ctl, &ctl, sizeof(ServeControl),
+                               cudaMemcpyHostToDevice, ss));
+  KRR_TRY(serve_launch_inner_start(S->init_dev + sl->id, ss));
+  KRR_CUDA_TRY(cudaEventRecord(S->ev_slot[sl->id], ss));
+  sl->phase = Phase::Init;
+  return KRR_OK;
+}
+
+// Inner solve finished: x += d, r = y - M x (float-float product), norms.
+static krr_status start_refine(krr_server *S, Slot *sl) {
+  cudaStream_t ss = S->s_slot[sl->id];
+  const int64_t nm = sl->N * sl->m;
+  KRR_TRY(add_f32_to_f64(sl->alpha64, sl->desc.x, nm, ss));
+  KRR_TRY(kmv_ff(sl->Pff, sl->mu * (double)sl->N, sl->alpha64, sl->N, sl->m, sl->mx64, sl->N,
+                 ss, sl->ffpart, sl->ffvsplit));
+  sl->entries += kmv_entries(sl->N);
+  KRR_TRY(residual_f64(sl->Y64, sl->mx64, sl->r64, nm, ss));
+  KRR_TRY(start_norms(S, sl));
+  sl->phase = Phase::Refine;
+  return KRR_OK;
+}
+
+static krr_status on_built(krr_server *S, Slot *sl) {
+  sl->t_built = S->now();
+  if (sl->build_status != KRR_OK) {
+    sl->relres = 1.0;
+    complete(S, sl, sl->build_status);
+    return KRR_OK;
+  }
+  // the slot's one-slot table for its inner-solve starts
+  ServeTable *T1 = S->init_host + sl->id;
+  T1->nslots = 0;
+  table_add(T1, sl->desc);
+  cudaStream_t ss = S->s_slot[sl->id];
+  KRR_CUDA_TRY(cudaMemcpyAsync(S->init_dev + sl->id, T1, table_bytes(1), cudaMemcpyHostToDevice,
+                               ss));
+  sl->budget = sl->maxit;
+  sl->first_norms = true;
+  KRR_TRY(start_norms(S, sl));
+  sl->phase = Phase::Norms;
+  return KRR_OK;
+}
+
+static krr_status on_event(krr_server *S, Slot *sl) {
+  const double *sq = S->sumsq_host + (size_t)sl->id * SERVE_MAX_M;
+  switch (sl->phase) {
+    case Phase::Norms:
+      sl->yn.assign(sl->m, 0.0);
+      for (int c = 0; c < sl->m; ++c) sl->yn[c] = std::sqrt(sq[c]);
+      sl->rn = sl->yn;
+      return decide(S, sl);
+    case Phase::Init:
+      sl->phase = Phase::Inner;
+      S->table_dirty = true;
+      return KRR_OK;
+    case Phase::Refine:
+      sl->rn.assign(sl->m, 0.0);
+      for (int c = 0; c < sl->m; ++c) sl->rn[c] = std::sqrt(sq[c]);
+      sl->outer += 1;
+      return decide(S, sl);
+    case Phase::Final:
+      complete(S, sl, sl->status);
+      return KRR_OK;
+    default:
+      return KRR_OK;
+  }
+}
+
+static void admit(krr_server *S) {
+  while (!S->queue.empty()) {
+    Slot *front = S->queue.front().get();
+    int active = 0, free_id = -1;
+    for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+      if (S->slots[i]) ++active;
+      else if (free_id < 0) free_id = i;
+    }
+    if (active >= S->cfg.max_slots || free_id < 0) return;
+    if (S->reserved + front->bytes > S->budget) return;
+    std::unique_ptr<Slot> sl = std::move(S->queue.front());
+    S->queue.pop_front();
+    sl->id = free_id;
+    sl->t_admit = S->now();
+    sl->phase = Phase::Building;
+    S->reserved += sl->bytes;
+    S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+    Slot *raw = sl.get();
+    S->slots[free_id] = std::move(sl);
+    {
+      std::lock_guard<std::mutex> lk(S->mtx);
+      S->build_q.push_back(raw);
+    }
+    S->cv.notify_one();
+  }
+}
+
+static krr_status launch_step(krr_server *S, int nslots) {
+  const int U = S->cfg.iters_per_step;
+  if (S->cfg.use_graph) {
+    if (!S->graph) {
+      cudaGraph_t g = nullptr;
+      KRR_CUDA_TRY(cudaStreamBeginCapture(S->s_iter, cudaStreamCaptureModeThreadLocal));
+      krr_status st = serve_launch_iterations(S->table_dev, S->counters_dev, U, S->s_iter);
+      cudaError_t e = cudaStreamEndCapture(S->s_iter, &g);
+      if (st != KRR_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      KRR_CUDA_TRY(e);
+      e = cudaGraphInstantiate(&S->graph, g, 0);
+      cudaGraphDestroy(g);
+      KRR_CUDA_TRY(e);
+    }
+    KRR_CUDA_TRY(cudaGraphLaunch(S->graph, S->s_iter));
+    count_launches((unsigned long long)U * SERVE_KERNELS_PER_ITER);
+  } else {
+    KRR_TRY(serve_launch_iterations(S->table_dev, S->counters_dev, U, S->s_iter));
+  }
+  S->steps += 1;
+  S->step_kernels += (int64_t)U * SERVE_KERNELS_PER_ITER;
+  S->max_concurrent = std::max(S->max_concurrent, nslots);
+  return KRR_OK;
+}
+
+// Admission, finished builds and the slot streams' events: everything that
+// does not touch the slots of a running step.
+static krr_status service(krr_server *S) {
+  admit(S);
+  std::vector<Slot *> built;
+  {
+    std::lock_guard<std::mutex> lk(S->mtx);
+    built.swap(S->built);
+  }
+  for (Slot *sl : built) KRR_TRY(on_built(S, sl));
+  for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+    Slot *sl = S->slots[i].get();
+    if (!sl) continue;
+    if (sl->phase == Phase::Norms || sl->phase == Phase::Init || sl->phase == Phase::Refine ||
+        sl->phase == Phase::Final) {
+      const cudaError_t e = cudaEventQuery(S->ev_slot[i]);
+      if (e == cudaErrorNotReady) continue;
+      KRR_CUDA_TRY(e);
+      KRR_TRY(on_event(S, sl));
+    }
+  }
+  // freed slots may admit more
+  admit(S);
+  return KRR_OK;
+}
+
+static krr_status server_step(krr_server *S, int64_t *unfinished) {
+  KRR_TRY(service(S));
+  std::vector<Slot *> inner;
+  for (int i = 0; i < SERVE_MAX_SLOTS; ++i)
+    if (S->slots[i] && S->slots[i]->phase == Phase::Inner) inner.push_back(S->slots[i].get());
+  if (!inner.empty()) {
+    if (S->table_dirty) {
+      ServeTable *T = S->table_host;
+      T->nslots = 0;
+      for (Slot *sl : inner) table_add(T, sl->desc);
+      KRR_CUDA_TRY(cudaMemcpyAsync(S->table_dev, T, table_bytes(T->nslots),
+                                   cudaMemcpyHostToDevice, S->s_iter));
+      S->table_dirty = false;
+    }
+    KRR_TRY(launch_step(S, (int)inner.size()));
+    KRR_CUDA_TRY(cudaMemcpyAsync(S->status_host, S->status_dev,
+                                 sizeof(ServeStatus) * SERVE_MAX_SLOTS, cudaMemcpyDeviceToHost,
+                                 S->s_iter));
+    KRR_CUDA_TRY(cudaEventRecord(S->ev_step, S->s_iter));
+    // keep the other slots moving while the step runs
+    for (;;) {
+      const cudaError_t e = cudaEventQuery(S->ev_step);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) KRR_CUDA_TRY(e);
+      KRR_TRY(service(S));
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (Slot *sl : inner) {
+      const ServeStatus &st = S->status_host[sl->id];
+      if (st.live) continue;
+      sl->iters += st.iters_max;
+      sl->budget -= st.iters_max;
+      sl->entries += kmv_entries(sl->N) * st.iters_max;
+      sl->breakdown = st.breakdown != 0;
+      S->table_dirty = true;
+      KRR_TRY(start_refine(S, sl));
+    }
+  } else {
+    bool busy = false;
+    for (int i = 0; i < SERVE_MAX_SLOTS; ++i) busy = busy || (bool)S->slots[i];
+    if (busy) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (unfinished) {
+    int64_t n = (int64_t)S->queue.size();
+    for (int i = 0; i < SERVE_MAX_SLOTS; ++i) n += S->slots[i] ? 1 : 0;
+    *unfinished = n;
+  }
+  return KRR_OK;
+}
+
+static void server_free(krr_server *S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mtx);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->builder.joinable()) S->builder.join();
+  cudaDeviceSynchronize();
+  for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+    if (S->slots[i]) {
+      free_factor(S->slots[i]->f);
+      S->slots[i]->f = nullptr;
+      if (S->slots[i]->arena) cudaFreeAsync(S->slots[i]->arena, S->s_free);
+      S->slots[i].reset();
+    }
+  }
+  cudaDeviceSynchronize();
+  S->queue.clear();
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  cudaFree(S->table_dev);
+  cudaFree(S->init_dev);
+  cudaFree(S->scalars_dev);
+  cudaFree(S->status_dev);
+  cudaFree(S->counters_dev);
+  cudaFreeHost(S->table_host);
+  cudaFreeHost(S->init_host);
+  cudaFreeHost(S->status_host);
+  cudaFreeHost(S->ctl_host);
+  cudaFreeHost(S->sumsq_host);
+  for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+    if (S->ev_slot[i]) cudaEventDestroy(S->ev_slot[i]);
+    if (S->s_slot[i]) cudaStreamDestroy(S->s_slot[i]);
+  }
+  if (S->ev_step) cudaEventDestroy(S->ev_step);
+  if (S->s_iter) cudaStreamDestroy(S->s_iter);
+  if (S->s_build) cudaStreamDestroy(S->s_build);
+  if (S->s_free) cudaStreamDestroy(S->s_free);
+  delete S;
+}
+
+static krr_status server_init(krr_server *S) {
+  KRR_CUDA_TRY(cudaGetDevice(&S->device));
+  int lo = 0, hi = 0;
+  KRR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_iter, cudaStreamNonBlocking, hi));
+  KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_build, cudaStreamNonBlocking, lo));
+  KRR_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_free, cudaStreamNonBlocking));
+  for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+    KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_slot[i], cudaStreamNonBlocking, hi));
+    KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_slot[i], cudaEventDisableTiming));
+  }
+  KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_step, cudaEventDisableTiming));
+  KRR_CUDA_TRY(cudaMalloc(&S->table_dev, sizeof(ServeTable)));
+  KRR_CUDA_TRY(cudaMalloc(&S->init_dev, sizeof(ServeTable) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMalloc(&S->scalars_dev, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMalloc(&S->status_dev, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMalloc(&S->counters_dev, sizeof(int) * 64));
+  KRR_CUDA_TRY(cudaMemset(S->scalars_dev, 0, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMemset(S->status_dev, 0, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMemset(S->table_dev, 0, sizeof(ServeTable)));
+  KRR_CUDA_TRY(cudaMallocHost(&S->table_host, sizeof(ServeTable)));
+  KRR_CUDA_TRY(cudaMallocHost(&S->init_host, sizeof(ServeTable) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMallocHost(&S->status_host, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMallocHost(&S->ctl_host, sizeof(ServeControl) * SERVE_MAX_SLOTS));
+  KRR_CUDA_TRY(cudaMallocHost(&S->sumsq_host, sizeof(double) * SERVE_MAX_SLOTS * SERVE_MAX_M));
+  std::memset(S->table_host, 0, sizeof(ServeTable));
+  KRR_TRY(serve_configure_product());
+  if (S->cfg.hbm_budget_bytes > 0) {
+    S->budget = S->cfg.hbm_budget_bytes;
+  } else {
+    size_t fr = 0, tot = 0;
+    KRR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    S->budget = 0.9 * (double)fr;
+  }
+  KRR_CUDA_TRY(cudaDeviceSynchronize());
+  S->t0 = Clock::now();
+  S->builder = std::thread(builder_main, S);
+  return KRR_OK;
+}
+
+}  // namespace krr
+
+// ============================================================= C ABI
+extern "C" {
+
+krr_status krr_server_footprint(int64_t N, int d, int m, int k, double *bytes) {
+  krr::clear_error();
+  KRR_REQUIRE(bytes, "bytes is NULL");
+  KRR_REQUIRE(N >= 1 && d >= 1 && d <= 32 && m >= 1 && m <= 16 && k >= 0 && k <= N,
+              "bad request shape");
+  *bytes = krr::serve_footprint(N, d, m, k);
+  return KRR_OK;
+}
+
+krr_status krr_server_create(const krr_server_config *cfg, krr_server **out) {
+  krr::clear_error();
+  KRR_REQUIRE(cfg && out, "NULL argument");
+  *out = nullptr;
+  KRR_REQUIRE(cfg->max_slots >= 1 && cfg->max_slots <= KRR_SERVE_MAX_SLOTS,
+              "max_slots must be in [1, %d]", KRR_SERVE_MAX_SLOTS);
+  KRR_REQUIRE(cfg->iters_per_step >= 1 && cfg->iters_per_step <= 64,
+              "iters_per_step must be in [1, 64]");
+  KRR_REQUIRE(cfg->hbm_budget_bytes >= 0 && std::isfinite(cfg->hbm_budget_bytes),
+              "hbm_budget_bytes must be >= 0");
+  KRR_REQUIRE(cfg->reserved == 0, "reserved must be 0");
+  krr_server *S = new (std::nothrow) krr_server();
+  if (!S) return KRR_ENOMEM;
+  S->cfg = *cfg;
+  const krr_status st = krr::server_init(S);
+  if (st != KRR_OK) {
+    krr::server_free(S);
+    return st;
+  }
+  *out = S;
+  return KRR_OK;
+}
+
+krr_status krr_server_submit(krr_server *S, const double *X, int64_t N, int d, krr_kernel kern,
+                             double sigma, const double *Y, int m, double mu, int k,
+                             uint64_t seed, double tol, int maxit, double *alpha_out,
+                             int64_t *id_out) {
+  krr::clear_error();
+  KRR_REQUIRE(S && X && Y && alpha_out, "NULL argument");
+  KRR_REQUIRE(N >= 1 && N <= (int64_t)1 << 26, "N must be in [1, 2^26]");
+  KRR_REQUIRE(d >= 1 && d <= 32, "d must be in [1, 32]");
+  KRR_REQUIRE(kern == KRR_GAUSSIAN || kern == KRR_LAPLACE_L1 || kern == KRR_MATERN52,
+              "unknown kernel %d", (int)kern);
+  KRR_REQUIRE(sigma > 0 && std::isfinite(sigma), "sigma must be positive");
+  KRR_REQUIRE(m >= 1 && m <= 16, "m must be in [1, 16]");
+  KRR_REQUIRE(mu > 0 && std::isfinite(mu), "mu must be positive");
+  KRR_REQUIRE(k >= 0 && k <= N && k <= 4096, "k must be in [0, min(N, 4096)]");
+  KRR_REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+  KRR_REQUIRE(maxit >= 1, "maxit must be >= 1");
+  const double bytes = krr::serve_footprint(N, d, m, k);
+  if (bytes > S->budget) {
+    krr::set_error("request needs about %.3g bytes, more than the server's budget %.3g", bytes,
+                   S->budget);
+    return KRR_ENOMEM;
+  }
+  std::unique_ptr<Slot> sl(new (std::nothrow) Slot());
+  if (!sl) return KRR_ENOMEM;
+  sl->req_id = S->next_id++;
+  sl->X = X;
+  sl->Y = Y;
+  sl->alpha_out = alpha_out;
+  sl->N = N;
+  sl->d = d;
+  sl->kern = (int)kern;
+  sl->sigma = sigma;
+  sl->m = m;
+  sl->mu = mu;
+  sl->k = k;
+  sl->seed = seed;
+  sl->tol = tol;
+  sl->maxit = maxit;
+  sl->bytes = bytes;
+  sl->t_submit = S->now();
+  if (id_out) *id_out = sl->req_id;
+  S->queue.push_back(std::move(sl));
+  S->submitted += 1;
+  return KRR_OK;
+}
+
+krr_status krr_server_step(krr_server *S, int64_t *unfinished) {
+  krr::clear_error();
+  KRR_REQUIRE(S, "server is NULL");
+  return krr::server_step(S, unfinished);
+}
+
+krr_status krr_server_poll(krr_server *S, krr_request_result *out, int max_results, int *n_out) {
+  krr::clear_error();
+  KRR_REQUIRE(S && n_out, "NULL argument");
+  KRR_REQUIRE(max_results >= 0 && (out || max_results == 0), "bad result buffer");
+  const int n = std::min<int>(max_results, (int)S->done.size());
+  for (int i = 0; i < n; ++i) out[i] = S->done[i];
+  S->done.erase(S->done.begin(), S->done.begin() + n);
+  *n_out = n;
+  return KRR_OK;
+}
+
+krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *out) {
+  krr::clear_error();
+  KRR_REQUIRE(S && out, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = S->submitted;
+  out->completed = S->completed;
+  out->queued = (int64_t)S->queue.size();
+  int64_t adm = 0;
+  for (int i = 0; i < krr::SERVE_MAX_SLOTS; ++i) adm += S->slots[i] ? 1 : 0;
+  out->admitted = adm;
+  out->steps = S->steps;
+  out->step_kernels = S->step_kernels;
+  out->max_concurrent = S->max_concurrent;
+  out->reserved_bytes = S->reserved;
+  out->peak_reserved_bytes = S->peak_reserved;
+  out->budget_bytes = S->budget;
+  out->kernel_entries = S->entries_total;
+  return KRR_OK;
+}
+
+double krr_server_clock(const krr_server *S) { return S ? S->now() : 0.0; }
+
+void krr_server_destroy(krr_server *S) { krr::server_free(S); }
+
+}  // extern "C"

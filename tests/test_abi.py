@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "krr.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return re.findall(r"KRR_API\s+(?:krr_status|void|const char \*|uint64_t)\s*(\w+)\s*\(", text)
+    return re.findall(r"KRR_API\s+(?:krr_status|void|const char \*|uint64_t|double)\s*(\w+)\s*\(", text)
 
 
 @pytest.fixture(scope="module")
@@ -88,3 +88,43 @@ def test_argument_validation_before_any_launch(lib):
     _einval(lib.krr_sparse_sign(4, 8, 65, 0, p(rows), p(V), None), lib, "zeta")
     _einval(lib.krr_rpc_sample(p(V), 4, 0.0, 0, 0, 0, p(rows), C.byref(C.c_int()), None), lib,
             "ndraw")
+
+
+def test_server_footprint_is_host_only_and_monotone(lib):
+    """The admission estimate needs no device and grows with every size."""
+    def fp(N, d, m, k):
+        b = C.c_double()
+        assert lib.krr_server_footprint(N, d, m, k, C.byref(b)) == 0
+        return b.value
+    base = fp(20000, 8, 4, 1000)
+    assert base > 20000 * 1000 * 12          # at least the float64 + float32 factor
+    assert fp(40000, 8, 4, 1000) > base
+    assert fp(20000, 16, 4, 1000) > base   # same float-float tile height as d = 8
+    assert fp(20000, 8, 16, 1000) > base
+    assert fp(20000, 8, 4, 2000) > base
+    assert fp(20000, 8, 4, 0) < base
+    b = C.c_double()
+    _einval(lib.krr_server_footprint(0, 8, 4, 10, C.byref(b)), lib, "shape")
+    _einval(lib.krr_server_footprint(100, 8, 17, 10, C.byref(b)), lib, "shape")
+    _einval(lib.krr_server_footprint(100, 8, 4, 101, C.byref(b)), lib, "shape")
+
+
+def test_server_config_validation(lib):
+    import paper_2304_12465_gb300._native as N_
+    h = C.c_void_p()
+    for cfg, frag in [(N_.ServerConfig(0, 4, 1, 0, 0.0), "max_slots"),
+                      (N_.ServerConfig(65, 4, 1, 0, 0.0), "max_slots"),
+                      (N_.ServerConfig(4, 0, 1, 0, 0.0), "iters_per_step"),
+                      (N_.ServerConfig(4, 65, 1, 0, 0.0), "iters_per_step"),
+                      (N_.ServerConfig(4, 4, 1, 0, -1.0), "hbm_budget"),
+                      (N_.ServerConfig(4, 4, 1, 3, 0.0), "reserved")]:
+        _einval(lib.krr_server_create(C.byref(cfg), C.byref(h)), lib, frag)
+        assert not h.value
+    X = np.zeros((4, 2))
+    rid = C.c_int64()
+    p = C.c_void_p(X.ctypes.data)
+    _einval(lib.krr_server_submit(None, p, 4, 2, 0, 1.0, p, 1, 1e-3, 1, 0, 1e-6, 10, p,
+                                  C.byref(rid)), lib, "NULL")
+    n = C.c_int()
+    _einval(lib.krr_server_poll(None, None, 0, C.byref(n)), lib, "NULL")
+    _einval(lib.krr_server_step(None, None), lib, "server")
