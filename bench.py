@@ -51,6 +51,20 @@ def parse():
                     help="also time the plain float64 path (one step, slow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
+    ap.add_argument("--workload", default="c2", choices=["c2", "serving"],
+                    help="c2: one RPCholesky + refined PCG solve per step (headline); "
+                         "serving: a Poisson stream of solve requests through the server")
+    ap.add_argument("--requests", type=int, default=512, help="serving: stream length")
+    ap.add_argument("--n-max", type=int, default=200_000,
+                    help="serving: largest N of the log-uniform range [2000, n_max]")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="serving: mean arrivals per second (0: all at time 0)")
+    ap.add_argument("--slots", type=int, default=32, help="serving: max concurrent solves")
+    ap.add_argument("--iters-per-step", type=int, default=4, help="serving: PCG iterations/step")
+    ap.add_argument("--serving-log", default="",
+                    help="serving: write one JSON line per request to this file")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="c2: skip the bounded serving stream reported beside the headline")
     return ap.parse_args()
 
 
@@ -278,6 +292,132 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def serve_stream(K, reqs, rate, slots, iters_per_step, seed=5, log=""):
+    """Runs a request stream through the server: request i arrives at the i-th
+    point of a Poisson process of the given rate (all at once for rate 0) and
+    is submitted when the server clock passes its arrival time.  Inputs are
+    host arrays (copied to the device by the server), results land in host
+    arrays; latency = completion - arrival."""
+    from inputs import make_serving_request
+    data = [make_serving_request(r) for r in reqs]
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate > 0 else np.zeros(len(reqs))
+    arrive = np.cumsum(gaps) - gaps[0]
+    launches0 = K.krr_launch_count()
+    with K.KrrServer(max_slots=slots, iters_per_step=iters_per_step) as srv:
+        t0 = srv.clock()
+        nxt, done = 0, []
+        while True:
+            now = srv.clock() - t0
+            while nxt < len(reqs) and arrive[nxt] <= now:
+                r = reqs[nxt]
+                X, Y = data[nxt]
+                rid = srv.submit(X, r["kernel"], r["sigma"], Y, r["mu"], r["k"], tol=1e-6,
+                                 maxit=5000, seed=r["seed"])
+                assert rid == nxt
+                nxt += 1
+            left = srv.step()
+            done += srv.poll()
+            if nxt == len(reqs) and left == 0:
+                break
+        t_end = srv.clock() - t0
+        stats = srv.stats()
+    launches = K.krr_launch_count() - launches0
+    if log:
+        with open(log, "w") as fh:
+            for d in sorted(done, key=lambda d: d["id"]):
+                r = reqs[d["id"]]
+                fh.write(json.dumps({**{k: r[k] for k in ("N", "d", "kernel", "sigma", "mu", "m",
+                                                          "k", "seed")},
+                                     **{k: v for k, v in d.items() if k != "alpha"},
+                                     "arrive": float(arrive[d["id"]])}) + "\n")
+    lat = np.array([d["t_done"] - t0 - arrive[d["id"]] for d in done])
+    wait = np.array([d["t_admit"] - t0 - arrive[d["id"]] for d in done])
+    build = np.array([d["t_built"] - d["t_admit"] for d in done])
+    status = {}
+    for d in done:
+        status[d["status_name"]] = status.get(d["status_name"], 0) + 1
+    entries = float(sum(d["kernel_entries"] for d in done))
+    return {
+        "requests": len(reqs), "wall_s": t_end,
+        "solves_per_s": len(reqs) / t_end,
+        "kernel_evals_per_s": entries / t_end,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)),
+                         "p99": float(np.percentile(wait, 99))},
+        "build_s": {"p50": float(np.percentile(build, 50)),
+                    "p99": float(np.percentile(build, 99))},
+        "status": status,
+        "iters": {"p50": float(np.median([d["iters"] for d in done])),
+                  "max": int(max(d["iters"] for d in done))},
+        "rel_residual_max": float(max(d["rel_residual"] for d in done)),
+        "max_concurrent": stats["max_concurrent"], "steps": stats["steps"],
+        "step_device_s": stats["step_ms"] / 1e3, "build_thread_s": stats["build_s"],
+        "escalations": stats["escalations"], "escalate_thread_s": stats["escalate_s"],
+        "escalated_ok": sum(1 for d in done if d["escalated"] and d["status"] == 0),
+        "peak_reserved_gb": stats["peak_reserved_bytes"] / 1e9,
+        "gpu_launches": int(launches),
+        "arrival_rate_per_s": rate if rate > 0 else "all at t=0",
+        "slots": slots, "iters_per_step": iters_per_step,
+        "h2d_bytes": int(sum(a.nbytes + b.nbytes for a, b in data)),
+        "d2h_bytes": int(sum(8 * r["m"] * r["N"] for r in reqs)),
+    }
+
+
+def run_serving(args):
+    """Serving workload: a Poisson stream of KRR solve requests (N log-uniform
+    in [2000, 200000], d in {4, 8, 16, 32}, three kernels, sigma log-uniform
+    in [0.3, 3], mu log-uniform in [1e-8, 1e-4], 1-16 right-hand sides,
+    RPCholesky k = min(1000, N/10)), tol 1e-6; solves/s and p50/p99 latency."""
+    import torch
+    import paper_2304_12465_gb300 as K
+    from inputs import make_serving_stream
+
+    dist, rank, world = dist_setup(args.gpus)
+    K.load()
+    reqs = make_serving_stream(args.requests, seed=4 + rank, n_range=(2000, args.n_max))
+    warm = make_serving_stream(max(args.warmup, 1), seed=1000 + rank, n_range=(2000, 20000))
+    serve_stream(K, warm, 0.0, args.slots, args.iters_per_step)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    clocks.start()
+    res = serve_stream(K, reqs, args.rate, args.slots, args.iters_per_step,
+                       log=args.serving_log)
+    clk = clocks.stop()
+    wall = res["wall_s"]
+    if dist:
+        t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t[0])
+    value = world * args.requests / wall
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.requests, "warmup": len(warm), "ms_per_step": wall / args.requests * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson stream of {args.requests} KRR solve "
+                                   f"requests, N log-uniform [2000, {args.n_max}], "
+                                   "d in {4,8,16,32}, "
+                                   "Gaussian/Laplace/Matern-5/2, sigma log-uniform [0.3, 3], "
+                                   "mu log-uniform [1e-8, 1e-4], 1-16 RHS, "
+                                   "k = min(1000, N/10), tol 1e-6",
+                       "l2": "inputs larger than L2 (each request's points, factor and "
+                             "state are distinct)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "serving": res,
+            "e2e": {"value": value, "unit": "solves/s",
+                    "h2d_bytes_per_step": res["h2d_bytes"] // args.requests,
+                    "d2h_bytes_per_step": res["d2h_bytes"] // args.requests},
+            "clocks": clk, "gpu_launches": res["gpu_launches"],
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(w, target_s: float = 6.0):
     """The oracle's float64 product on a bounded sample of rows of the same
     workload, timed on this host's cores; kernel evaluations per second."""
@@ -341,6 +481,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_native(args)
 

@@ -323,8 +323,8 @@ KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
 /*                                                                            */
 /* Requests wait in a queue and are admitted in arrival order while a slot is */
 /* free and the sum of the admitted requests' estimated footprints           */
-/* (krr_server_footprint) stays within the server's HBM budget.  A builder    */
-/* thread with its own stream copies X and Y to the device and builds the     */
+/* (krr_server_footprint) stays within the server's HBM budget.  Builder      */
+/* threads, each with its own stream, copy X and Y to the device and build the*/
 /* factor, the Woodbury core and the prepared points; the solve then keeps    */
 /* them and its CG state resident.  Each krr_server_step advances the inner   */
 /* PCG iteration of every iterating request by iters_per_step iterations,     */
@@ -343,6 +343,7 @@ KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
 /* Threading: one host thread at a time may call a server's functions.        */
 /* ------------------------------------------------------------------------ */
 #define KRR_SERVE_MAX_SLOTS 64
+#define KRR_SERVE_MAX_BUILDERS 8
 
 typedef struct krr_server krr_server;
 
@@ -350,7 +351,7 @@ typedef struct {
   int max_slots;            /* concurrent requests, 1..KRR_SERVE_MAX_SLOTS    */
   int iters_per_step;       /* inner PCG iterations per step, 1..64           */
   int use_graph;            /* replay each step as one CUDA graph launch      */
-  int reserved;             /* must be 0                                      */
+  int build_threads;        /* builder threads (own streams), 0..8; 0: 4      */
   double hbm_budget_bytes;  /* admission budget; 0: 90% of the free HBM at    */
                             /* creation                                       */
 } krr_server_config;
@@ -363,10 +364,15 @@ typedef struct {
   int outer_refinements;
   int rank;                 /* RPCholesky rank                                */
   int m;
+  int escalated;            /* 1: the float32 inner iterations stalled and    */
+                            /* the solve finished with float64 CG vectors and */
+                            /* float-float products                           */
+  int reserved;
   double rel_residual;      /* worst column's relative residual, float64-     */
                             /* accurate product                               */
   double kernel_entries;    /* kernel entries evaluated by this request       */
   double t_submit, t_admit, t_built, t_done;   /* seconds on krr_server_clock */
+  char error[160];          /* message of a failed build ("" otherwise)       */
 } krr_request_result;
 
 typedef struct {
@@ -379,12 +385,20 @@ typedef struct {
   double peak_reserved_bytes;
   double budget_bytes;
   double kernel_entries;    /* over the completed requests                    */
+  double step_ms;           /* device time of the steps (CUDA events)         */
+  double build_s;           /* builder-thread wall time spent on builds       */
+  double escalate_s;        /* worker wall time spent on escalated solves     */
+  int64_t escalations;      /* requests handed to the float-float continuation */
+  /* device ms per kernel of the step, summed over steps, recorded only while */
+  /* krr_set_profiling is on and use_graph is 0: product, reduce, alpha,      */
+  /* update, resid, F^T r, its reduction, W t, W^T u, z, beta, direction      */
+  double phase_ms[12];
 } krr_server_stats;
 
 /* Estimated peak device bytes of one request (host-only; no GPU needed).     */
 KRR_API krr_status krr_server_footprint(int64_t N, int d, int m, int k, double *bytes);
 
-/* Creates a server on the current device (streams, a builder thread, the     */
+/* Creates a server on the current device (streams, builder threads, the     */
 /* device tables).  KRR_EINVAL for a config outside the documented ranges.    */
 KRR_API krr_status krr_server_create(const krr_server_config *cfg, krr_server **out);
 
@@ -410,7 +424,7 @@ KRR_API krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *o
 /* Seconds since the server was created (the clock of the result times).      */
 KRR_API double krr_server_clock(const krr_server *S);
 
-/* Waits for the device, stops the builder and frees everything.              */
+/* Waits for the device, stops the builders and frees everything.             */
 KRR_API void krr_server_destroy(krr_server *S);
 
 /* Timing instrumentation: while on (non-zero), solves record CUDA events

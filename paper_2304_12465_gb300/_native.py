@@ -36,18 +36,20 @@ class KrrInfo(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_slots", C.c_int), ("iters_per_step", C.c_int), ("use_graph", C.c_int),
-                ("reserved", C.c_int), ("hbm_budget_bytes", C.c_double)]
+                ("build_threads", C.c_int), ("hbm_budget_bytes", C.c_double)]
 
 
 class RequestResult(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int), ("iters", C.c_int),
                 ("outer_refinements", C.c_int), ("rank", C.c_int), ("m", C.c_int),
-                ("rel_residual", C.c_double), ("kernel_entries", C.c_double),
+                ("escalated", C.c_int), ("reserved", C.c_int), ("rel_residual", C.c_double), ("kernel_entries", C.c_double),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_built", C.c_double),
-                ("t_done", C.c_double)]
+                ("t_done", C.c_double), ("error", C.c_char * 160)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["error"] = d["error"].decode(errors="replace")
+        return d
 
 
 class ServerStats(C.Structure):
@@ -55,10 +57,17 @@ class ServerStats(C.Structure):
                 ("admitted", C.c_int64), ("steps", C.c_int64), ("step_kernels", C.c_int64),
                 ("max_concurrent", C.c_int), ("reserved", C.c_int),
                 ("reserved_bytes", C.c_double), ("peak_reserved_bytes", C.c_double),
-                ("budget_bytes", C.c_double), ("kernel_entries", C.c_double)]
+                ("budget_bytes", C.c_double), ("kernel_entries", C.c_double),
+                ("step_ms", C.c_double), ("build_s", C.c_double), ("escalate_s", C.c_double),
+                ("escalations", C.c_int64), ("phase_ms", C.c_double * 12)]
+
+    PHASES = ("product", "reduce", "alpha", "update", "resid", "ft_r", "ft_r_reduce", "w_t",
+              "wt_u", "z", "beta", "direction")
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
+        return d
 
 
 class KrrError(RuntimeError):

@@ -383,10 +383,10 @@ class KrrServer:
     """
 
     def __init__(self, max_slots: int = 16, iters_per_step: int = 4, use_graph: bool = True,
-                 hbm_budget_bytes: float = 0.0):
+                 hbm_budget_bytes: float = 0.0, build_threads: int = 0):
         lib = load()
-        cfg = N_.ServerConfig(int(max_slots), int(iters_per_step), 1 if use_graph else 0, 0,
-                              float(hbm_budget_bytes))
+        cfg = N_.ServerConfig(int(max_slots), int(iters_per_step), 1 if use_graph else 0,
+                              int(build_threads), float(hbm_budget_bytes))
         h = C.c_void_p()
         check(lib.krr_server_create(C.byref(cfg), C.byref(h)), "krr_server_create")
         self._h = h

@@ -29,6 +29,25 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_error.clear(); }
 
+krr_status raise_smem_limit_ptr(const void *func, size_t bytes) {
+  static std::mutex mtx;
+  static std::vector<std::pair<const void *, size_t>> limits;
+  std::lock_guard<std::mutex> lk(mtx);
+  for (auto &e : limits) {
+    if (e.first != func) continue;
+    if (bytes <= e.second) return KRR_OK;
+    KRR_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+    e.second = bytes;
+    return KRR_OK;
+  }
+  if (bytes > 48 * 1024)
+    KRR_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+  limits.emplace_back(func, bytes > 48 * 1024 ? bytes : 48 * 1024);
+  return KRR_OK;
+}
+
 static thread_local cudaStream_t g_alloc_stream = nullptr;
 void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
 cudaStream_t alloc_stream() { return g_alloc_stream; }
@@ -45,7 +64,11 @@ bool is_device_ptr(const void *p) {
 }
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool g_count_launches = true;
+void set_launch_counting(bool on) { g_count_launches = on; }
+void count_launch() {
+  if (g_count_launches) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int num_sms() {

@@ -29,6 +29,9 @@ void clear_error();
 // Counts this library's kernel launches (reported by krr_launch_count).
 void count_launch();
 void count_launches(unsigned long long n);
+// Off while this thread captures a CUDA graph: its launches are counted when
+// the graph is launched.
+void set_launch_counting(bool on);
 
 #define KRR_LAUNCH_CHECK()          \
   do {                              \
@@ -49,6 +52,16 @@ void count_launches(unsigned long long n);
       return KRR_EINVAL;                                                        \
     }                                                                           \
   } while (0)
+
+// Raises a kernel's dynamic shared memory limit to at least `bytes` and never
+// lowers it: host threads that run in parallel (the serving engine's
+// builders) launch the same kernels with different sizes, and a lower limit
+// set by one thread would make another thread's larger launch fail.
+krr_status raise_smem_limit_ptr(const void *func, size_t bytes);
+template <typename F>
+krr_status raise_smem_limit(F *func, size_t bytes) {
+  return raise_smem_limit_ptr((const void *)func, bytes);
+}
 
 // ------------------------------------------------------- device buffers
 // Stream-ordered scratch owned by one call (cudaMallocAsync / cudaFreeAsync).

@@ -314,8 +314,7 @@ potrf_diag_kernel(double *__restrict__ A, int w, int64_t lda, double *__restrict
 static krr_status diag_block(double *A, int w, int64_t lda, double *Dinv, int *status,
                              int factor, cudaStream_t s) {
   const size_t smem = 2 * CH_NB * (CH_NB + 1) * sizeof(double);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KRR_TRY(raise_smem_limit(potrf_diag_kernel, smem));
   potrf_diag_kernel<<<1, 256, smem, s>>>(A, w, lda, Dinv, status, factor);
   KRR_LAUNCH_CHECK();
   return KRR_OK;

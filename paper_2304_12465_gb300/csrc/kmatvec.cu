@@ -520,10 +520,7 @@ krr_status kernel_columns_f64(const double *Xd, int64_t N, int d, int kern, doub
   for (int c0 = 0; c0 < nc; c0 += 128) {
     const int ncg = (nc - c0 < 128) ? nc - c0 : 128;
     const size_t smem = (size_t)ncg * d * sizeof(double);
-    if (smem > 48 * 1024)
-      KRR_CUDA_TRY(cudaFuncSetAttribute(kernel_columns_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+    KRR_TRY(raise_smem_limit(kernel_columns_kernel, smem));
     kernel_columns_kernel<<<ceil_div(N, 128), 128, smem, s>>>(
         Xd, N, d, kern, sigma, cols + c0, ncg, G + (int64_t)c0 * ldg, ldg);
     KRR_LAUNCH_CHECK();

@@ -470,8 +470,7 @@ krr_status krill_build_device(krill_precond *P, cudaStream_t s) {
   KRR_TRY(rowptr.alloc(sr + 1, s));
   KRR_TRY(off.alloc((size_t)nch * sr, s));
   const size_t hsm = (size_t)sr * sizeof(int);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(row_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(hsm > 48 * 1024 ? hsm : 48 * 1024)));
+  KRR_TRY(raise_smem_limit(row_hist_kernel, hsm));
   row_hist_kernel<<<nch, 256, hsm, s>>>(rows.p, N, zeta, sr, hist.p);
   KRR_LAUNCH_CHECK();
   row_total_kernel<<<ceil_div(sr, 256), 256, 0, s>>>(hist.p, nch, sr, total.p);
@@ -481,8 +480,7 @@ krr_status krill_build_device(krill_precond *P, cudaStream_t s) {
   row_offsets_kernel<<<ceil_div(sr, 256), 256, 0, s>>>(hist.p, nch, sr, rowptr.p, off.p);
   KRR_LAUNCH_CHECK();
   const size_t fsm = (size_t)sr * sizeof(int64_t);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(row_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(fsm > 48 * 1024 ? fsm : 48 * 1024)));
+  KRR_TRY(raise_smem_limit(row_fill_kernel, fsm));
   row_fill_kernel<<<nch, 32, fsm, s>>>(rows.p, vals.p, N, zeta, sr, off.p, col_n.p, col_v.p);
   KRR_LAUNCH_CHECK();
   // sketch

@@ -173,8 +173,7 @@ static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const doub
   KRR_TRY(u.alloc((size_t)rank * m, s));
   KRR_TRY(v.alloc((size_t)rank * m, s));
   const size_t smem = (size_t)m * TT_ROWS * sizeof(T);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(tall_t_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+  KRR_TRY(raise_smem_limit(tall_t_kernel<T>, smem));
   tall_t_kernel<T><<<nb, 256, smem, s>>>(F, N, rank, R, m, part.p);
   KRR_LAUNCH_CHECK();
   tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 8), 256, 0, s>>>(part.p, nb, rank, m,

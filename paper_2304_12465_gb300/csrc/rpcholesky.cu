@@ -299,12 +299,8 @@ krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, doubl
   KRR_TRY(Lb.alloc((size_t)B * B, s));
 
   const size_t chol_smem = (size_t)B * B * sizeof(double);
-  KRR_CUDA_TRY(cudaFuncSetAttribute(block_chol_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(chol_smem > 48 * 1024 ? chol_smem : 48 * 1024)));
-  KRR_CUDA_TRY(cudaFuncSetAttribute(block_trsm_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(chol_smem > 48 * 1024 ? chol_smem : 48 * 1024)));
+  KRR_TRY(raise_smem_limit(block_chol_kernel, chol_smem));
+  KRR_TRY(raise_smem_limit(block_trsm_kernel, chol_smem));
 
   int rank = 0;
   uint64_t t = 0;

@@ -473,45 +473,117 @@ __global__ void __launch_bounds__(1024) serve_sumsq_kernel(const double *__restr
   }
 }
 
+__global__ void serve_add_f64_kernel(double *__restrict__ x, const double *__restrict__ d,
+                                     int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += d[e];
+}
+
 static unsigned serve_vec_grid() { return (unsigned)(num_sms() * 4); }
 
-static krr_status serve_launch_precond(const ServeTable *T, cudaStream_t s) {
+// Optional per-kernel timing of a step (events after every launch).
+struct PhaseEvents {
+  std::vector<cudaEvent_t> ev;   // U * SERVE_KERNELS_PER_ITER + 1
+  size_t next = 0;
+  krr_status mark(cudaStream_t s) {
+    if (ev.empty()) return KRR_OK;
+    KRR_CUDA_TRY(cudaEventRecord(ev[next++], s));
+    return KRR_OK;
+  }
+};
+
+static krr_status serve_launch_precond(const ServeTable *T, cudaStream_t s,
+                                       PhaseEvents *pe = nullptr) {
   const unsigned g = serve_vec_grid();
   serve_tt_kernel<<<g, 256, 0, s>>>(T);
   KRR_LAUNCH_CHECK();
+  if (pe) KRR_TRY(pe->mark(s));
   serve_ttred_kernel<<<g, 256, 0, s>>>(T);
   KRR_LAUNCH_CHECK();
+  if (pe) KRR_TRY(pe->mark(s));
   serve_tri_kernel<false><<<g, 256, 0, s>>>(T);
   KRR_LAUNCH_CHECK();
+  if (pe) KRR_TRY(pe->mark(s));
   serve_tri_kernel<true><<<g, 256, 0, s>>>(T);
   KRR_LAUNCH_CHECK();
+  if (pe) KRR_TRY(pe->mark(s));
   serve_tn_kernel<<<g, SERVE_VB, 0, s>>>(T);
   KRR_LAUNCH_CHECK();
+  if (pe) KRR_TRY(pe->mark(s));
   return KRR_OK;
 }
 
 // U inner PCG iterations of every slot in T (SERVE_KERNELS_PER_ITER kernels
 // each), in the order of the single-solve loop: product, alpha, update,
 // convergence test, preconditioner, beta, direction.
-static krr_status serve_launch_iterations(const ServeTable *T, int *counters, int U,
-                                          cudaStream_t s) {
+// Streams and events of the product's parallel branches.
+constexpr int SERVE_BRANCHES = 8;
+struct ProductBranches {
+  cudaStream_t side[SERVE_BRANCHES] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[SERVE_BRANCHES] = {};
+};
+
+// (A + lambda I) p partial sums of every slot of T: one launch per variant
+// present (Th: host copy of the table at T), forked onto parallel branches and
+// joined back into s.
+static krr_status serve_launch_product(const ServeTable *T, const ServeTable *Th,
+                                       const ProductBranches &B, cudaStream_t s) {
+  const int nc = Th->nclasses;
+  if (nc == 0) return KRR_OK;
+  const int nb = nc < SERVE_BRANCHES ? nc : SERVE_BRANCHES;
+  KRR_CUDA_TRY(cudaEventRecord(B.fork, s));
+  for (int b = 0; b < nb; ++b) KRR_CUDA_TRY(cudaStreamWaitEvent(B.side[b], B.fork, 0));
+  for (int c = 0; c < nc; ++c) {
+    const ServeClass &C = Th->cls[c];
+    const ServeSlotDesc &d0 = Th->slot[C.slot[0]];
+    const int items = C.off[C.nslots];
+    cudaStream_t bs = B.side[c % nb];
+    cudaError_t e = cudaErrorInvalidValue;
+    if (d0.kern == KGAUSS) e = serve_launch_product_gauss(d0.dp, d0.M, items, T, c, bs);
+    else if (d0.kern == KLAPLACE) e = serve_launch_product_laplace(d0.dp, d0.M, items, T, c, bs);
+    else if (d0.kern == KMATERN) e = serve_launch_product_matern(d0.dp, d0.M, items, T, c, bs);
+    count_launch();
+    KRR_CUDA_TRY(e);
+  }
+  for (int b = 0; b < nb; ++b) {
+    KRR_CUDA_TRY(cudaEventRecord(B.join[b], B.side[b]));
+    KRR_CUDA_TRY(cudaStreamWaitEvent(s, B.join[b], 0));
+  }
+  return KRR_OK;
+}
+
+// U inner PCG iterations of every slot in T, in the order of the
+// single-solve loop: product, alpha, update, convergence test,
+// preconditioner, beta, direction.
+static krr_status serve_launch_iterations(const ServeTable *T, const ServeTable *Th,
+                                          const ProductBranches &B, int U, cudaStream_t s,
+                                          PhaseEvents *pe = nullptr) {
   const unsigned g = serve_vec_grid();
-  KRR_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int) * U, s));
+  if (pe) KRR_TRY(pe->mark(s));
   for (int it = 0; it < U; ++it) {
-    KRR_TRY(serve_launch_product(T, counters + it, s));
+    KRR_TRY(serve_launch_product(T, Th, B, s));
+    if (pe) KRR_TRY(pe->mark(s));
     serve_reduce_kernel<<<g, SERVE_VB, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
+    if (pe) KRR_TRY(pe->mark(s));
     serve_alpha_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
+    if (pe) KRR_TRY(pe->mark(s));
     serve_update_kernel<<<g, SERVE_VB, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
+    if (pe) KRR_TRY(pe->mark(s));
     serve_resid_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
-    KRR_TRY(serve_launch_precond(T, s));
+    if (pe) KRR_TRY(pe->mark(s));
+    KRR_TRY(serve_launch_precond(T, s, pe));
     serve_beta_kernel<<<1, SERVE_COL_THREADS, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
+    if (pe) KRR_TRY(pe->mark(s));
     serve_dir_kernel<<<g, SERVE_VB, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
+    if (pe) KRR_TRY(pe->mark(s));
   }
   return KRR_OK;
 }
@@ -578,7 +650,7 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-enum class Phase { Queued, Building, Norms, Init, Inner, Refine, Final };
+enum class Phase { Queued, Building, Norms, Init, Inner, Refine, Escalated, Final };
 
 struct Slot {
   // request
@@ -588,7 +660,8 @@ struct Slot {
   double *alpha_out = nullptr;
   int64_t N = 0;
   int d = 0, kern = 0, m = 0, k = 0, maxit = 0;
-  double sigma = 0, mu = 0, tol = 0, bytes = 0;
+  double sigma = 0, mu = 0, tol = 0;
+  int64_t bytes = 0;
   uint64_t seed = 0;
   double t_submit = 0, t_admit = 0, t_built = 0;
   // engine state
@@ -610,6 +683,9 @@ struct Slot {
   int outer = 0, iters = 0, budget = 0;
   double prev_worst = 1e300, relres = 1.0, entries = 0.0;
   bool breakdown = false, first_norms = true;
+  int inner_limit = 0;
+  bool inner_capped = false;   // the last inner solve stopped at its limit
+  bool escalated = false;      // finished with float-float inner products
   krr_status status = KRR_OK;
 };
 
@@ -619,16 +695,20 @@ struct krr_server {
   krr_server_config cfg{};
   int device = 0;
   Clock::time_point t0;
-  cudaStream_t s_iter = nullptr, s_build = nullptr, s_free = nullptr;
+  cudaStream_t s_iter = nullptr, s_free = nullptr;
+  cudaStream_t s_build[krr::SERVE_MAX_BUILDERS] = {};
+  int nbuilders = 0;
   cudaStream_t s_slot[krr::SERVE_MAX_SLOTS] = {};
   cudaEvent_t ev_slot[krr::SERVE_MAX_SLOTS] = {};
   cudaEvent_t ev_step = nullptr;
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // device time of a step
   // device
   ServeTable *table_dev = nullptr;
   ServeTable *init_dev = nullptr;      // one single-slot table per slot index
   ServeScalars *scalars_dev = nullptr;
   ServeStatus *status_dev = nullptr;
-  int *counters_dev = nullptr;
+  krr::ProductBranches branches;
+  int64_t captures = 0;
   // pinned host
   ServeTable *table_host = nullptr;
   ServeTable *init_host = nullptr;
@@ -641,17 +721,22 @@ struct krr_server {
   std::deque<std::unique_ptr<Slot>> queue;
   std::vector<krr_request_result> done;
   bool table_dirty = true;
-  // builder
-  std::thread builder;
+  // builders
+  std::vector<std::thread> builders;
   std::mutex mtx;
   std::condition_variable cv;
   std::deque<Slot *> build_q;
   std::vector<Slot *> built;
   bool stop = false;
   // accounting
-  double budget = 0, reserved = 0, peak_reserved = 0, entries_total = 0;
+  int64_t budget = 0, reserved = 0, peak_reserved = 0;
+  double entries_total = 0;
   int64_t next_id = 0, submitted = 0, completed = 0, steps = 0, step_kernels = 0;
   int max_concurrent = 0;
+  double step_ms = 0, build_s = 0, escalate_s = 0;
+  double phase_ms[krr::SERVE_KERNELS_PER_ITER] = {};
+  krr::PhaseEvents phase_ev;
+  int64_t escalations = 0;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -665,11 +750,23 @@ static size_t table_bytes(int nslots) {
 static void table_add(ServeTable *T, const ServeSlotDesc &d) {
   const int s = T->nslots;
   if (s == 0) {
-    T->prod_off[0] = T->vec_off[0] = T->tt_off[0] = T->ttr_off[0] = T->tri_off[0] =
-        T->col_off[0] = 0;
+    T->vec_off[0] = T->tt_off[0] = T->ttr_off[0] = T->tri_off[0] = T->col_off[0] = 0;
+    T->nclasses = 0;
   }
   T->slot[s] = d;
-  T->prod_off[s + 1] = T->prod_off[s] + d.row_tiles * d.splits;
+  // the slot joins the product launch of its variant
+  int c = 0;
+  while (c < T->nclasses && T->cls[c].variant != d.variant) ++c;
+  if (c == T->nclasses) {
+    T->cls[c].variant = d.variant;
+    T->cls[c].nslots = 0;
+    T->cls[c].off[0] = 0;
+    T->nclasses += 1;
+  }
+  ServeClass &C = T->cls[c];
+  C.slot[C.nslots] = s;
+  C.off[C.nslots + 1] = C.off[C.nslots] + d.row_tiles * d.splits;
+  C.nslots += 1;
   T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
   T->tt_off[s + 1] = T->tt_off[s] + d.nbt;
   T->ttr_off[s + 1] = T->ttr_off[s] + (d.rank > 0 ? d.rank * d.m : 0);
@@ -682,8 +779,7 @@ template <typename T>
 static void rebind(DevBuf<T> &b, cudaStream_t s) { b.s = s; }
 
 // ------------------------------------------------------------- build
-static krr_status build_slot(krr_server *S, Slot *sl) {
-  cudaStream_t s = S->s_build;
+static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   const int64_t N = sl->N;
   const int d = sl->d, m = sl->m;
   DevBuf<double> xtmp;
@@ -789,9 +885,114 @@ static krr_status build_slot(krr_server *S, Slot *sl) {
   return KRR_OK;
 }
 
-static void builder_main(krr_server *S) {
+static double worst_rel(const Slot *sl);
+
+// Higher-precision continuation of a solve whose float32 inner iterations
+// stopped making progress (the float32 product's rounding exceeds the shift
+// lambda for very small mu): the same refinement loop with float64 CG
+// vectors, the float-float product inside the inner PCG and the Woodbury
+// preconditioner applied in float64 to the float32 factor it was built from.
+// Runs on a worker thread; the slot's data are not used by anything else.
+static krr_status escalate_slot(krr_server *S, Slot *sl, cudaStream_t s) {
+  (void)S;
+  const int64_t N = sl->N, nm = N * sl->m;
+  const int m = sl->m;
+  const double lambda = sl->mu * (double)N;
+  DevBuf<double> b64, d64, F64;
+  KRR_TRY(b64.alloc((size_t)nm, s));
+  KRR_TRY(d64.alloc((size_t)nm, s));
+  krr_factor view;   // float64 copy of the float32 factor (exactly representable)
+  view.N = N;
+  NystromCore identity;
+  identity.lambda = lambda;
+  const NystromCore *core = sl->core ? sl->core : &identity;
+  if (sl->core && sl->core->rank > 0) {
+    KRR_TRY(F64.alloc((size_t)N * sl->core->rank, s));
+    KRR_TRY(convert_f32_to_f64(sl->core->F32, F64.p, N * sl->core->rank, s));
+    view.F = F64.p;
+  }
+  PcgOps<double> ops;
+  ops.product = [&](const double *in, double *out, cudaStream_t st) {
+    return kmv_ff(sl->Pff, lambda, in, N, m, out, N, st, sl->ffpart, sl->ffvsplit);
+  };
+  ops.precond = [&](const double *in, double *out, cudaStream_t st) {
+    return nystrom_apply_f64(&view, core, in, m, out, st);
+  };
+  // second stage: when even these residuals stall (the float-float product's
+  // own rounding, about 2^-48 of sum_j |a_ij x_j|, is then of the order of
+  // the residual), residuals come from the float64 product on the caller's X
+  DevBuf<double> X64, part64;
+  bool res64 = false;
+  auto residual64 = [&]() -> krr_status {
+    KRR_TRY(kmv_f64(X64.p, N, sl->d, sl->kern, sl->sigma, lambda, sl->alpha64, N, m, sl->mx64,
+                    N, s, part64));
+    sl->entries += kmv_entries(N);
+    KRR_TRY(residual_f64(sl->Y64, sl->mx64, sl->r64, nm, s));
+    return column_norms(sl->r64, N, m, sl->rn.data(), s);
+  };
+  sl->escalated = true;
+  krr_status final_status = KRR_ENOCONV;
+  double prev = 1e300;
+  for (int outer = 0;; ++outer) {
+    double worst = worst_rel(sl);
+    sl->relres = worst;
+    if (worst <= sl->tol) { final_status = KRR_OK; break; }
+    if (outer >= 10 || sl->budget <= 0) break;
+    if (outer > 0 && worst > 0.5 * prev) {
+      if (res64) break;
+      res64 = true;
+      KRR_TRY(X64.alloc((size_t)N * sl->d, s));
+      KRR_CUDA_TRY(cudaMemcpyAsync(X64.p, sl->X, sizeof(double) * N * sl->d, cudaMemcpyDefault,
+                                   s));
+      KRR_TRY(residual64());
+      worst = worst_rel(sl);
+      sl->relres = worst;
+      if (worst <= sl->tol) { final_status = KRR_OK; break; }
+    }
+    prev = worst;
+    std::vector<double> itol(m);
+    KRR_CUDA_TRY(cudaMemcpyAsync(b64.p, sl->r64, sizeof(double) * nm, cudaMemcpyDeviceToDevice,
+                                 s));
+    for (int c = 0; c < m; ++c) {
+      const double rel = sl->yn[c] > 0 ? sl->rn[c] / sl->yn[c] : 0.0;
+      itol[c] = rel > sl->tol ? std::max(0.3 * sl->tol / rel, 1e-12) : 1.0;
+      if (!(rel > sl->tol))
+        KRR_CUDA_TRY(cudaMemsetAsync(b64.p + (int64_t)c * N, 0, sizeof(double) * N, s));
+    }
+    PcgStats st;
+    KRR_TRY(pcg_run<double>(ops, N, m, b64.p, d64.p, itol.data(), sl->budget, s, &st));
+    sl->iters += st.iters_max;
+    sl->budget -= st.iters_max;
+    sl->entries += kmv_entries(N) * (st.products + 1);
+    serve_add_f64_kernel<<<serve_vec_grid(), 256, 0, s>>>(sl->alpha64, d64.p, nm);
+    KRR_LAUNCH_CHECK();
+    if (res64) {
+      KRR_TRY(residual64());
+    } else {
+      KRR_TRY(kmv_ff(sl->Pff, lambda, sl->alpha64, N, m, sl->mx64, N, s, sl->ffpart,
+                     sl->ffvsplit));
+      KRR_TRY(residual_f64(sl->Y64, sl->mx64, sl->r64, nm, s));
+      KRR_TRY(column_norms(sl->r64, N, m, sl->rn.data(), s));
+    }
+    sl->outer += 1;
+    if (st.breakdown) {
+      final_status = KRR_EBREAKDOWN;
+      break;
+    }
+  }
+  if (final_status != KRR_OK) {
+    sl->relres = worst_rel(sl);
+    if (sl->relres <= sl->tol) final_status = KRR_OK;
+  }
+  view.F = nullptr;
+  sl->status = final_status;
+  return KRR_OK;
+}
+
+static void builder_main(krr_server *S, int b) {
   cudaSetDevice(S->device);
-  set_alloc_stream(S->s_build);
+  cudaStream_t s = S->s_build[b];
+  set_alloc_stream(s);
   for (;;) {
     Slot *sl = nullptr;
     {
@@ -802,11 +1003,25 @@ static void builder_main(krr_server *S) {
       S->build_q.pop_front();
     }
     clear_error();
-    const krr_status st = build_slot(S, sl);
-    if (st != KRR_OK) cudaStreamSynchronize(S->s_build);
+    const bool esc = sl->phase == Phase::Escalated;
+    const auto t0 = Clock::now();
+    const krr_status st = esc ? escalate_slot(S, sl, s) : build_slot(S, sl, s);
+    cudaStreamSynchronize(s);
+    const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
     {
       std::lock_guard<std::mutex> lk(S->mtx);
-      sl->build_status = st;
+      if (esc) {
+        S->escalate_s += dt;
+        S->escalations += 1;
+      } else {
+        S->build_s += dt;
+      }
+      if (esc) {
+        // a failure of the launches themselves ends the request with it
+        if (st != KRR_OK) sl->status = st;
+      } else {
+        sl->build_status = st;
+      }
       if (st != KRR_OK) sl->error = krr_last_error();
       S->built.push_back(sl);
     }
@@ -823,12 +1038,14 @@ static void complete(krr_server *S, Slot *sl, krr_status st) {
   r.outer_refinements = sl->outer;
   r.rank = sl->desc.rank;
   r.m = sl->m;
+  r.escalated = sl->escalated ? 1 : 0;
   r.rel_residual = sl->relres;
   r.kernel_entries = sl->entries;
   r.t_submit = sl->t_submit;
   r.t_admit = sl->t_admit;
   r.t_built = sl->t_built;
   r.t_done = S->now();
+  std::snprintf(r.error, sizeof(r.error), "%s", sl->error.c_str());
   S->done.push_back(r);
   S->completed += 1;
   S->entries_total += sl->entries;
@@ -870,16 +1087,30 @@ static double worst_rel(const Slot *sl) {
   return w;
 }
 
+static void escalate(krr_server *S, Slot *sl) {
+  sl->phase = Phase::Escalated;
+  {
+    std::lock_guard<std::mutex> lk(S->mtx);
+    S->build_q.push_back(sl);
+  }
+  S->cv.notify_one();
+}
+
 // One decision of the refinement loop after a float64 residual is known.
 static krr_status decide(krr_server *S, Slot *sl) {
   constexpr int kMaxOuter = 12;
   constexpr double kInnerFloor = 1e-4;
+  constexpr int kInnerCap = 1000;   // iterations of one float32 inner solve
   const double worst = worst_rel(sl);
   sl->relres = worst;
   if (worst <= sl->tol) return finalize(S, sl, KRR_OK);
-  if (sl->breakdown) return finalize(S, sl, KRR_EBREAKDOWN);
-  if (sl->outer >= kMaxOuter || sl->budget <= 0) return finalize(S, sl, KRR_ENOCONV);
-  if (sl->outer > 0 && worst > 0.5 * sl->prev_worst) return finalize(S, sl, KRR_ENOCONV);
+  // float32 inner solves that break down, run into their cap or stop
+  // reducing the residual hand the solve to the float-float continuation
+  if (sl->breakdown || sl->inner_capped || sl->outer >= kMaxOuter || sl->budget <= 0 ||
+      (sl->outer > 0 && worst > 0.5 * sl->prev_worst)) {
+    escalate(S, sl);
+    return KRR_OK;
+  }
   sl->prev_worst = worst;
   ServeControl &ctl = S->ctl_host[sl->id];
   std::memset(&ctl, 0, sizeof(ctl));
@@ -888,7 +1119,8 @@ static krr_status decide(krr_server *S, Slot *sl) {
     ctl.need[c] = rel > sl->tol ? 1 : 0;
     ctl.tol[c] = ctl.need[c] ? std::max(0.3 * sl->tol / rel, kInnerFloor) : 1.0;
   }
-  ctl.limit = sl->budget;
+  ctl.limit = std::min(sl->budget, kInnerCap);
+  sl->inner_limit = ctl.limit;
   cudaStream_t ss = S->s_slot[sl->id];
   KRR_CUDA_TRY(cudaMemcpyAsync(&S->scalars_dev[sl->id].ctl, &ctl, sizeof(ServeControl),
                                cudaMemcpyHostToDevice, ss));
@@ -913,6 +1145,7 @@ static krr_status start_refine(krr_server *S, Slot *sl) {
 }
 
 static krr_status on_built(krr_server *S, Slot *sl) {
+  if (sl->phase == Phase::Escalated) return finalize(S, sl, sl->status);
   sl->t_built = S->now();
   if (sl->build_status != KRR_OK) {
     sl->relres = 1.0;
@@ -987,12 +1220,19 @@ static void admit(krr_server *S) {
 
 static krr_status launch_step(krr_server *S, int nslots) {
   const int U = S->cfg.iters_per_step;
+  const ServeTable *Th = S->table_host;
+  const unsigned long long kernels =
+      (unsigned long long)U * (SERVE_KERNELS_PER_ITER - 1 + Th->nclasses);
   if (S->cfg.use_graph) {
     if (!S->graph) {
+      // the launch sequence depends on the variants present: captured again
+      // whenever the slot set changes
       cudaGraph_t g = nullptr;
+      set_launch_counting(false);
       KRR_CUDA_TRY(cudaStreamBeginCapture(S->s_iter, cudaStreamCaptureModeThreadLocal));
-      krr_status st = serve_launch_iterations(S->table_dev, S->counters_dev, U, S->s_iter);
+      krr_status st = serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter);
       cudaError_t e = cudaStreamEndCapture(S->s_iter, &g);
+      set_launch_counting(true);
       if (st != KRR_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
@@ -1001,14 +1241,25 @@ static krr_status launch_step(krr_server *S, int nslots) {
       e = cudaGraphInstantiate(&S->graph, g, 0);
       cudaGraphDestroy(g);
       KRR_CUDA_TRY(e);
+      S->captures += 1;
     }
     KRR_CUDA_TRY(cudaGraphLaunch(S->graph, S->s_iter));
-    count_launches((unsigned long long)U * SERVE_KERNELS_PER_ITER);
+    count_launches(kernels);
+  } else if (profiling_on()) {
+    PhaseEvents &pe = S->phase_ev;
+    const size_t need = (size_t)U * SERVE_KERNELS_PER_ITER + 1;
+    while (pe.ev.size() < need) {
+      cudaEvent_t e;
+      KRR_CUDA_TRY(cudaEventCreate(&e));
+      pe.ev.push_back(e);
+    }
+    pe.next = 0;
+    KRR_TRY(serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter, &pe));
   } else {
-    KRR_TRY(serve_launch_iterations(S->table_dev, S->counters_dev, U, S->s_iter));
+    KRR_TRY(serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter));
   }
   S->steps += 1;
-  S->step_kernels += (int64_t)U * SERVE_KERNELS_PER_ITER;
+  S->step_kernels += (int64_t)kernels;
   S->max_concurrent = std::max(S->max_concurrent, nslots);
   return KRR_OK;
 }
@@ -1052,8 +1303,14 @@ static krr_status server_step(krr_server *S, int64_t *unfinished) {
       KRR_CUDA_TRY(cudaMemcpyAsync(S->table_dev, T, table_bytes(T->nslots),
                                    cudaMemcpyHostToDevice, S->s_iter));
       S->table_dirty = false;
+      if (S->graph) {
+        KRR_CUDA_TRY(cudaGraphExecDestroy(S->graph));
+        S->graph = nullptr;
+      }
     }
+    KRR_CUDA_TRY(cudaEventRecord(S->ev_t0, S->s_iter));
     KRR_TRY(launch_step(S, (int)inner.size()));
+    KRR_CUDA_TRY(cudaEventRecord(S->ev_t1, S->s_iter));
     KRR_CUDA_TRY(cudaMemcpyAsync(S->status_host, S->status_dev,
                                  sizeof(ServeStatus) * SERVE_MAX_SLOTS, cudaMemcpyDeviceToHost,
                                  S->s_iter));
@@ -1066,6 +1323,17 @@ static krr_status server_step(krr_server *S, int64_t *unfinished) {
       KRR_TRY(service(S));
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    float ms = 0.0f;
+    KRR_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev_t0, S->ev_t1));
+    S->step_ms += ms;
+    if (S->phase_ev.next > 1) {
+      for (size_t e = 1; e < S->phase_ev.next; ++e) {
+        float pm = 0.0f;
+        KRR_CUDA_TRY(cudaEventElapsedTime(&pm, S->phase_ev.ev[e - 1], S->phase_ev.ev[e]));
+        S->phase_ms[(e - 1) % SERVE_KERNELS_PER_ITER] += pm;
+      }
+      S->phase_ev.next = 0;
+    }
     for (Slot *sl : inner) {
       const ServeStatus &st = S->status_host[sl->id];
       if (st.live) continue;
@@ -1073,6 +1341,7 @@ static krr_status server_step(krr_server *S, int64_t *unfinished) {
       sl->budget -= st.iters_max;
       sl->entries += kmv_entries(sl->N) * st.iters_max;
       sl->breakdown = st.breakdown != 0;
+      sl->inner_capped = st.iters_max >= sl->inner_limit;
       S->table_dirty = true;
       KRR_TRY(start_refine(S, sl));
     }
@@ -1096,7 +1365,8 @@ static void server_free(krr_server *S) {
     S->stop = true;
   }
   S->cv.notify_all();
-  if (S->builder.joinable()) S->builder.join();
+  for (auto &t : S->builders)
+    if (t.joinable()) t.join();
   cudaDeviceSynchronize();
   for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
     if (S->slots[i]) {
@@ -1113,7 +1383,11 @@ static void server_free(krr_server *S) {
   cudaFree(S->init_dev);
   cudaFree(S->scalars_dev);
   cudaFree(S->status_dev);
-  cudaFree(S->counters_dev);
+  for (int b = 0; b < SERVE_BRANCHES; ++b) {
+    if (S->branches.side[b]) cudaStreamDestroy(S->branches.side[b]);
+    if (S->branches.join[b]) cudaEventDestroy(S->branches.join[b]);
+  }
+  if (S->branches.fork) cudaEventDestroy(S->branches.fork);
   cudaFreeHost(S->table_host);
   cudaFreeHost(S->init_host);
   cudaFreeHost(S->status_host);
@@ -1124,8 +1398,12 @@ static void server_free(krr_server *S) {
     if (S->s_slot[i]) cudaStreamDestroy(S->s_slot[i]);
   }
   if (S->ev_step) cudaEventDestroy(S->ev_step);
+  for (cudaEvent_t e : S->phase_ev.ev) cudaEventDestroy(e);
+  if (S->ev_t0) cudaEventDestroy(S->ev_t0);
+  if (S->ev_t1) cudaEventDestroy(S->ev_t1);
   if (S->s_iter) cudaStreamDestroy(S->s_iter);
-  if (S->s_build) cudaStreamDestroy(S->s_build);
+  for (int b = 0; b < SERVE_MAX_BUILDERS; ++b)
+    if (S->s_build[b]) cudaStreamDestroy(S->s_build[b]);
   if (S->s_free) cudaStreamDestroy(S->s_free);
   delete S;
 }
@@ -1135,18 +1413,26 @@ static krr_status server_init(krr_server *S) {
   int lo = 0, hi = 0;
   KRR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_iter, cudaStreamNonBlocking, hi));
-  KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_build, cudaStreamNonBlocking, lo));
+  S->nbuilders = S->cfg.build_threads > 0 ? S->cfg.build_threads : 4;
+  for (int b = 0; b < S->nbuilders; ++b)
+    KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_build[b], cudaStreamNonBlocking, lo));
   KRR_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_free, cudaStreamNonBlocking));
   for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
     KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_slot[i], cudaStreamNonBlocking, hi));
     KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_slot[i], cudaEventDisableTiming));
   }
   KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_step, cudaEventDisableTiming));
+  KRR_CUDA_TRY(cudaEventCreate(&S->ev_t0));
+  KRR_CUDA_TRY(cudaEventCreate(&S->ev_t1));
   KRR_CUDA_TRY(cudaMalloc(&S->table_dev, sizeof(ServeTable)));
   KRR_CUDA_TRY(cudaMalloc(&S->init_dev, sizeof(ServeTable) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMalloc(&S->scalars_dev, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMalloc(&S->status_dev, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
-  KRR_CUDA_TRY(cudaMalloc(&S->counters_dev, sizeof(int) * 64));
+  for (int b = 0; b < SERVE_BRANCHES; ++b) {
+    KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->branches.side[b], cudaStreamNonBlocking, hi));
+    KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->branches.join[b], cudaEventDisableTiming));
+  }
+  KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->branches.fork, cudaEventDisableTiming));
   KRR_CUDA_TRY(cudaMemset(S->scalars_dev, 0, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMemset(S->status_dev, 0, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMemset(S->table_dev, 0, sizeof(ServeTable)));
@@ -1156,17 +1442,16 @@ static krr_status server_init(krr_server *S) {
   KRR_CUDA_TRY(cudaMallocHost(&S->ctl_host, sizeof(ServeControl) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMallocHost(&S->sumsq_host, sizeof(double) * SERVE_MAX_SLOTS * SERVE_MAX_M));
   std::memset(S->table_host, 0, sizeof(ServeTable));
-  KRR_TRY(serve_configure_product());
   if (S->cfg.hbm_budget_bytes > 0) {
-    S->budget = S->cfg.hbm_budget_bytes;
+    S->budget = (int64_t)S->cfg.hbm_budget_bytes;
   } else {
     size_t fr = 0, tot = 0;
     KRR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    S->budget = 0.9 * (double)fr;
+    S->budget = (int64_t)(0.9 * (double)fr);
   }
   KRR_CUDA_TRY(cudaDeviceSynchronize());
   S->t0 = Clock::now();
-  S->builder = std::thread(builder_main, S);
+  for (int b = 0; b < S->nbuilders; ++b) S->builders.emplace_back(builder_main, S, b);
   return KRR_OK;
 }
 
@@ -1194,7 +1479,8 @@ krr_status krr_server_create(const krr_server_config *cfg, krr_server **out) {
               "iters_per_step must be in [1, 64]");
   KRR_REQUIRE(cfg->hbm_budget_bytes >= 0 && std::isfinite(cfg->hbm_budget_bytes),
               "hbm_budget_bytes must be >= 0");
-  KRR_REQUIRE(cfg->reserved == 0, "reserved must be 0");
+  KRR_REQUIRE(cfg->build_threads >= 0 && cfg->build_threads <= KRR_SERVE_MAX_BUILDERS,
+              "build_threads must be in [0, %d]", KRR_SERVE_MAX_BUILDERS);
   krr_server *S = new (std::nothrow) krr_server();
   if (!S) return KRR_ENOMEM;
   S->cfg = *cfg;
@@ -1223,10 +1509,10 @@ krr_status krr_server_submit(krr_server *S, const double *X, int64_t N, int d, k
   KRR_REQUIRE(k >= 0 && k <= N && k <= 4096, "k must be in [0, min(N, 4096)]");
   KRR_REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
   KRR_REQUIRE(maxit >= 1, "maxit must be >= 1");
-  const double bytes = krr::serve_footprint(N, d, m, k);
+  const int64_t bytes = (int64_t)std::ceil(krr::serve_footprint(N, d, m, k));
   if (bytes > S->budget) {
-    krr::set_error("request needs about %.3g bytes, more than the server's budget %.3g", bytes,
-                   S->budget);
+    krr::set_error("request needs about %.3g bytes, more than the server's budget %.3g",
+                   (double)bytes, (double)S->budget);
     return KRR_ENOMEM;
   }
   std::unique_ptr<Slot> sl(new (std::nothrow) Slot());
@@ -1283,10 +1569,18 @@ krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *out) {
   out->steps = S->steps;
   out->step_kernels = S->step_kernels;
   out->max_concurrent = S->max_concurrent;
-  out->reserved_bytes = S->reserved;
-  out->peak_reserved_bytes = S->peak_reserved;
-  out->budget_bytes = S->budget;
+  out->reserved_bytes = (double)S->reserved;
+  out->peak_reserved_bytes = (double)S->peak_reserved;
+  out->budget_bytes = (double)S->budget;
   out->kernel_entries = S->entries_total;
+  out->step_ms = S->step_ms;
+  for (int k = 0; k < krr::SERVE_KERNELS_PER_ITER; ++k) out->phase_ms[k] = S->phase_ms[k];
+  {
+    std::lock_guard<std::mutex> lk(const_cast<krr_server *>(S)->mtx);
+    out->build_s = S->build_s;
+    out->escalate_s = S->escalate_s;
+    out->escalations = S->escalations;
+  }
   return KRR_OK;
 }
 

@@ -19,6 +19,7 @@
 namespace krr {
 
 constexpr int SERVE_MAX_SLOTS = 64;     // slots per table (== KRR_SERVE_MAX_SLOTS)
+constexpr int SERVE_MAX_BUILDERS = 8;   // builder threads (== KRR_SERVE_MAX_BUILDERS)
 constexpr int SERVE_MAX_M = 16;         // right-hand sides per solve
 constexpr int SERVE_VB = 256;           // rows per vector block (one per thread)
 constexpr int SERVE_TT_ROWS = 512;      // rows per block of F^T r
@@ -86,11 +87,23 @@ struct ServeSlotDesc {
   ServeStatus *status;
 };
 
+constexpr int SERVE_NUM_VARIANTS = 60;  // 3 kernels x 4 DP classes x 5 M classes
+
+// The slots of one product variant: the product launch of that variant
+// covers their (row tile, split) items, item i of slot slot[j] being
+// i - off[j] for off[j] <= i < off[j + 1].
+struct ServeClass {
+  int variant;
+  int nslots;
+  int slot[SERVE_MAX_SLOTS];          // indices into ServeTable::slot
+  int off[SERVE_MAX_SLOTS + 1];
+};
+
 // Work list of one launch sequence: cumulative item counts per phase.
 struct ServeTable {
   int nslots;
-  int pad;
-  int prod_off[SERVE_MAX_SLOTS + 1];   // product tiles (row tile, split)
+  int nclasses;
+  ServeClass cls[SERVE_NUM_VARIANTS];  // product launches, one per variant present
   int vec_off[SERVE_MAX_SLOTS + 1];    // vector blocks of SERVE_VB rows
   int tt_off[SERVE_MAX_SLOTS + 1];     // F^T r blocks of SERVE_TT_ROWS rows
   int ttr_off[SERVE_MAX_SLOTS + 1];    // rank x m reductions
@@ -122,15 +135,13 @@ __host__ __device__ inline int serve_variant(int kern, int dp, int M) {
   return (kern * 4 + di) * 5 + mi;
 }
 
-// Largest shared memory of a grouped product tile (DP 32, M 16).
-int serve_prod_smem_bytes();
-
-// Kernel attributes of the grouped product; call once before any launch (and
-// before stream capture).
-krr_status serve_configure_product();
-
-// Grouped product over the table at T (device pointer); counter (device, zero
-// at launch) hands out the work items.
-krr_status serve_launch_product(const ServeTable *T, int *counter, cudaStream_t s);
+// Grouped product of class `cls` of the table at T (device pointer): one CTA
+// per item, `items` of them (serve_kmv_*.cu, one file per kernel function).
+cudaError_t serve_launch_product_gauss(int dp, int M, int items, const ServeTable *T, int cls,
+                                       cudaStream_t s);
+cudaError_t serve_launch_product_laplace(int dp, int M, int items, const ServeTable *T, int cls,
+                                         cudaStream_t s);
+cudaError_t serve_launch_product_matern(int dp, int M, int items, const ServeTable *T, int cls,
+                                        cudaStream_t s);
 
 }  // namespace krr

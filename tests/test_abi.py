@@ -117,7 +117,8 @@ def test_server_config_validation(lib):
                       (N_.ServerConfig(4, 0, 1, 0, 0.0), "iters_per_step"),
                       (N_.ServerConfig(4, 65, 1, 0, 0.0), "iters_per_step"),
                       (N_.ServerConfig(4, 4, 1, 0, -1.0), "hbm_budget"),
-                      (N_.ServerConfig(4, 4, 1, 3, 0.0), "reserved")]:
+                      (N_.ServerConfig(4, 4, 1, 9, 0.0), "build_threads"),
+                      (N_.ServerConfig(4, 4, 1, -1, 0.0), "build_threads")]:
         _einval(lib.krr_server_create(C.byref(cfg), C.byref(h)), lib, frag)
         assert not h.value
     X = np.zeros((4, 2))
