@@ -19,15 +19,20 @@ constexpr int TT_ROWS = 512;   // rows per block of the transposed product
 constexpr int RED_BLOCKS = 512;
 
 // part[b][l][c] = sum_{n in block b} F[n + l N] R[c][n]
-// One warp per column l; each lane holds TT_ROWS/32 rows, all loaded before
-// any arithmetic so that many loads are in flight.
-template <typename T>
+// Block (b, g) covers rows [b TT_ROWS, (b + 1) TT_ROWS) and the columns
+// [g TT_COLS, (g + 1) TT_COLS) (column groups give enough blocks to stream F
+// at HBM speed).  One warp per column; each lane holds TT_ROWS/32 rows, all
+// loaded before any arithmetic so that many loads are in flight.  M is m
+// rounded up to 1, 2, 4, 8 or 16 (specialised: a runtime column count costs
+// the unrolled loops several times their work).
+constexpr int TT_COLS = 64;
+
+template <typename T, int M>
 __global__ void __launch_bounds__(256)
 tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict__ R, int m,
               double *__restrict__ part) {
   constexpr int PER_LANE = TT_ROWS / 32;
-  extern __shared__ __align__(16) unsigned char tall_t_smem[];
-  T(*sR)[TT_ROWS] = reinterpret_cast<T(*)[TT_ROWS]>(tall_t_smem);   // m x TT_ROWS
+  __shared__ T sR[M][TT_ROWS];
   const int64_t n0 = (int64_t)blockIdx.x * TT_ROWS;
   const int nr = (int)min((int64_t)TT_ROWS, N - n0);
   for (int e = threadIdx.x; e < m * TT_ROWS; e += blockDim.x) {
@@ -36,7 +41,8 @@ tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict_
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int l = warp; l < rank; l += blockDim.x >> 5) {
+  const int l1 = min(rank, (int)(blockIdx.y + 1) * TT_COLS);
+  for (int l = (int)blockIdx.y * TT_COLS + warp; l < l1; l += blockDim.x >> 5) {
     const T *col = F + (int64_t)l * N + n0;
     T f[PER_LANE];
 #pragma unroll
@@ -44,17 +50,17 @@ tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict_
       const int n = lane + 32 * q;
       f[q] = (n < nr) ? col[n] : T(0);
     }
-    T acc[16];
+    T acc[M];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = T(0);
+    for (int c = 0; c < M; ++c) acc[c] = T(0);
 #pragma unroll
     for (int q = 0; q < PER_LANE; ++q) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c)
+      for (int c = 0; c < M; ++c)
         if (c < m) acc[c] = fma(f[q], sR[c][lane + 32 * q], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < M; ++c) {
       if (c < m) {
         const T v = warp_sum(acc[c]);
         if (lane == 0) part[((int64_t)blockIdx.x * rank + l) * m + c] = (double)v;
@@ -113,25 +119,25 @@ __global__ void tri_gemv_kernel(const double *__restrict__ Mt, int rank,
 
 // Z[c][n] = (R[c][n] - sum_l F[n + l N] v[c][l]) / lambda
 // One thread per row; the column loop loads LU values of F before using them
-// so that enough loads are in flight to stream F at HBM speed.
-template <typename T>
+// so that enough loads are in flight to stream F at HBM speed.  M as above.
+template <typename T, int M>
 __global__ void __launch_bounds__(256)
 tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
               int m, const T *__restrict__ R, double inv_lambda, T *__restrict__ Z) {
   constexpr int LCH = 256;
   constexpr int LU = 16;
-  __shared__ T sv[LCH][16];
+  __shared__ T sv[LCH][M];
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool ok = n < N;
-  T acc[16];
+  T acc[M];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = T(0);
+  for (int c = 0; c < M; ++c) acc[c] = T(0);
   for (int l0 = 0; l0 < rank; l0 += LCH) {
     const int nl = min(LCH, rank - l0);
     __syncthreads();
-    for (int e = threadIdx.x; e < m * LCH; e += blockDim.x) {
+    for (int e = threadIdx.x; e < M * LCH; e += blockDim.x) {
       const int c = e / LCH, l = e % LCH;
-      sv[l][c] = (l < nl) ? (T)v[(int64_t)c * rank + l0 + l] : T(0);
+      sv[l][c] = (l < nl && c < m) ? (T)v[(int64_t)c * rank + l0 + l] : T(0);
     }
     __syncthreads();
     for (int lb = 0; lb < nl; lb += LU) {
@@ -142,8 +148,7 @@ tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__rest
 #pragma unroll
       for (int u = 0; u < LU; ++u) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-          if (c < m) acc[c] = fma(f[u], sv[lb + u][c], acc[c]);
+        for (int c = 0; c < M; ++c) acc[c] = fma(f[u], sv[lb + u][c], acc[c]);
       }
     }
   }
@@ -153,18 +158,45 @@ tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__rest
   }
 }
 
+static int tall_pad_m(int m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16; }
+
+template <typename T>
+static krr_status launch_tall_t(const T *F, int64_t N, int rank, const T *R, int m,
+                                double *part, cudaStream_t s) {
+  const dim3 grid(ceil_div(N, TT_ROWS), ceil_div(rank, TT_COLS));
+  switch (tall_pad_m(m)) {
+    case 1: tall_t_kernel<T, 1><<<grid, 256, 0, s>>>(F, N, rank, R, m, part); break;
+    case 2: tall_t_kernel<T, 2><<<grid, 256, 0, s>>>(F, N, rank, R, m, part); break;
+    case 4: tall_t_kernel<T, 4><<<grid, 256, 0, s>>>(F, N, rank, R, m, part); break;
+    case 8: tall_t_kernel<T, 8><<<grid, 256, 0, s>>>(F, N, rank, R, m, part); break;
+    default: tall_t_kernel<T, 16><<<grid, 256, 0, s>>>(F, N, rank, R, m, part); break;
+  }
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
+template <typename T>
+static krr_status launch_tall_n(const T *F, int64_t N, int rank, const double *v, int m,
+                                const T *R, double inv_lambda, T *Z, cudaStream_t s) {
+  const unsigned grid = ceil_div(N, 256);
+  switch (tall_pad_m(m)) {
+    case 1: tall_n_kernel<T, 1><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 2: tall_n_kernel<T, 2><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 4: tall_n_kernel<T, 4><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 8: tall_n_kernel<T, 8><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    default: tall_n_kernel<T, 16><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+  }
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
 template <typename T>
 static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const double *W,
                                      const double *Wt, double lambda, const T *R, int m, T *Z,
                                      cudaStream_t s) {
   if (rank == 0) {
     // P = lambda I
-    DevBuf<double> zero;
-    KRR_TRY(zero.alloc(m, s));
-    KRR_CUDA_TRY(cudaMemsetAsync(zero.p, 0, sizeof(double) * m, s));
-    tall_n_kernel<T><<<ceil_div(N, 256), 256, 0, s>>>(F, N, 0, zero.p, m, R, 1.0 / lambda, Z);
-    KRR_LAUNCH_CHECK();
-    return KRR_OK;
+    return launch_tall_n<T>(F, N, 0, nullptr, m, R, 1.0 / lambda, Z, s);
   }
   const int nb = ceil_div(N, TT_ROWS);
   DevBuf<double> part, t, u, v;
@@ -172,18 +204,13 @@ static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const doub
   KRR_TRY(t.alloc((size_t)rank * m, s));
   KRR_TRY(u.alloc((size_t)rank * m, s));
   KRR_TRY(v.alloc((size_t)rank * m, s));
-  const size_t smem = (size_t)m * TT_ROWS * sizeof(T);
-  KRR_TRY(raise_smem_limit(tall_t_kernel<T>, smem));
-  tall_t_kernel<T><<<nb, 256, smem, s>>>(F, N, rank, R, m, part.p);
-  KRR_LAUNCH_CHECK();
+  KRR_TRY(launch_tall_t<T>(F, N, rank, R, m, part.p, s));
   tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 8), 256, 0, s>>>(part.p, nb, rank, m,
                                                                     t.p);
   KRR_LAUNCH_CHECK();
   KRR_TRY(tri_apply_lower(Wt, rank, t.p, m, u.p, s));
   KRR_TRY(tri_apply_lower_t(W, rank, u.p, m, v.p, s));
-  tall_n_kernel<T><<<ceil_div(N, 256), 256, 0, s>>>(F, N, rank, v.p, m, R, 1.0 / lambda, Z);
-  KRR_LAUNCH_CHECK();
-  return KRR_OK;
+  return launch_tall_n<T>(F, N, rank, v.p, m, R, 1.0 / lambda, Z, s);
 }
 
 krr_status nystrom_apply_f64(const krr_factor *f, const NystromCore *c, const double *R,

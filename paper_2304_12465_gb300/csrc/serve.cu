@@ -182,50 +182,66 @@ serve_resid_kernel(const ServeTable *__restrict__ T) {
   }
 }
 
-// part[b][l][c] = sum over the block's rows n of F[n + l N] r[c][n]
-__global__ void __launch_bounds__(256) serve_tt_kernel(const ServeTable *__restrict__ T) {
+// part[b][l][c] = sum over the rows n of block b of F[n + l N] r[c][n], for
+// the columns l of group g (SERVE_TT_COLS of them): one warp per column, the
+// lanes' rows loaded before the arithmetic.  M is the slot's padded m.
+template <int M>
+__device__ __forceinline__ void serve_tt_item(const ServeSlotDesc &d, int b, int g,
+                                              float (*sR)[SERVE_TT_ROWS]) {
   constexpr int PER_LANE = SERVE_TT_ROWS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t N = d.N, n0 = (int64_t)b * SERVE_TT_ROWS;
+  const int nr = (int)min((int64_t)SERVE_TT_ROWS, N - n0);
+  const int m = d.m, rank = d.rank;
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * SERVE_TT_ROWS; e += blockDim.x) {
+    const int c = e / SERVE_TT_ROWS, r = e % SERVE_TT_ROWS;
+    sR[c][r] = (r < nr) ? d.r[(int64_t)c * N + n0 + r] : 0.0f;
+  }
+  __syncthreads();
+  const int l1 = min(rank, (g + 1) * SERVE_TT_COLS);
+  for (int l = g * SERVE_TT_COLS + warp; l < l1; l += blockDim.x >> 5) {
+    const float *col = d.F + (int64_t)l * N + n0;
+    float f[PER_LANE];
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
+      const int r = lane + 32 * q;
+      f[q] = (r < nr) ? col[r] : 0.0f;
+    }
+    float acc[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) acc[c] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        if (c < m) acc[c] = fmaf(f[q], sR[c][lane + 32 * q], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      if (c < m) {
+        const float v = warp_sum(acc[c]);
+        if (lane == 0) d.ttpart[((int64_t)b * rank + l) * m + c] = (double)v;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) serve_tt_kernel(const ServeTable *__restrict__ T) {
   __shared__ float sR[SERVE_MAX_M][SERVE_TT_ROWS];
   const int n = T->nslots, total = T->tt_off[n];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int s = serve_find_slot(T->tt_off, n, item);
     const ServeSlotDesc &d = T->slot[s];
     if (!d.sc->live) continue;
-    const int b = item - T->tt_off[s];
-    const int64_t N = d.N, n0 = (int64_t)b * SERVE_TT_ROWS;
-    const int nr = (int)min((int64_t)SERVE_TT_ROWS, N - n0);
-    const int m = d.m, rank = d.rank;
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * SERVE_TT_ROWS; e += blockDim.x) {
-      const int c = e / SERVE_TT_ROWS, r = e % SERVE_TT_ROWS;
-      sR[c][r] = (r < nr) ? d.r[(int64_t)c * N + n0 + r] : 0.0f;
-    }
-    __syncthreads();
-    for (int l = warp; l < rank; l += blockDim.x >> 5) {
-      const float *col = d.F + (int64_t)l * N + n0;
-      float f[PER_LANE];
-#pragma unroll
-      for (int q = 0; q < PER_LANE; ++q) {
-        const int r = lane + 32 * q;
-        f[q] = (r < nr) ? col[r] : 0.0f;
-      }
-      float acc[SERVE_MAX_M];
-#pragma unroll
-      for (int c = 0; c < SERVE_MAX_M; ++c) acc[c] = 0.0f;
-#pragma unroll
-      for (int q = 0; q < PER_LANE; ++q) {
-#pragma unroll
-        for (int c = 0; c < SERVE_MAX_M; ++c)
-          if (c < m) acc[c] = fmaf(f[q], sR[c][lane + 32 * q], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < SERVE_MAX_M; ++c) {
-        if (c < m) {
-          const float v = warp_sum(acc[c]);
-          if (lane == 0) d.ttpart[((int64_t)b * rank + l) * m + c] = (double)v;
-        }
-      }
+    const int local = item - T->tt_off[s];
+    const int b = local % d.nbt, g = local / d.nbt;
+    switch (d.M) {
+      case 1: serve_tt_item<1>(d, b, g, sR); break;
+      case 2: serve_tt_item<2>(d, b, g, sR); break;
+      case 4: serve_tt_item<4>(d, b, g, sR); break;
+      case 8: serve_tt_item<8>(d, b, g, sR); break;
+      default: serve_tt_item<16>(d, b, g, sR); break;
     }
   }
 }
@@ -282,11 +298,58 @@ __global__ void __launch_bounds__(256) serve_tri_kernel(const ServeTable *__rest
   }
 }
 
-// z = (r - F v) / lambda; block partials of r.z
-__global__ void __launch_bounds__(SERVE_VB) serve_tn_kernel(const ServeTable *__restrict__ T) {
+// z = (r - F v) / lambda for one block of SERVE_VB rows; block partials of r.z
+template <int M>
+__device__ __forceinline__ void serve_tn_item(const ServeSlotDesc &d, int b,
+                                              float (*sv)[SERVE_MAX_M],
+                                              double (*red)[SERVE_MAX_M]) {
   constexpr int LCH = 256;
   constexpr int LU = 16;
-  __shared__ float sv[LCH][SERVE_MAX_M];
+  const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
+  const bool ok = i < N;
+  const int m = d.m, rank = d.rank;
+  float acc[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) acc[c] = 0.0f;
+  for (int l0 = 0; l0 < rank; l0 += LCH) {
+    const int nl = min(LCH, rank - l0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < M * LCH; e += blockDim.x) {
+      const int c = e / LCH, l = e % LCH;
+      sv[l][c] = (l < nl && c < m) ? (float)d.v[(int64_t)c * rank + l0 + l] : 0.0f;
+    }
+    __syncthreads();
+    for (int lb = 0; lb < nl; lb += LU) {
+      float f[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u)
+        f[u] = (ok && lb + u < nl) ? d.F[i + (int64_t)(l0 + lb + u) * N] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) acc[c] = fmaf(f[u], sv[lb + u][c], acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    if (c < m) {
+      double rz = 0.0;
+      if (ok) {
+        const int64_t e = (int64_t)c * N + i;
+        const float rv = d.r[e];
+        const float zv = (float)(((double)rv - (double)acc[c]) * d.inv_lam);
+        d.z[e] = zv;
+        rz = (double)rv * (double)zv;
+      }
+      serve_block_put(red, c, rz);
+    }
+  }
+  serve_block_flush(red, m, d.dpart1, d.nbv, b);
+}
+
+__global__ void __launch_bounds__(SERVE_VB) serve_tn_kernel(const ServeTable *__restrict__ T) {
+  __shared__ float sv[256][SERVE_MAX_M];
   __shared__ double red[SERVE_VB / 32][SERVE_MAX_M];
   const int n = T->nslots, total = T->vec_off[n];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -294,48 +357,13 @@ __global__ void __launch_bounds__(SERVE_VB) serve_tn_kernel(const ServeTable *__
     const ServeSlotDesc &d = T->slot[s];
     if (!d.sc->live) continue;
     const int b = item - T->vec_off[s];
-    const int64_t N = d.N, i = (int64_t)b * SERVE_VB + threadIdx.x;
-    const bool ok = i < N;
-    const int m = d.m, rank = d.rank;
-    float acc[SERVE_MAX_M];
-#pragma unroll
-    for (int c = 0; c < SERVE_MAX_M; ++c) acc[c] = 0.0f;
-    for (int l0 = 0; l0 < rank; l0 += LCH) {
-      const int nl = min(LCH, rank - l0);
-      __syncthreads();
-      for (int e = threadIdx.x; e < m * LCH; e += blockDim.x) {
-        const int c = e / LCH, l = e % LCH;
-        sv[l][c] = (l < nl) ? (float)d.v[(int64_t)c * rank + l0 + l] : 0.0f;
-      }
-      __syncthreads();
-      for (int lb = 0; lb < nl; lb += LU) {
-        float f[LU];
-#pragma unroll
-        for (int u = 0; u < LU; ++u)
-          f[u] = (ok && lb + u < nl) ? d.F[i + (int64_t)(l0 + lb + u) * N] : 0.0f;
-#pragma unroll
-        for (int u = 0; u < LU; ++u) {
-#pragma unroll
-          for (int c = 0; c < SERVE_MAX_M; ++c)
-            if (c < m) acc[c] = fmaf(f[u], sv[lb + u][c], acc[c]);
-        }
-      }
+    switch (d.M) {
+      case 1: serve_tn_item<1>(d, b, sv, red); break;
+      case 2: serve_tn_item<2>(d, b, sv, red); break;
+      case 4: serve_tn_item<4>(d, b, sv, red); break;
+      case 8: serve_tn_item<8>(d, b, sv, red); break;
+      default: serve_tn_item<16>(d, b, sv, red); break;
     }
-#pragma unroll
-    for (int c = 0; c < SERVE_MAX_M; ++c) {
-      if (c < m) {
-        double rz = 0.0;
-        if (ok) {
-          const int64_t e = (int64_t)c * N + i;
-          const float rv = d.r[e];
-          const float zv = (float)(((double)rv - (double)acc[c]) * d.inv_lam);
-          d.z[e] = zv;
-          rz = (double)rv * (double)zv;
-        }
-        serve_block_put(red, c, rz);
-      }
-    }
-    serve_block_flush(red, m, d.dpart1, d.nbv, b);
   }
 }
 
@@ -768,7 +796,7 @@ static void table_add(ServeTable *T, const ServeSlotDesc &d) {
   C.off[C.nslots + 1] = C.off[C.nslots] + d.row_tiles * d.splits;
   C.nslots += 1;
   T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
-  T->tt_off[s + 1] = T->tt_off[s] + d.nbt;
+  T->tt_off[s + 1] = T->tt_off[s] + d.nbt * ((d.rank + SERVE_TT_COLS - 1) / SERVE_TT_COLS);
   T->ttr_off[s + 1] = T->ttr_off[s] + (d.rank > 0 ? d.rank * d.m : 0);
   T->tri_off[s + 1] = T->tri_off[s] + d.rank;
   T->col_off[s + 1] = T->col_off[s] + d.m;

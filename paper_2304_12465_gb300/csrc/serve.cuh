@@ -23,6 +23,7 @@ constexpr int SERVE_MAX_BUILDERS = 8;   // builder threads (== KRR_SERVE_MAX_BUI
 constexpr int SERVE_MAX_M = 16;         // right-hand sides per solve
 constexpr int SERVE_VB = 256;           // rows per vector block (one per thread)
 constexpr int SERVE_TT_ROWS = 512;      // rows per block of F^T r
+constexpr int SERVE_TT_COLS = 64;       // columns of F per block of F^T r
 constexpr int SERVE_MAX_SPLITS = 32;    // column splits of one slot's product
 constexpr int SERVE_MIN_CHUNK = 256;    // columns per split at least
 
@@ -105,7 +106,7 @@ struct ServeTable {
   int nclasses;
   ServeClass cls[SERVE_NUM_VARIANTS];  // product launches, one per variant present
   int vec_off[SERVE_MAX_SLOTS + 1];    // vector blocks of SERVE_VB rows
-  int tt_off[SERVE_MAX_SLOTS + 1];     // F^T r blocks of SERVE_TT_ROWS rows
+  int tt_off[SERVE_MAX_SLOTS + 1];     // F^T r blocks (row block, column group)
   int ttr_off[SERVE_MAX_SLOTS + 1];    // rank x m reductions
   int tri_off[SERVE_MAX_SLOTS + 1];    // triangular rows (rank)
   int col_off[SERVE_MAX_SLOTS + 1];    // CG columns
