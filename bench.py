@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=512, help="serving: stream length")
     ap.add_argument("--n-max", type=int, default=200_000,
                     help="serving: largest N of the log-uniform range [2000, n_max]")
-    ap.add_argument("--rate", type=float, default=0.0,
-                    help="serving: mean arrivals per second (0: all at time 0)")
+    ap.add_argument("--rates", default="0.8",
+                    help="serving: Poisson arrival rates as fractions of the closed-loop "
+                         "throughput measured first on the same stream (comma separated)")
     ap.add_argument("--slots", type=int, default=32, help="serving: max concurrent solves")
     ap.add_argument("--iters-per-step", type=int, default=4, help="serving: PCG iterations/step")
     ap.add_argument("--serving-log", default="",
@@ -249,6 +250,19 @@ def run_native(args):
         "clocks": clk,
         "gpu_launches": int(launches),
     }
+    if not args.no_serving and world == 1:
+        # a bounded sample of the serving workload: the first 32 requests of the
+        # serving stream, closed loop, then Poisson arrivals at 0.8x its throughput
+        from inputs import make_serving_stream
+        sreqs = make_serving_stream(32, seed=4 + rank)
+        closed, runs = serving_protocol(K, sreqs, [0.8], 32, 4)
+        result["serving"] = {"requests": 32, "arrival_rate": "0.8 x closed-loop throughput",
+                             "solves_per_s": runs["0.8x"]["solves_per_s"],
+                             "latency_s": runs["0.8x"]["latency_s"],
+                             "closed_loop_solves_per_s": closed["solves_per_s"],
+                             "status": runs["0.8x"]["status"],
+                             "escalations": runs["0.8x"]["escalations"]}
+
     if rank == 0 and world == 1 and args.fp64_path:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -365,17 +379,32 @@ def serve_stream(K, reqs, rate, slots, iters_per_step, seed=5, log=""):
     }
 
 
+def serving_protocol(K, reqs, rates, slots, iters_per_step, log=""):
+    """Closed loop (every request at time 0) to measure the stream's
+    throughput, then Poisson arrivals at the given fractions of it."""
+    closed = serve_stream(K, reqs, 0.0, slots, iters_per_step)
+    runs = {}
+    for f in rates:
+        rho = f * closed["solves_per_s"]
+        runs[f"{f:g}x"] = serve_stream(K, reqs, rho, slots, iters_per_step,
+                                       log=log if f == rates[0] else "")
+    return closed, runs
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of KRR solve requests (N log-uniform
     in [2000, 200000], d in {4, 8, 16, 32}, three kernels, sigma log-uniform
     in [0.3, 3], mu log-uniform in [1e-8, 1e-4], 1-16 right-hand sides,
-    RPCholesky k = min(1000, N/10)), tol 1e-6; solves/s and p50/p99 latency."""
+    RPCholesky k = min(1000, N/10), x ~ N(0, I)), tol 1e-6.  The stream runs
+    closed loop first; its throughput sets the Poisson rates; value = solves/s
+    and p50/p99 latency at the first rate."""
     import torch
     import paper_2304_12465_gb300 as K
     from inputs import make_serving_stream
 
     dist, rank, world = dist_setup(args.gpus)
     K.load()
+    rates = [float(x) for x in args.rates.split(",")]
     reqs = make_serving_stream(args.requests, seed=4 + rank, n_range=(2000, args.n_max))
     warm = make_serving_stream(max(args.warmup, 1), seed=1000 + rank, n_range=(2000, 20000))
     serve_stream(K, warm, 0.0, args.slots, args.iters_per_step)
@@ -384,10 +413,11 @@ def run_serving(args):
     if dist:
         dist.barrier()
     clocks.start()
-    res = serve_stream(K, reqs, args.rate, args.slots, args.iters_per_step,
-                       log=args.serving_log)
+    closed, runs = serving_protocol(K, reqs, rates, args.slots, args.iters_per_step,
+                                    log=args.serving_log)
     clk = clocks.stop()
-    wall = res["wall_s"]
+    head = runs[f"{rates[0]:g}x"]
+    wall = head["wall_s"]
     if dist:
         t = torch.tensor([wall], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -401,18 +431,20 @@ def run_serving(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"serving: Poisson stream of {args.requests} KRR solve "
                                    f"requests, N log-uniform [2000, {args.n_max}], "
-                                   "d in {4,8,16,32}, "
+                                   "d in {4,8,16,32}, x ~ N(0, I), "
                                    "Gaussian/Laplace/Matern-5/2, sigma log-uniform [0.3, 3], "
                                    "mu log-uniform [1e-8, 1e-4], 1-16 RHS, "
-                                   "k = min(1000, N/10), tol 1e-6",
+                                   "k = min(1000, N/10), tol 1e-6; arrival rate "
+                                   f"{rates[0]:g} x the closed-loop throughput",
                        "l2": "inputs larger than L2 (each request's points, factor and "
                              "state are distinct)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "serving": res,
+            "latency_s": head["latency_s"],
+            "serving": {"closed_loop": closed, **runs},
             "e2e": {"value": value, "unit": "solves/s",
-                    "h2d_bytes_per_step": res["h2d_bytes"] // args.requests,
-                    "d2h_bytes_per_step": res["d2h_bytes"] // args.requests},
-            "clocks": clk, "gpu_launches": res["gpu_launches"],
+                    "h2d_bytes_per_step": head["h2d_bytes"] // args.requests,
+                    "d2h_bytes_per_step": head["d2h_bytes"] // args.requests},
+            "clocks": clk, "gpu_launches": head["gpu_launches"],
         }), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -72,6 +72,14 @@ typedef enum {
                             mixed path uses for its refinement residuals       */
 } krr_precision;
 
+/* Pivot rule of the partial Cholesky factorization: RPCholesky (Alg. 3)    */
+/* and the two rules the paper compares it with in Sec. 4.                   */
+typedef enum {
+    KRR_PIVOT_RPCHOLESKY = 0,  /* pivots ~ residual diagonal (Alg. 3)          */
+    KRR_PIVOT_UNIFORM = 1,     /* a uniformly random k-subset of the columns   */
+    KRR_PIVOT_GREEDY = 2       /* the largest residual diagonal entry          */
+} krr_pivot_rule;
+
 typedef struct krr_factor krr_factor;        /* RPCholesky factor F, pivots S */
 typedef struct krill_precond krill_precond;  /* KRILL preconditioner          */
 
@@ -173,6 +181,31 @@ KRR_API krr_status krr_rpc_sample(const double *dres, int64_t N, double dfloor,
 KRR_API krr_status krr_rpcholesky(const double *X, int64_t N, int d, krr_kernel kern,
                           double sigma, int k, int block, uint64_t seed,
                           void *stream, krr_factor **F_out);
+
+/* ------------------------------------------------------------------------ */
+/* The partial Cholesky factorization of krr_rpcholesky with another pivot    */
+/* rule (Sec. 4, the comparison strategies): the blocks, the Schur update,    */
+/* the drop rule and the handle are the same; only the pivots of each block   */
+/* differ.                                                                    */
+/*   KRR_PIVOT_RPCHOLESKY: krr_rpcholesky itself.                             */
+/*   KRR_PIVOT_UNIFORM: the k pivots are a uniformly random k-subset of the   */
+/*     N columns drawn before the first block, independently of A: draw       */
+/*     q = 0, 1, ... takes word 0 of Philox4x64-10 with counter (q, 0, 1, 0)  */
+/*     and key (seed, 0x5250434850495653) as floor(u N / 2^64), keeping first */
+/*     occurrences; blocks take them in that order.  A pivot the factor       */
+/*     already spans is dropped and still counts, so the rank can be < k.     */
+/*   KRR_PIVOT_GREEDY: each block takes the `block` largest residual diagonal */
+/*     entries above the drop threshold, in descending order (ties: smaller   */
+/*     index); block 0 means 1, one pivot at a time, which is the paper's     */
+/*     greedy rule (Cholesky with complete diagonal pivoting); larger blocks  */
+/*     are a blocked variant.                                                 */
+/* block 0 otherwise means min(100, ceil(k/10)).  Arguments and errors as     */
+/* krr_rpcholesky, plus KRR_EINVAL for an unknown rule.                       */
+/* ------------------------------------------------------------------------ */
+KRR_API krr_status krr_pivoted_cholesky(const double *X, int64_t N, int d, krr_kernel kern,
+                                        double sigma, int k, int block, uint64_t seed,
+                                        krr_pivot_rule rule, void *stream,
+                                        krr_factor **F_out);
 
 /* Rank reached, number of blocks drawn and N of a factor. */
 KRR_API krr_status krr_factor_info(const krr_factor *F, int64_t *N, int *rank,

@@ -158,21 +158,18 @@ def make_serving_stream(n_requests: int = 512, seed: int = 4,
 
 
 def make_serving_request(desc: Dict) -> Tuple[np.ndarray, np.ndarray]:
-    """Points and targets of one serving request: x from a 4-component Gaussian
-    mixture scaled by 1/sqrt(d) (so pairwise distances are O(1) for every d,
-    on the scale of the bandwidth range), m right-hand sides
-    y_r = cos(2 pi r <w, x>) + N(0, 0.01^2) for a random unit vector w."""
+    """Points and targets of one serving request: x ~ N(0, I_d) and m
+    right-hand sides y_r = sin(r <w, x>) + N(0, 0.01^2), r = 1..m, for a
+    random unit vector w (seeded by the request's seed)."""
     rng = np.random.default_rng(int(desc["seed"]) + 7919)
     n, d, m = int(desc["N"]), int(desc["d"]), int(desc["m"])
-    means = rng.standard_normal((4, d))
-    comp = rng.integers(0, 4, size=n)
-    X = (means[comp] + 0.5 * rng.standard_normal((n, d))) / np.sqrt(d)
+    X = rng.standard_normal((n, d))
     w = rng.standard_normal(d)
     w /= np.linalg.norm(w)
     proj = X @ w
     Y = np.empty((m, n))
     for r in range(1, m + 1):
-        Y[r - 1] = np.cos(2 * np.pi * r * proj) + 0.01 * rng.standard_normal(n)
+        Y[r - 1] = np.sin(r * proj) + 0.01 * rng.standard_normal(n)
     return np.ascontiguousarray(X), Y
 
 

@@ -58,6 +58,14 @@ def lib():
         L.orc_rpc_sample.restype = C.c_int
         L.orc_rpc_sample.argtypes = [dp, C.c_int64, C.c_double, C.c_uint64, C.c_uint64,
                                      C.c_int, ip]
+        L.orc_uniform_pivots.restype = C.c_int
+        L.orc_uniform_pivots.argtypes = [C.c_int64, C.c_int, C.c_uint64, ip]
+        L.orc_greedy_pick.restype = C.c_int
+        L.orc_greedy_pick.argtypes = [dp, C.c_int64, C.c_double, C.c_int, ip]
+        L.orc_pivoted_cholesky.restype = C.c_int
+        L.orc_pivoted_cholesky.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                           C.c_int, C.c_int, C.c_uint64, C.c_int, dp, ip, dp,
+                                           ip, dp]
         L.orc_rpcholesky.restype = C.c_int
         L.orc_rpcholesky.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double,
                                      C.c_int, C.c_int, C.c_uint64, dp, ip, dp, ip, dp]
@@ -205,23 +213,53 @@ def default_block(k: int) -> int:
     return min(100, -(-k // 10))
 
 
-def rpcholesky(X, kern: int, sigma: float, k: int, B: int = 0,
-               seed: int = 0) -> RPCholeskyResult:
-    """Alg. 3, blocked RPCholesky, with the sampler reading described in
-    krr_oracle.c.  B = 0 selects Alg. 1's default block size."""
+PIVOT_RPCHOLESKY, PIVOT_UNIFORM, PIVOT_GREEDY = 0, 1, 2
+
+
+def uniform_pivots(N: int, k: int, seed: int) -> np.ndarray:
+    """The uniform pivot rule of Sec. 4: a uniformly random k-subset of the
+    N columns, in draw order (reading in krr_oracle.c)."""
+    out = np.empty(min(k, N), dtype=np.int64)
+    got = lib().orc_uniform_pivots(N, k, seed, _i(out))
+    return out[:got]
+
+
+def greedy_pick(dres, npick: int, dfloor: float = 0.0) -> np.ndarray:
+    """The npick largest residuals above dfloor, descending (ties: smallest
+    index) -- the greedy pivot rule of Sec. 4."""
+    dres = _f64(dres)
+    out = np.empty(npick, dtype=np.int64)
+    got = lib().orc_greedy_pick(_d(dres), dres.shape[0], dfloor, npick, _i(out))
+    return out[:got]
+
+
+def pivoted_cholesky(X, kern: int, sigma: float, k: int, B: int = 0, seed: int = 0,
+                     rule: int = PIVOT_RPCHOLESKY) -> RPCholeskyResult:
+    """Alg. 3 with the pivots of each block chosen by `rule`: RPCholesky
+    sampling, uniform sampling or greedy selection (Sec. 4).  B = 0 selects
+    Alg. 1's default block size for RPCholesky and uniform, and 1 (one pivot
+    at a time, the paper's greedy rule) for greedy.  With the uniform rule
+    k counts the pivots used, kept or dropped, so the rank can be below k."""
     X = _f64(X)
     N, d = X.shape
     k = min(k, N)
-    B = B or default_block(k)
+    B = B or (1 if rule == PIVOT_GREEDY else default_block(k))
     F = np.zeros((k, N))
     S = np.zeros(k, dtype=np.int64)
     dres = np.empty(N)
     nb = np.zeros(1, dtype=np.int64)
     hist = np.zeros(k + N + 1)
-    rank = lib().orc_rpcholesky(_d(X), N, d, kern, sigma, k, B, seed, _d(F), _i(S),
-                                _d(dres), _i(nb), _d(hist))
+    rank = lib().orc_pivoted_cholesky(_d(X), N, d, kern, sigma, k, B, seed, rule, _d(F), _i(S),
+                                      _d(dres), _i(nb), _d(hist))
     return RPCholeskyResult(F[:rank].copy(), S[:rank].copy(), dres, rank, int(nb[0]),
                             hist[:int(nb[0]) + 1].copy())
+
+
+def rpcholesky(X, kern: int, sigma: float, k: int, B: int = 0,
+               seed: int = 0) -> RPCholeskyResult:
+    """Alg. 3, blocked RPCholesky, with the sampler reading described in
+    krr_oracle.c.  B = 0 selects Alg. 1's default block size."""
+    return pivoted_cholesky(X, kern, sigma, k, B, seed, PIVOT_RPCHOLESKY)
 
 
 # --------------------------------------------------------------------------

@@ -232,6 +232,58 @@ int orc_rpc_sample(const double *dres, int64_t N, double dfloor, uint64_t seed,
 }
 
 /* ------------------------------------------------------------------------ */
+/* The two pivot rules the paper compares RPCholesky with (Sec. 4, "Failure  */
+/* of uniform sampling" / "Failure of greedy selection").                    */
+/* Uniform: the k pivots are a uniformly random k-subset of the N columns,   */
+/* drawn independently of A.  Reading: draw q = 0, 1, ... takes word 0 of     */
+/* Philox(counter (q, 0, 1, 0), key (seed, pivot tag)) as the index           */
+/* floor(u * N / 2^64), keeping first occurrences until k distinct indices   */
+/* are found; the pivots enter the blocked Cholesky in that order, so a     */
+/* column the factor already spans is dropped and still counts as a pivot.   */
+/* Writes min(k, N) indices.                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_uniform_pivots(int64_t N, int k, uint64_t seed, int64_t *S)
+{
+    if ((int64_t)k > N) k = (int)N;
+    unsigned char *seen = (unsigned char *)calloc((size_t)N, 1);
+    const uint64_t key[2] = {seed, ORC_TAG_PIVOTS};
+    int got = 0;
+    for (uint64_t q = 0; got < k; ++q) {
+        uint64_t ctr[4] = {q, 0, 1, 0}, out[4];
+        orc_philox4x64(ctr, key, out);
+        int64_t i = (int64_t)(((unsigned __int128)out[0] * (uint64_t)N) >> 64);
+        if (seen[i]) continue;
+        seen[i] = 1;
+        S[got++] = i;
+    }
+    free(seen);
+    return got;
+}
+
+/* Greedy: each pivot is the largest entry of the residual diagonal after    */
+/* the previous steps (ties: the smallest index).  With a block of b > 1 the */
+/* b largest entries of the block's residual diagonal are taken (in          */
+/* descending order), a blocked variant; b = 1 is the paper's rule.          */
+/* Returns the number of picks (fewer than npick if fewer are eligible).     */
+int orc_greedy_pick(const double *dres, int64_t N, double dfloor, int npick, int64_t *picks)
+{
+    int got = 0;
+    for (int j = 0; j < npick; ++j) {
+        int64_t best = -1;
+        for (int64_t i = 0; i < N; ++i) {
+            if (!(dres[i] > 0.0 && dres[i] > dfloor)) continue;
+            int taken = 0;
+            for (int q = 0; q < got; ++q) if (picks[q] == i) { taken = 1; break; }
+            if (taken) continue;
+            if (best < 0 || dres[i] > dres[best]) best = i;
+        }
+        if (best < 0) break;
+        picks[got++] = best;
+    }
+    return got;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 3, blocked RPCholesky.                                               */
 /*   F <- 0, S <- {}, d <- diag(A), i <- 0                                    */
 /*   while i < k:                                                            */
@@ -254,9 +306,13 @@ int orc_rpc_sample(const double *dres, int64_t N, double dfloor, uint64_t seed,
 /* first block and after every block.                                        */
 /* Returns the rank reached (< k only if every weight became zero).           */
 /* ------------------------------------------------------------------------ */
-int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
-                   int k, int B, uint64_t seed, double *F, int64_t *S,
-                   double *dres, int64_t *nblocks_out, double *trace_hist)
+/* rule selects the pivots of each block: 0 RPCholesky (the sampler above),  */
+/* 1 uniform (the next B of orc_uniform_pivots; the loop ends when all k are */
+/* used, whatever the rank), 2 greedy (orc_greedy_pick); the rest of the     */
+/* block is the same for every rule.                                         */
+int orc_pivoted_cholesky(const double *X, int64_t N, int d, int kern, double sigma,
+                         int k, int B, uint64_t seed, int rule, double *F, int64_t *S,
+                         double *dres, int64_t *nblocks_out, double *trace_hist)
 {
     double maxdiag = 0.0;
     for (int64_t n = 0; n < N; ++n) {
@@ -277,13 +333,29 @@ int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
     double *Fn = (double *)malloc(sizeof(double) * (size_t)N * (size_t)B);
 
     const double thr = (double)N * DBL_EPSILON * maxdiag;
+    int64_t *upiv = NULL;
+    int nupiv = 0, used = 0;
+    if (rule == 1) {
+        upiv = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+        nupiv = orc_uniform_pivots(N, k, seed, upiv);
+    }
     int rank = 0;
     uint64_t t = 0;
-    while (rank < k) {
-        int nd = (k - rank < B) ? (k - rank) : B;
-        int got = orc_rpc_sample(dres, N, thr, seed, t, nd, draws);
+    while (rule == 1 ? used < nupiv : rank < k) {
+        int nd, got;
+        if (rule == 1) {
+            nd = (nupiv - used < B) ? (nupiv - used) : B;
+            memcpy(draws, upiv + used, sizeof(int64_t) * (size_t)nd);
+            used += nd;
+            got = nd;
+        } else {
+            nd = (k - rank < B) ? (k - rank) : B;
+            if (rule == 2) got = orc_greedy_pick(dres, N, thr, nd, draws);
+            else got = orc_rpc_sample(dres, N, thr, seed, t, nd, draws);
+        }
         ++t;
         if (got == 0) break;
+        nd = got;
 
         /* Unique, first-occurrence order */
         int nc = 0;
@@ -359,8 +431,16 @@ int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
         }
     }
     if (nblocks_out) *nblocks_out = (int64_t)t;
-    free(draws); free(cand); free(acc); free(G); free(R); free(Fn);
+    free(draws); free(cand); free(acc); free(G); free(R); free(Fn); free(upiv);
     return rank;
+}
+
+int orc_rpcholesky(const double *X, int64_t N, int d, int kern, double sigma,
+                   int k, int B, uint64_t seed, double *F, int64_t *S,
+                   double *dres, int64_t *nblocks_out, double *trace_hist)
+{
+    return orc_pivoted_cholesky(X, N, d, kern, sigma, k, B, seed, 0, F, S, dres,
+                                nblocks_out, trace_hist);
 }
 
 /* ------------------------------------------------------------------------ */

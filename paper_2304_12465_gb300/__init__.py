@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     krr_pcg_solve,
     krr_pcg_solve_batched,
     krr_predict,
+    krr_pivoted_cholesky,
     krr_precond_apply,
     krr_rpc_sample,
     krr_rpcholesky,

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA",
 
 GAUSSIAN, LAPLACE_L1, MATERN52 = 0, 1, 2
 PREC_FP64, PREC_MIXED, PREC_FLOAT_FLOAT = 0, 1, 2
+PIVOT_RPCHOLESKY, PIVOT_UNIFORM, PIVOT_GREEDY = 0, 1, 2
 
 
 class KrrInfo(C.Structure):
@@ -88,6 +89,8 @@ SIGNATURES = {
     "krr_rpc_sample": (_int, [_vp, _i64, _dbl, _u64, _u64, _int, _vp, C.POINTER(_int), _vp]),
     "krr_rpcholesky": (_int, [_vp, _i64, _int, _int, _dbl, _int, _int, _u64, _vp,
                               C.POINTER(_vp)]),
+    "krr_pivoted_cholesky": (_int, [_vp, _i64, _int, _int, _dbl, _int, _int, _u64, _int, _vp,
+                                    C.POINTER(_vp)]),
     "krr_factor_info": (_int, [_vp, C.POINTER(_i64), C.POINTER(_int), C.POINTER(_int)]),
     "krr_factor_export": (_int, [_vp, _vp, _vp, _vp]),
     "krr_factor_free": (None, [_vp]),

@@ -206,6 +206,24 @@ def krr_rpcholesky(X, kern, sigma: float, k: int, block: int = 0, seed: int = 0,
     return Factor(h)
 
 
+_PIVOTS = {"rpcholesky": N_.PIVOT_RPCHOLESKY, "uniform": N_.PIVOT_UNIFORM,
+           "greedy": N_.PIVOT_GREEDY}
+
+
+def krr_pivoted_cholesky(X, kern, sigma: float, k: int, block: int = 0, seed: int = 0,
+                         rule="rpcholesky", stream=None) -> Factor:
+    """Partial Cholesky with the pivot rule 'rpcholesky', 'uniform' or 'greedy'."""
+    lib = load()
+    Xk, Xp = _arr(X)
+    Nn, d = Xk.shape
+    h = C.c_void_p()
+    r = _PIVOTS[rule] if isinstance(rule, str) else int(rule)
+    check(lib.krr_pivoted_cholesky(Xp, Nn, d, _kern(kern), float(sigma), int(k), int(block),
+                                   int(seed), r, _stream(stream, X), C.byref(h)),
+          "krr_pivoted_cholesky")
+    return Factor(h)
+
+
 def krr_precond_apply(F: Factor, mu: float, R, prec="fp64", stream=None):
     lib = load()
     Rk, Rp = _arr(R)

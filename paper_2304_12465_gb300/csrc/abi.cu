@@ -362,11 +362,22 @@ krr_status krr_rpc_sample(const double *dres, int64_t N, double dfloor, uint64_t
 
 krr_status krr_rpcholesky(const double *X, int64_t N, int d, krr_kernel kern, double sigma,
                           int k, int block, uint64_t seed, void *stream, krr_factor **F_out) {
+  return krr_pivoted_cholesky(X, N, d, kern, sigma, k, block, seed, KRR_PIVOT_RPCHOLESKY,
+                              stream, F_out);
+}
+
+krr_status krr_pivoted_cholesky(const double *X, int64_t N, int d, krr_kernel kern,
+                                double sigma, int k, int block, uint64_t seed,
+                                krr_pivot_rule rule, void *stream, krr_factor **F_out) {
   clear_error();
   KRR_CHECK_POINTS(X, N, d, kern, sigma);
   KRR_REQUIRE(F_out, "F_out is NULL");
   *F_out = nullptr;
   KRR_REQUIRE(k >= 1 && k <= 4096 && k <= N, "k must be in [1, min(N, 4096)]");
+  KRR_REQUIRE(rule == KRR_PIVOT_RPCHOLESKY || rule == KRR_PIVOT_UNIFORM ||
+                  rule == KRR_PIVOT_GREEDY,
+              "unknown pivot rule %d", (int)rule);
+  if (block == 0 && rule == KRR_PIVOT_GREEDY) block = 1;
   if (block == 0) block = (k + 9) / 10 < 100 ? (k + 9) / 10 : 100;
   KRR_REQUIRE(block >= 1 && block <= RPC_MAX_BLOCK, "block must be in [1, %d]", RPC_MAX_BLOCK);
   cudaStream_t s = (cudaStream_t)stream;
@@ -375,7 +386,7 @@ krr_status krr_rpcholesky(const double *X, int64_t N, int d, krr_kernel kern, do
   KRR_TRY(device_view(X, (size_t)N * d, s, tx, &Xd));
   krr_factor *f = new (std::nothrow) krr_factor();
   if (!f) return KRR_ENOMEM;
-  krr_status st = rpcholesky_device(Xd, N, d, kern, sigma, k, block, seed, s, f);
+  krr_status st = rpcholesky_device(Xd, N, d, kern, sigma, k, block, seed, s, f, (int)rule);
   if (st == KRR_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -16,8 +16,11 @@ krr_status rpc_sample_device(const double *dres, int64_t N, double dfloor, uint6
                              uint64_t t, int ndraw, int64_t *draws, int64_t *cand, int *counts,
                              cudaStream_t s);
 
+// Alg. 3 with the pivot rule of krr_pivot_rule (RPCholesky sampling by
+// default; uniform and greedy are the comparison rules of Sec. 4).
 krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, double sigma,
-                             int k, int B, uint64_t seed, cudaStream_t s, krr_factor *f);
+                             int k, int B, uint64_t seed, cudaStream_t s, krr_factor *f,
+                             int rule = KRR_PIVOT_RPCHOLESKY);
 
 // Woodbury core for (mu, prec), built on first use and cached in the factor.
 krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s,

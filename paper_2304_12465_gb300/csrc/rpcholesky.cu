@@ -146,6 +146,105 @@ krr_status rpc_sample_device(const double *dres, int64_t N, double dfloor, uint6
   return KRR_OK;
 }
 
+// --------------------------------------------- uniform and greedy rules
+// The pivot rules the paper compares RPCholesky with (Sec. 4).
+//
+// Uniform: a uniformly random k-subset of the columns, drawn independently
+// of A: draw q takes word 0 of Philox(counter (q, 0, 1, 0), key (seed, pivot
+// tag)) as floor(u N / 2^64), keeping first occurrences (a bitmap of the
+// columns seen) until k distinct indices are found.  One thread; the loop is
+// bounded (far above the expected k + k^2 / (2N) draws for k <= N) and
+// reports failure through out_count.
+__global__ void uniform_pivots_kernel(int64_t N, int k, uint64_t seed, unsigned *__restrict__ seen,
+                                      int64_t *__restrict__ S, int *__restrict__ out_count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int got = 0;
+  const uint64_t qmax = 64ull * (uint64_t)k + 4096ull;
+  for (uint64_t q = 0; got < k && q < qmax; ++q) {
+    uint64_t ctr[4] = {q, 0ull, 1ull, 0ull}, out[4];
+    philox4x64_10(ctr, seed, kTagPivots, out);
+    const int64_t i = (int64_t)scale_u64(out[0], (uint64_t)N);
+    const unsigned bit = 1u << (i & 31);
+    if (seen[i >> 5] & bit) continue;
+    seen[i >> 5] |= bit;
+    S[got++] = i;
+  }
+  *out_count = got;
+}
+
+// Greedy: the npick largest residuals above dfloor in descending order (ties:
+// the smallest index); npick = 1 is the paper's rule.  One CTA; pick j is the
+// largest (value, -index) strictly below pick j - 1 in that order.
+constexpr int GREEDY_THREADS = 1024;
+__global__ void __launch_bounds__(GREEDY_THREADS)
+greedy_pick_kernel(const double *__restrict__ dres, int64_t N, double dfloor, int npick,
+                   int64_t *__restrict__ cand, int *__restrict__ counts) {
+  __shared__ double sv[GREEDY_THREADS / 32];
+  __shared__ int64_t si[GREEDY_THREADS / 32];
+  __shared__ double prev_v;
+  __shared__ int64_t prev_i;
+  __shared__ int got;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    prev_v = INFINITY;
+    prev_i = -1;
+    got = 0;
+  }
+  __syncthreads();
+  for (int j = 0; j < npick; ++j) {
+    const double pv = prev_v;
+    const int64_t pi = prev_i;
+    double bv = -1.0;
+    int64_t bi = -1;
+    for (int64_t i = threadIdx.x; i < N; i += GREEDY_THREADS) {
+      const double v = dres[i];
+      if (!(v > 0.0) || !(v > dfloor)) continue;
+      // strictly after the previous pick in (value desc, index asc) order
+      if (v > pv || (v == pv && i <= pi)) continue;
+      if (bi < 0 || v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[warp] = bv;
+      si[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = -1.0;
+      int64_t b = -1;
+      for (int w = 0; w < GREEDY_THREADS / 32; ++w) {
+        if (si[w] >= 0 && (b < 0 || sv[w] > v || (sv[w] == v && si[w] < b))) {
+          v = sv[w];
+          b = si[w];
+        }
+      }
+      if (b >= 0) {
+        cand[got] = b;
+        got = got + 1;
+        prev_v = v;
+        prev_i = b;
+      }
+    }
+    __syncthreads();
+    if (got <= j) break;   // nothing eligible left
+  }
+  if (threadIdx.x == 0) {
+    counts[0] = got > 0 ? npick : 0;
+    counts[1] = got;
+  }
+}
+
 // ------------------------------------------------------- block kernels
 // Fs (nc x rank, column-major) = F(cand, 0:rank)
 __global__ void gather_rows_kernel(const double *__restrict__ F, int64_t N, int rank,
@@ -265,7 +364,8 @@ __global__ void max_reduce_kernel(const double *__restrict__ v, int64_t n,
 
 // ----------------------------------------------------------- driver
 krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, double sigma,
-                             int k, int B, uint64_t seed, cudaStream_t s, krr_factor *f) {
+                             int k, int B, uint64_t seed, cudaStream_t s, krr_factor *f,
+                             int rule) {
   f->N = N;
   f->d = d;
   f->kern = kern;
@@ -302,17 +402,50 @@ krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, doubl
   KRR_TRY(raise_smem_limit(block_chol_kernel, chol_smem));
   KRR_TRY(raise_smem_limit(block_trsm_kernel, chol_smem));
 
+  // the uniform rule's k pivots are drawn before the first block
+  DevBuf<int64_t> upiv;
+  int nupiv = 0, used = 0;
+  if (rule == KRR_PIVOT_UNIFORM) {
+    DevBuf<unsigned> seen;
+    KRR_TRY(seen.alloc((size_t)(N + 31) / 32, s));
+    KRR_TRY(upiv.alloc(k, s));
+    KRR_CUDA_TRY(cudaMemsetAsync(seen.p, 0, sizeof(unsigned) * (size_t)((N + 31) / 32), s));
+    uniform_pivots_kernel<<<1, 32, 0, s>>>(N, k, seed, seen.p, upiv.p, counts.p);
+    KRR_LAUNCH_CHECK();
+    KRR_CUDA_TRY(cudaMemcpyAsync(&nupiv, counts.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nupiv < k) {
+      set_error("uniform pivot draw ended early (%d of %d)", nupiv, k);
+      return KRR_ECUDA;
+    }
+  }
+
   int rank = 0;
   uint64_t t = 0;
   int hcounts[4];
-  while (rank < k) {
-    const int nd = (k - rank < B) ? (k - rank) : B;
-    KRR_TRY(rpc_sample_device(f->dres, N, thr, seed, t, nd, draws.p, cand.p, counts.p, s));
-    ++t;
-    KRR_CUDA_TRY(cudaMemcpyAsync(hcounts, counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    KRR_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hcounts[0] == 0) break;
-    const int nc = hcounts[1];
+  while (rule == KRR_PIVOT_UNIFORM ? used < nupiv : rank < k) {
+    int nc;
+    if (rule == KRR_PIVOT_UNIFORM) {
+      nc = (nupiv - used < B) ? (nupiv - used) : B;
+      KRR_CUDA_TRY(cudaMemcpyAsync(cand.p, upiv.p + used, sizeof(int64_t) * nc,
+                                   cudaMemcpyDeviceToDevice, s));
+      used += nc;
+      ++t;
+    } else {
+      const int nd = (k - rank < B) ? (k - rank) : B;
+      if (rule == KRR_PIVOT_GREEDY) {
+        greedy_pick_kernel<<<1, GREEDY_THREADS, 0, s>>>(f->dres, N, thr, nd, cand.p, counts.p);
+        KRR_LAUNCH_CHECK();
+      } else {
+        KRR_TRY(rpc_sample_device(f->dres, N, thr, seed, t, nd, draws.p, cand.p, counts.p, s));
+      }
+      ++t;
+      KRR_CUDA_TRY(cudaMemcpyAsync(hcounts, counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                   s));
+      KRR_CUDA_TRY(cudaStreamSynchronize(s));
+      if (hcounts[0] == 0) break;
+      nc = hcounts[1];
+    }
     // G = A(:, S') - F(:, 0:rank) F(S', 0:rank)^T
     KRR_TRY(kernel_columns_f64(Xd, N, d, kern, sigma, cand.p, nc, G.p, N, s));
     if (rank > 0) {

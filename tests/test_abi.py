@@ -77,6 +77,8 @@ def test_argument_validation_before_any_launch(lib):
     h = C.c_void_p()
     _einval(lib.krr_rpcholesky(p(X), 4, 2, 0, 1.0, 5, 0, 0, None, C.byref(h)), lib, "k must")
     _einval(lib.krr_rpcholesky(p(X), 4, 2, 0, 1.0, 2, 129, 0, None, C.byref(h)), lib, "block")
+    _einval(lib.krr_pivoted_cholesky(p(X), 4, 2, 0, 1.0, 2, 0, 0, 3, None, C.byref(h)), lib,
+            "pivot rule")
     assert not h.value
     info = None
     _einval(lib.krr_pcg_solve(p(X), 4, 2, 0, 1.0, p(Y), 1, 0.0, None, 1e-6, 0, 0, p(Y), None,

@@ -93,3 +93,42 @@ def test_full_size_ill_conditioned(K):
     pivots and F to rounding."""
     w = make_c2_mixed()
     compare_factor(K, w.X, w.kernel, w.sigma, w.k, w.block, seed=w.seed, atol=1e-8)
+
+
+def compare_rule(K, X, kern, sigma, k, B, seed, rule, atol=1e-10):
+    ref = O.pivoted_cholesky(X, kern, sigma, k, B, seed, rule=rule)
+    name = {O.PIVOT_UNIFORM: "uniform", O.PIVOT_GREEDY: "greedy"}[rule]
+    f = K.krr_pivoted_cholesky(X, kern, sigma, k, B, seed, rule=name)
+    F, S, D = f.export()
+    assert f.rank == ref.rank
+    assert f.nblocks == ref.nblocks
+    np.testing.assert_array_equal(S, ref.S)
+    np.testing.assert_allclose(F, ref.F, atol=atol, rtol=0)
+    np.testing.assert_allclose(D, ref.dres, atol=atol, rtol=0)
+    f.free()
+
+
+@pytest.mark.parametrize("rule", [O.PIVOT_UNIFORM, O.PIVOT_GREEDY])
+@pytest.mark.parametrize("kern,N,k,B", [(O.GAUSSIAN, 333, 57, 0), (O.LAPLACE_L1, 1000, 80, 8),
+                                        (O.MATERN52, 2500, 120, 0)])
+def test_pivot_rules(K, rule, kern, N, k, B):
+    """The comparison pivot rules of Sec. 4 (uniform, greedy one at a time or
+    in blocks): identical pivots and blocks, F to rounding."""
+    rng = np.random.default_rng(N + kern)
+    X = rng.standard_normal((N, 5))
+    compare_rule(K, X, kern, 1.2, k, B, seed=kern + 3, rule=rule)
+
+
+def test_uniform_rule_counts_dropped_pivots(K):
+    """Sec. 4's two-block example: two uniform pivots usually land in the
+    large block, the second is dropped and the rank stays 1."""
+    X = np.zeros((512, 2))
+    X[504:] = 60.0
+    for seed in range(4):
+        compare_rule(K, X, O.GAUSSIAN, 1.0, 2, 1, seed, O.PIVOT_UNIFORM)
+
+
+def test_greedy_full_size(K):
+    """100000 points with 5% near-duplicates, rank 200 greedy one at a time."""
+    w = make_c2_mixed()
+    compare_rule(K, w.X, w.kernel, w.sigma, 200, 0, 0, O.PIVOT_GREEDY, atol=1e-8)
