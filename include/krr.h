@@ -457,6 +457,62 @@ KRR_API krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *o
 /* Seconds since the server was created (the clock of the result times).      */
 KRR_API double krr_server_clock(const krr_server *S);
 
+/* ------------------------------------------------------------------------ */
+/* Eviction and checkpoint/resume of served requests (the paper has no        */
+/* counterpart; a server uses it to free HBM for other work, and a caller to  */
+/* move a solve between servers or processes).                                */
+/* A running request is evicted at its next refinement boundary: when its     */
+/* float64 residual is known and another inner PCG solve would start, alpha   */
+/* and the residual move to host memory, its device memory and budget are     */
+/* released, and it is parked.  A queued request is parked at once.  A        */
+/* request that meets the tolerance (or is handed to the float-float          */
+/* continuation) before a boundary finishes instead.  A parked request is     */
+/* resumed at the head of the queue (krr_server_resume) or exported as a      */
+/* checkpoint (krr_server_export) and then leaves this server.  On resume or  */
+/* import its factor, core and points are rebuilt (the build is               */
+/* deterministic for a fixed seed) and the refinement continues from the      */
+/* saved state, so the result is bit-identical to an uninterrupted solve.     */
+/* ------------------------------------------------------------------------ */
+typedef enum {
+    KRR_REQ_QUEUED = 0, KRR_REQ_BUILDING = 1, KRR_REQ_ITERATING = 2,
+    KRR_REQ_ESCALATED = 3, KRR_REQ_FINISHING = 4, KRR_REQ_PARKED = 5, KRR_REQ_DONE = 6
+} krr_request_state;
+
+typedef struct {
+    int64_t id;
+    int state;                /* krr_request_state                              */
+    int iters;                /* inner PCG iterations so far                    */
+    int outer_refinements;    /* float64 residuals computed so far              */
+    int reserved;
+    double rel_residual;      /* worst column, after the last refinement        */
+} krr_request_progress;
+
+/* Progress of a request that is queued, running, parked, or finished and not */
+/* yet returned by krr_server_poll; KRR_EINVAL for other ids.                 */
+KRR_API krr_status krr_server_progress(const krr_server *S, int64_t id,
+                                       krr_request_progress *out);
+
+/* Marks a queued or running request for eviction (see above).                */
+KRR_API krr_status krr_server_evict(krr_server *S, int64_t id);
+
+/* Puts a parked request back at the head of the admission queue.             */
+KRR_API krr_status krr_server_resume(krr_server *S, int64_t id);
+
+/* Checkpoint of a parked request.  buf NULL: *size receives the bytes needed */
+/* (a header, 2 m norms and, once started, alpha and the float64 residual,    */
+/* 2 N m doubles).  Otherwise writes it into buf (*size bytes available,      */
+/* KRR_EINVAL if too small) and removes the request from this server: it is   */
+/* not reported by krr_server_poll, and its caller buffers are released.      */
+KRR_API krr_status krr_server_export(krr_server *S, int64_t id, void *buf, size_t *size);
+
+/* Queues a request from a checkpoint (checked for its magic, version, sizes  */
+/* and shapes; KRR_EINVAL otherwise) with the caller's X and Y -- the same    */
+/* data the checkpointed request was submitted with -- and a new output       */
+/* buffer; ownership and admission as krr_server_submit.                      */
+KRR_API krr_status krr_server_import(krr_server *S, const void *buf, size_t size,
+                                     const double *X, const double *Y, double *alpha_out,
+                                     int64_t *id_out);
+
 /* Waits for the device, stops the builders and frees everything.             */
 KRR_API void krr_server_destroy(krr_server *S);
 

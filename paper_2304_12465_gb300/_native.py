@@ -53,6 +53,19 @@ class RequestResult(C.Structure):
         return d
 
 
+class RequestProgress(C.Structure):
+    _fields_ = [("id", C.c_int64), ("state", C.c_int), ("iters", C.c_int),
+                ("outer_refinements", C.c_int), ("reserved", C.c_int),
+                ("rel_residual", C.c_double)]
+
+    STATES = ("queued", "building", "iterating", "escalated", "finishing", "parked", "done")
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d["state_name"] = self.STATES[self.state]
+        return d
+
+
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
                 ("admitted", C.c_int64), ("steps", C.c_int64), ("step_kernels", C.c_int64),
@@ -113,6 +126,11 @@ SIGNATURES = {
     "krr_server_poll": (_int, [_vp, C.POINTER(RequestResult), _int, C.POINTER(_int)]),
     "krr_server_get_stats": (_int, [_vp, C.POINTER(ServerStats)]),
     "krr_server_clock": (_dbl, [_vp]),
+    "krr_server_progress": (_int, [_vp, _i64, C.POINTER(RequestProgress)]),
+    "krr_server_evict": (_int, [_vp, _i64]),
+    "krr_server_resume": (_int, [_vp, _i64]),
+    "krr_server_export": (_int, [_vp, _i64, _vp, C.POINTER(C.c_size_t)]),
+    "krr_server_import": (_int, [_vp, _vp, C.c_size_t, _vp, _vp, _vp, C.POINTER(_i64)]),
     "krr_server_destroy": (None, [_vp]),
     "krr_set_profiling": (None, [_int]),
     "krr_last_error": (C.c_char_p, []),

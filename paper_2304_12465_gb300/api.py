@@ -472,6 +472,46 @@ class KrrServer:
     def clock(self) -> float:
         return float(load().krr_server_clock(self.handle))
 
+    def progress(self, rid: int) -> dict:
+        pr = N_.RequestProgress()
+        check(load().krr_server_progress(self.handle, int(rid), C.byref(pr)),
+              "krr_server_progress")
+        return pr.as_dict()
+
+    def evict(self, rid: int) -> None:
+        check(load().krr_server_evict(self.handle, int(rid)), "krr_server_evict")
+
+    def resume(self, rid: int) -> None:
+        check(load().krr_server_resume(self.handle, int(rid)), "krr_server_resume")
+
+    def export(self, rid: int) -> bytes:
+        """Checkpoint of a parked request; the request leaves this server."""
+        lib = load()
+        n = C.c_size_t(0)
+        check(lib.krr_server_export(self.handle, int(rid), None, C.byref(n)), "krr_server_export")
+        buf = C.create_string_buffer(n.value)
+        check(lib.krr_server_export(self.handle, int(rid), buf, C.byref(n)), "krr_server_export")
+        self._keep.pop(int(rid), None)
+        return buf.raw[:n.value]
+
+    def import_(self, blob: bytes, X, Y, out=None) -> int:
+        """Queues a request from a checkpoint with the original X and Y."""
+        lib = load()
+        Xk, Xp = _arr(X)
+        Yk, Yp = _arr(Y)
+        Nn = Xk.shape[0]
+        m = _shape2(Yk)[0]
+        if out is None:
+            A, Ap = _empty_like_container(Y, (m, Nn))
+        else:
+            A, Ap = out, C.c_void_p(out.data_ptr() if _is_torch(out) else out.ctypes.data)
+        raw = C.create_string_buffer(bytes(blob), len(blob))
+        rid = C.c_int64()
+        check(lib.krr_server_import(self.handle, raw, len(blob), Xp, Yp, Ap, C.byref(rid)),
+              "krr_server_import")
+        self._keep[rid.value] = (Xk, Yk, A)
+        return rid.value
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             load().krr_server_destroy(self._h)

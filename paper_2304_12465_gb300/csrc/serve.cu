@@ -715,7 +715,26 @@ struct Slot {
   bool inner_capped = false;   // the last inner solve stopped at its limit
   bool escalated = false;      // finished with float-float inner products
   krr_status status = KRR_OK;
+  // eviction / checkpoint
+  bool evict_req = false;      // leave the device at the next refinement boundary
+  bool resume = false;         // continue from saved_alpha / saved_r when built
+  std::vector<double> saved_alpha, saved_r;
 };
+
+// Checkpoint of a parked request: this header, then yn[m], rn[m], alpha
+// (m x N) and the float64 residual r (m x N), all native-endian.
+struct Checkpoint {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  int64_t N;
+  int32_t d, kern, m, k;
+  double sigma, mu, tol;
+  uint64_t seed;
+  int32_t maxit, outer, iters, budget;
+  double prev_worst, relres, entries;
+};
+constexpr char kCheckpointMagic[8] = {'K', 'R', 'R', 'C', 'K', 'P', 'T', '1'};
 
 }  // namespace
 
@@ -747,6 +766,7 @@ struct krr_server {
   // slots
   std::unique_ptr<Slot> slots[krr::SERVE_MAX_SLOTS];
   std::deque<std::unique_ptr<Slot>> queue;
+  std::vector<std::unique_ptr<Slot>> parked;   // evicted, waiting for resume / export
   std::vector<krr_request_result> done;
   bool table_dirty = true;
   // builders
@@ -897,10 +917,22 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   D.dpart1 = (double *)(base + od1);
   D.r64 = sl->r64;
   KRR_CUDA_TRY(cudaMemcpyAsync(sl->Y64, sl->Y, nm * 8, cudaMemcpyDefault, s));
-  KRR_CUDA_TRY(cudaMemsetAsync(sl->alpha64, 0, nm * 8, s));
-  KRR_CUDA_TRY(cudaMemcpyAsync(sl->r64, sl->Y64, nm * 8, cudaMemcpyDeviceToDevice, s));
+  if (sl->resume) {
+    // continue a parked or imported solve where it left off
+    KRR_CUDA_TRY(cudaMemcpyAsync(sl->alpha64, sl->saved_alpha.data(), nm * 8,
+                                 cudaMemcpyHostToDevice, s));
+    KRR_CUDA_TRY(cudaMemcpyAsync(sl->r64, sl->saved_r.data(), nm * 8, cudaMemcpyHostToDevice,
+                                 s));
+  } else {
+    KRR_CUDA_TRY(cudaMemsetAsync(sl->alpha64, 0, nm * 8, s));
+    KRR_CUDA_TRY(cudaMemcpyAsync(sl->r64, sl->Y64, nm * 8, cudaMemcpyDeviceToDevice, s));
+  }
   KRR_CUDA_TRY(cudaMemsetAsync(D.p, 0, nm * 4, s));
   KRR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (sl->resume) {
+    std::vector<double>().swap(sl->saved_alpha);
+    std::vector<double>().swap(sl->saved_r);
+  }
   // from here on the slot's memory is released on the free stream
   rebind(sl->P32.xt, S->s_free);
   rebind(sl->P32.cn, S->s_free);
@@ -1058,6 +1090,26 @@ static void builder_main(krr_server *S, int b) {
 }
 
 // ------------------------------------------------------------ phases
+// Releases a slot's device memory (every use of it has completed: the host
+// has seen the slot's last event).
+static void release_device(krr_server *S, Slot *sl) {
+  free_factor(sl->f);
+  sl->f = nullptr;
+  sl->core = nullptr;
+  if (sl->arena) cudaFreeAsync(sl->arena, S->s_free);
+  sl->arena = nullptr;
+  sl->P32.xt.release();
+  sl->P32.cn.release();
+  sl->P32.mean.release();
+  sl->Pff.xh.release();
+  sl->Pff.xl.release();
+  sl->Pff.ch.release();
+  sl->Pff.cl.release();
+  sl->Pff.mean.release();
+  sl->ffpart.release();
+  sl->ffvsplit.release();
+}
+
 static void complete(krr_server *S, Slot *sl, krr_status st) {
   krr_request_result r{};
   r.id = sl->req_id;
@@ -1079,12 +1131,32 @@ static void complete(krr_server *S, Slot *sl, krr_status st) {
   S->entries_total += sl->entries;
   S->reserved -= sl->bytes;
   // every use of the slot's memory has completed (its last event was seen)
-  free_factor(sl->f);
-  sl->f = nullptr;
-  if (sl->arena) cudaFreeAsync(sl->arena, S->s_free);
-  sl->arena = nullptr;
+  release_device(S, sl);
   const int id = sl->id;
   if (id >= 0) S->slots[id].reset();
+}
+
+// Eviction at a refinement boundary: alpha and the float64 residual move to
+// host memory, the slot and its budget are released, and the request waits
+// in the parked list (krr_server_resume / krr_server_export).
+static krr_status park(krr_server *S, Slot *sl) {
+  const size_t nm = (size_t)sl->N * sl->m;
+  cudaStream_t ss = S->s_slot[sl->id];
+  sl->saved_alpha.resize(nm);
+  sl->saved_r.resize(nm);
+  KRR_CUDA_TRY(cudaMemcpyAsync(sl->saved_alpha.data(), sl->alpha64, nm * 8,
+                               cudaMemcpyDeviceToHost, ss));
+  KRR_CUDA_TRY(cudaMemcpyAsync(sl->saved_r.data(), sl->r64, nm * 8, cudaMemcpyDeviceToHost, ss));
+  KRR_CUDA_TRY(cudaStreamSynchronize(ss));
+  release_device(S, sl);
+  S->reserved -= sl->bytes;
+  const int id = sl->id;
+  sl->id = -1;
+  sl->phase = Phase::Queued;
+  sl->evict_req = false;
+  sl->resume = true;
+  S->parked.push_back(std::move(S->slots[id]));
+  return KRR_OK;
 }
 
 static krr_status start_norms(krr_server *S, Slot *sl) {
@@ -1139,6 +1211,7 @@ static krr_status decide(krr_server *S, Slot *sl) {
     escalate(S, sl);
     return KRR_OK;
   }
+  if (sl->evict_req) return park(S, sl);
   sl->prev_worst = worst;
   ServeControl &ctl = S->ctl_host[sl->id];
   std::memset(&ctl, 0, sizeof(ctl));
@@ -1187,6 +1260,10 @@ static krr_status on_built(krr_server *S, Slot *sl) {
   cudaStream_t ss = S->s_slot[sl->id];
   KRR_CUDA_TRY(cudaMemcpyAsync(S->init_dev + sl->id, T1, table_bytes(1), cudaMemcpyHostToDevice,
                                ss));
+  if (sl->resume) {
+    sl->resume = false;
+    return decide(S, sl);
+  }
   sl->budget = sl->maxit;
   sl->first_norms = true;
   KRR_TRY(start_norms(S, sl));
@@ -1406,6 +1483,7 @@ static void server_free(krr_server *S) {
   }
   cudaDeviceSynchronize();
   S->queue.clear();
+  S->parked.clear();
   if (S->graph) cudaGraphExecDestroy(S->graph);
   cudaFree(S->table_dev);
   cudaFree(S->init_dev);
@@ -1613,6 +1691,177 @@ krr_status krr_server_get_stats(const krr_server *S, krr_server_stats *out) {
 }
 
 double krr_server_clock(const krr_server *S) { return S ? S->now() : 0.0; }
+
+krr_status krr_server_progress(const krr_server *S, int64_t id, krr_request_progress *out) {
+  krr::clear_error();
+  KRR_REQUIRE(S && out, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->id = id;
+  auto fill = [&](const Slot *sl, int state) {
+    out->state = state;
+    out->iters = sl->iters;
+    out->outer_refinements = sl->outer;
+    out->rel_residual = sl->relres;
+  };
+  for (int i = 0; i < krr::SERVE_MAX_SLOTS; ++i) {
+    const Slot *sl = S->slots[i].get();
+    if (!sl || sl->req_id != id) continue;
+    int st = KRR_REQ_ITERATING;
+    if (sl->phase == Phase::Building) st = KRR_REQ_BUILDING;
+    else if (sl->phase == Phase::Escalated) st = KRR_REQ_ESCALATED;
+    else if (sl->phase == Phase::Final) st = KRR_REQ_FINISHING;
+    fill(sl, st);
+    return KRR_OK;
+  }
+  for (const auto &sl : S->queue)
+    if (sl->req_id == id) { fill(sl.get(), KRR_REQ_QUEUED); return KRR_OK; }
+  for (const auto &sl : S->parked)
+    if (sl->req_id == id) { fill(sl.get(), KRR_REQ_PARKED); return KRR_OK; }
+  for (const auto &r : S->done)
+    if (r.id == id) {
+      out->state = KRR_REQ_DONE;
+      out->iters = r.iters;
+      out->outer_refinements = r.outer_refinements;
+      out->rel_residual = r.rel_residual;
+      return KRR_OK;
+    }
+  krr::set_error("request %lld is not known to the server (or was already polled)",
+                 (long long)id);
+  return KRR_EINVAL;
+}
+
+krr_status krr_server_evict(krr_server *S, int64_t id) {
+  krr::clear_error();
+  KRR_REQUIRE(S, "server is NULL");
+  for (int i = 0; i < krr::SERVE_MAX_SLOTS; ++i) {
+    Slot *sl = S->slots[i].get();
+    if (!sl || sl->req_id != id) continue;
+    KRR_REQUIRE(sl->phase != Phase::Escalated && sl->phase != Phase::Final,
+                "request %lld is finishing and cannot be evicted", (long long)id);
+    sl->evict_req = true;
+    return KRR_OK;
+  }
+  for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+    if ((*it)->req_id != id) continue;
+    // not started: nothing on the device, parked as it is
+    S->parked.push_back(std::move(*it));
+    S->queue.erase(it);
+    return KRR_OK;
+  }
+  krr::set_error("request %lld is not queued or running", (long long)id);
+  return KRR_EINVAL;
+}
+
+krr_status krr_server_resume(krr_server *S, int64_t id) {
+  krr::clear_error();
+  KRR_REQUIRE(S, "server is NULL");
+  for (auto it = S->parked.begin(); it != S->parked.end(); ++it) {
+    if ((*it)->req_id != id) continue;
+    S->queue.push_front(std::move(*it));
+    S->parked.erase(it);
+    return KRR_OK;
+  }
+  krr::set_error("request %lld is not parked", (long long)id);
+  return KRR_EINVAL;
+}
+
+krr_status krr_server_export(krr_server *S, int64_t id, void *buf, size_t *size) {
+  krr::clear_error();
+  KRR_REQUIRE(S && size, "NULL argument");
+  for (auto it = S->parked.begin(); it != S->parked.end(); ++it) {
+    Slot *sl = it->get();
+    if (sl->req_id != id) continue;
+    const size_t nm = sl->resume ? (size_t)sl->N * sl->m : 0;
+    const size_t need = sizeof(Checkpoint) + sizeof(double) * (2 * (size_t)sl->m + 2 * nm);
+    if (!buf) {
+      *size = need;
+      return KRR_OK;
+    }
+    KRR_REQUIRE(*size >= need, "checkpoint needs %zu bytes, buffer has %zu", need, *size);
+    Checkpoint h{};
+    std::memcpy(h.magic, kCheckpointMagic, sizeof(h.magic));
+    h.version = 1;
+    h.header_bytes = (uint32_t)sizeof(Checkpoint);
+    h.N = sl->N;
+    h.d = sl->d;
+    h.kern = sl->kern;
+    h.m = sl->m;
+    h.k = sl->k;
+    h.sigma = sl->sigma;
+    h.mu = sl->mu;
+    h.tol = sl->tol;
+    h.seed = sl->seed;
+    h.maxit = sl->maxit;
+    h.outer = sl->resume ? sl->outer : -1;   // -1: not started
+    h.iters = sl->iters;
+    h.budget = sl->budget;
+    h.prev_worst = sl->prev_worst;
+    h.relres = sl->relres;
+    h.entries = sl->entries;
+    char *p = (char *)buf;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    std::vector<double> zeros(sl->m, 0.0);
+    const std::vector<double> &yn = sl->resume ? sl->yn : zeros;
+    const std::vector<double> &rn = sl->resume ? sl->rn : zeros;
+    std::memcpy(p, yn.data(), sizeof(double) * sl->m);
+    p += sizeof(double) * sl->m;
+    std::memcpy(p, rn.data(), sizeof(double) * sl->m);
+    p += sizeof(double) * sl->m;
+    if (nm) {
+      std::memcpy(p, sl->saved_alpha.data(), sizeof(double) * nm);
+      p += sizeof(double) * nm;
+      std::memcpy(p, sl->saved_r.data(), sizeof(double) * nm);
+    }
+    *size = need;
+    S->parked.erase(it);
+    return KRR_OK;
+  }
+  krr::set_error("request %lld is not parked", (long long)id);
+  return KRR_EINVAL;
+}
+
+krr_status krr_server_import(krr_server *S, const void *buf, size_t size, const double *X,
+                             const double *Y, double *alpha_out, int64_t *id_out) {
+  krr::clear_error();
+  KRR_REQUIRE(S && buf && X && Y && alpha_out, "NULL argument");
+  KRR_REQUIRE(size >= sizeof(Checkpoint), "checkpoint too short");
+  Checkpoint h;
+  std::memcpy(&h, buf, sizeof(h));
+  KRR_REQUIRE(std::memcmp(h.magic, kCheckpointMagic, sizeof(h.magic)) == 0 && h.version == 1 &&
+                  h.header_bytes == sizeof(Checkpoint),
+              "not a checkpoint of this library");
+  KRR_REQUIRE(h.N >= 1 && h.N <= (int64_t)1 << 26 && h.d >= 1 && h.d <= 32 && h.m >= 1 &&
+                  h.m <= 16 && h.k >= 0 && h.k <= h.N && h.kern >= 0 && h.kern <= 2,
+              "corrupt checkpoint header");
+  const bool started = h.outer >= 0;
+  const size_t nm = started ? (size_t)h.N * h.m : 0;
+  const size_t need = sizeof(Checkpoint) + sizeof(double) * (2 * (size_t)h.m + 2 * nm);
+  KRR_REQUIRE(size >= need, "checkpoint truncated (%zu of %zu bytes)", size, need);
+  int64_t id = -1;
+  KRR_TRY(krr_server_submit(S, X, h.N, h.d, (krr_kernel)h.kern, h.sigma, Y, h.m, h.mu, h.k,
+                            h.seed, h.tol, h.maxit, alpha_out, &id));
+  if (started) {
+    Slot *sl = S->queue.back().get();
+    const char *p = (const char *)buf + sizeof(Checkpoint);
+    sl->yn.assign((const double *)p, (const double *)p + h.m);
+    p += sizeof(double) * h.m;
+    sl->rn.assign((const double *)p, (const double *)p + h.m);
+    p += sizeof(double) * h.m;
+    sl->saved_alpha.assign((const double *)p, (const double *)p + nm);
+    p += sizeof(double) * nm;
+    sl->saved_r.assign((const double *)p, (const double *)p + nm);
+    sl->outer = h.outer;
+    sl->iters = h.iters;
+    sl->budget = h.budget;
+    sl->prev_worst = h.prev_worst;
+    sl->relres = h.relres;
+    sl->entries = h.entries;
+    sl->resume = true;
+  }
+  if (id_out) *id_out = id;
+  return KRR_OK;
+}
 
 void krr_server_destroy(krr_server *S) { krr::server_free(S); }
 

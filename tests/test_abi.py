@@ -131,3 +131,15 @@ def test_server_config_validation(lib):
     n = C.c_int()
     _einval(lib.krr_server_poll(None, None, 0, C.byref(n)), lib, "NULL")
     _einval(lib.krr_server_step(None, None), lib, "server")
+
+
+def test_server_checkpoint_validation(lib):
+    import paper_2304_12465_gb300._native as N_
+    _einval(lib.krr_server_evict(None, 0), lib, "server")
+    _einval(lib.krr_server_resume(None, 0), lib, "server")
+    n = C.c_size_t()
+    _einval(lib.krr_server_export(None, 0, None, C.byref(n)), lib, "NULL")
+    rid = C.c_int64()
+    _einval(lib.krr_server_import(None, None, 0, None, None, None, C.byref(rid)), lib, "NULL")
+    pr = N_.RequestProgress()
+    _einval(lib.krr_server_progress(None, 0, C.byref(pr)), lib, "NULL")

@@ -176,3 +176,56 @@ def test_full_size_request_sampled_rows(K):
     Rs = Y[:, rows] - O.kmatvec(X, r["kernel"], r["sigma"], lam, alpha, rows)
     ynorm = np.linalg.norm(Y, axis=1)
     assert np.all(np.abs(Rs) <= TOL * ynorm[:, None])
+
+
+def test_evict_resume_and_checkpoint(K, data, alone):
+    """A request evicted during its first inner solve resumes on the same
+    server, and a checkpoint exported from one server finishes on another;
+    both results are bit-identical to the uninterrupted solve."""
+    i = 3                         # 16 right-hand sides, several refinements
+    r, (X, Y) = REQS[i], data[i]
+    assert alone[i]["outer_refinements"] >= 2
+
+    def run_into_first_inner_solve(srv, rid):
+        for _ in range(100000):
+            srv.step()
+            if srv.progress(rid)["state_name"] == "iterating":
+                break
+        for _ in range(3):          # the first inner solve is under way
+            srv.step()
+        assert srv.progress(rid)["state_name"] == "iterating"
+
+    with K.KrrServer(max_slots=4, iters_per_step=4) as srv:
+        rid = submit(srv, r, X, Y)
+        run_into_first_inner_solve(srv, rid)
+        srv.evict(rid)
+        for _ in range(100000):
+            srv.step()
+            if srv.progress(rid)["state_name"] == "parked":
+                break
+        pr = srv.progress(rid)
+        assert pr["state_name"] == "parked" and pr["outer_refinements"] >= 1
+        assert srv.stats()["reserved_bytes"] == 0
+        srv.resume(rid)
+        (res,) = srv.drain()
+    np.testing.assert_array_equal(res["alpha"], alone[i]["alpha"])
+    assert res["iters"] == alone[i]["iters"]
+
+    with K.KrrServer(max_slots=4, iters_per_step=4) as a:
+        rid = submit(a, r, X, Y)
+        run_into_first_inner_solve(a, rid)
+        a.evict(rid)
+        while a.progress(rid)["state_name"] != "parked":
+            a.step()
+        blob = a.export(rid)
+        with pytest.raises(K.KrrError):
+            a.progress(rid)
+    assert len(blob) > 2 * 8 * r["N"] * r["m"]
+    with K.KrrServer(max_slots=4, iters_per_step=1, use_graph=False) as b:
+        with pytest.raises(K.KrrError):
+            b.import_(b"not a checkpoint" * 10, X, Y)
+        b.import_(blob, X, Y)
+        (res,) = b.drain()
+    np.testing.assert_array_equal(res["alpha"], alone[i]["alpha"])
+    assert res["iters"] == alone[i]["iters"]
+    assert res["outer_refinements"] == alone[i]["outer_refinements"]
