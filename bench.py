@@ -51,8 +51,10 @@ def parse():
                     help="also time the plain float64 path (one step, slow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
-    ap.add_argument("--workload", default="c2", choices=["c2", "serving"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "serving"],
                     help="c2: one RPCholesky + refined PCG solve per step (headline); "
+                         "c1: the plain float64 solve; c3: the batched 8-setting x 2-shift "
+                         "product; c4: KRILL build + solve; "
                          "serving: a Poisson stream of solve requests through the server")
     ap.add_argument("--requests", type=int, default=512, help="serving: stream length")
     ap.add_argument("--n-max", type=int, default=200_000,
@@ -450,6 +452,123 @@ def run_serving(args):
         dist.destroy_process_group()
 
 
+def run_config(args):
+    """The other configurations, one step each:
+    c1 -- plain float64 path: RPCholesky (k = 200, B = 20) + float64 PCG to 1e-10,
+          N = 4096, d = 8;
+    c3 -- the batched product of 8 (kernel, sigma) settings x 2 shifts sharing one
+          tile generation, N = 500000, d = 8 (the product a batched PCG iteration runs);
+    c4 -- KRILL: krill_build (sparse sign sketch, Gram, Cholesky) + krill_solve
+          (refined PCG to 1e-6), N = 2e6, d = 20, k = 2000 centers.
+    value = kernel entries evaluated per second over the step."""
+    import torch
+    import paper_2304_12465_gb300 as K
+    from inputs import make_c1_plain_fp64, make_c3_batched, make_c4_krill
+
+    dist, rank, world = dist_setup(args.gpus)
+    K.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    extra = {}
+    if args.workload == "c1":
+        w = make_c1_plain_fp64()
+        X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
+
+        def step():
+            f = K.krr_rpcholesky(X, w.kernel, w.sigma, w.k, w.block, seed=w.seed)
+            a, info = K.krr_pcg_solve(X, w.kernel, w.sigma, Y, w.mu, f, tol=w.tol, prec="fp64")
+            rk = f.rank
+            f.free()
+            if info["status"] != "KRR_OK":
+                raise RuntimeError(f"solve did not converge: {info}")
+            return entries_rpcholesky(w.N, rk) + info["kernel_entries"], info
+        desc = (f"plain float64 KRR, N={w.N}, d={w.d}, Gaussian sigma={w.sigma}, mu={w.mu}, "
+                f"RPCholesky k={w.k} B={w.block}, float64 PCG to {w.tol}")
+        dtype = "f64"
+    elif args.workload == "c3":
+        w = make_c3_batched()
+        X = torch.from_numpy(w.X).to(dev)
+        kerns = [k for k, _ in w.settings]
+        sigmas = [sg for _, sg in w.settings]
+        ms = len(w.mus)
+        lams = [mu * w.N for _ in w.settings for mu in w.mus]
+        V = torch.from_numpy(np.random.default_rng(0).standard_normal(
+            (len(w.settings) * ms, w.N))).to(dev)
+
+        def step():
+            K.krr_kmatvec_batched(X, kerns, sigmas, lams, V)
+            return float(len(w.settings)) * w.N * w.N, {}
+        desc = (f"batched product, N={w.N}, d={w.d}, Matern-5/2 and Laplace at sigma in "
+                f"{{0.5,1,2,4}} (8 settings) x mu in {w.mus} sharing one tile generation")
+        dtype = "f32"
+        extra["entries_counted"] = "N^2 kernel evaluations per setting (8 per product)"
+    else:
+        w = make_c4_krill()
+        X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
+        centers = torch.from_numpy(w.centers).to(dev)
+
+        def step():
+            P = K.krill_build(X, w.kernel, w.sigma, centers, w.mu, seed=w.seed)
+            b, info = K.krill_solve(P, Y, w.tol)
+            P.free()
+            if info["status"] != "KRR_OK":
+                raise RuntimeError(f"solve did not converge: {info}")
+            zeta = max(1, math.ceil(math.log(w.k + 1)))
+            return zeta * float(w.N) * w.k + info["kernel_entries"], info
+        desc = (f"restricted KRR (KRILL), N={w.N}, d={w.d}, k={w.k} uniform centers, "
+                f"Gaussian sigma={w.sigma}, mu={w.mu}, sparse sign s=2k, tol {w.tol}")
+        dtype = "f32+f64"
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = K.krr_launch_count()
+    step_ms, entries, infos = [], 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        entries += n
+        infos.append(info)
+    launches = K.krr_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms, entries], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, entries = float(tmax[0]), float(t[1])
+    if rank == 0:
+        res = {"metric": METRIC, "value": entries / (total_ms / 1e3), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+               "config": {"workload": desc, "N": w.N, "d": w.d,
+                          "l2": "flushed between timed steps (512 MiB write)",
+                          "parallelism": "replicas" if world > 1 else "single GPU", **extra},
+               "clocks": clk, "gpu_launches": int(launches)}
+        if infos and infos[0]:
+            res["solve"] = {k: [i.get(k) for i in infos] for k in
+                            ("iters", "outer_refinements", "rel_residual", "t_build_s",
+                             "t_solve_s")}
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(w, target_s: float = 6.0):
     """The oracle's float64 product on a bounded sample of rows of the same
     workload, timed on this host's cores; kernel evaluations per second."""
@@ -515,6 +634,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload in ("c1", "c3", "c4"):
+        run_config(args)
     else:
         run_native(args)
 

@@ -516,6 +516,22 @@ KRR_API krr_status krr_server_import(krr_server *S, const void *buf, size_t size
 /* Waits for the device, stops the builders and frees everything.             */
 KRR_API void krr_server_destroy(krr_server *S);
 
+/* Autotuning of the float32 fused product (not in the paper).  While on     */
+/* (non-zero), the first float32 product of each (kernel, d rounded up to 4,  */
+/* m rounded up to 1/2/4/8/16, N) times candidate column tiles -- the split   */
+/* counts that make the grid 2, 4, 8, 16 and 32 waves of two CTAs per SM --   */
+/* once on the caller's stream (it synchronises that stream; a stream that is */
+/* being captured is not tuned) and keeps the fastest for the process.  Off   */
+/* (the default): 8 waves.  The split count sets the summation order, so a    */
+/* tuned product can differ from an untuned one at the rounding level; with   */
+/* a fixed choice, results are reproducible.                                  */
+KRR_API void krr_set_autotune(int on);
+
+/* Split count chosen by the autotuner for a float32 product shape, or 0 if   */
+/* that shape has not been tuned.                                             */
+KRR_API krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N,
+                                       int *splits);
+
 /* Timing instrumentation: while on (non-zero), solves record CUDA events
  * around every fused-product launch on the caller's stream and report the
  * summed device time in krr_info.kmv_ms / kmv_launches. */

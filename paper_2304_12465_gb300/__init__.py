@@ -23,6 +23,8 @@ from .api import (  # noqa: F401
     krr_rpc_sample,
     krr_rpcholesky,
     krr_server_footprint,
+    krr_autotune_choice,
+    krr_set_autotune,
     krr_set_profiling,
     krr_sparse_sign,
     krr_version,

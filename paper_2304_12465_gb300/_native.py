@@ -132,6 +132,8 @@ SIGNATURES = {
     "krr_server_export": (_int, [_vp, _i64, _vp, C.POINTER(C.c_size_t)]),
     "krr_server_import": (_int, [_vp, _vp, C.c_size_t, _vp, _vp, _vp, C.POINTER(_i64)]),
     "krr_server_destroy": (None, [_vp]),
+    "krr_set_autotune": (None, [_int]),
+    "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
     "krr_set_profiling": (None, [_int]),
     "krr_last_error": (C.c_char_p, []),
     "krr_version": (C.c_char_p, []),

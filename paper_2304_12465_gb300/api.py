@@ -370,6 +370,18 @@ def krill_solve(P: KrillPreconditioner, Y, tol: float, maxit: int = 0, stream=No
     return B, res
 
 
+def krr_set_autotune(on: bool) -> None:
+    load().krr_set_autotune(1 if on else 0)
+
+
+def krr_autotune_choice(kern, d: int, m: int, N: int) -> int:
+    """Split count the autotuner chose for a float32 product shape (0: none)."""
+    v = C.c_int()
+    check(load().krr_autotune_choice(_kern(kern), int(d), int(m), int(N), C.byref(v)),
+          "krr_autotune_choice")
+    return v.value
+
+
 def krr_set_profiling(on: bool) -> None:
     load().krr_set_profiling(1 if on else 0)
 

@@ -215,6 +215,18 @@ extern "C" {
 
 const char *krr_last_error(void) { return g_error.c_str(); }
 
+void krr_set_autotune(int on) { set_autotune(on != 0); }
+
+krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N, int *splits) {
+  clear_error();
+  KRR_REQUIRE(splits, "splits is NULL");
+  KRR_REQUIRE(valid_kernel(kern), "unknown kernel %d", (int)kern);
+  KRR_REQUIRE(d >= 1 && d <= 32 && m >= 1 && m <= 16 && N >= 1, "bad shape");
+  const int M = m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
+  *splits = tuned_splits((int)kern, (d + 3) / 4 * 4, M, N);
+  return KRR_OK;
+}
+
 const char *krr_version(void) { return "krr-gb300 0.1 (sm_103a)"; }
 
 uint64_t krr_launch_count(void) { return g_launches.load(); }

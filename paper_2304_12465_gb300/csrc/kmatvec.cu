@@ -1,5 +1,10 @@
 // Host drivers of the fused product (Alg. 1 "Product"), point preparation,
 // split reduction and kernel-column evaluation.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "kmv.cuh"
 #include "kmv_dispatch.cuh"
 
@@ -235,6 +240,84 @@ static int choose_splits(int64_t row_tiles, int64_t N, int tj, int per_sm, int w
   return (int)splits;
 }
 
+// ------------------------------------------------------------ autotuner
+// The column tile of the float32 product (the columns one CTA covers, set by
+// the number of column splits) is chosen per (kernel, padded dimension,
+// padded m, N) by timing candidate split counts -- the grid at 2, 4, 8, 16
+// and 32 waves of two CTAs per SM -- once, on the caller's stream and data,
+// when autotuning is on.  The choice is cached for the process; the default
+// rule is 8 waves.  Summation order depends on the split count, so a tuned
+// product can differ from an untuned one at the rounding level.
+static std::atomic<bool> g_autotune{false};
+static std::mutex g_tune_mtx;
+static std::map<std::tuple<int, int, int, int64_t>, int> g_tuned;
+
+void set_autotune(bool on) { g_autotune.store(on); }
+
+int tuned_splits(int kern, int dp, int M, int64_t N) {
+  std::lock_guard<std::mutex> lk(g_tune_mtx);
+  auto it = g_tuned.find(std::make_tuple(kern, dp, M, N));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
+static int kmv32_splits(const PointsF32 &P, int M, int64_t row_tiles, const Kmv32Args &base,
+                        DevBuf<float> &part, cudaStream_t s) {
+  const int64_t N = P.N;
+  const int dflt = choose_splits(row_tiles, N, KMV_TJ, 2, 8);
+  if (!g_autotune.load()) return dflt;
+  const auto key = std::make_tuple(P.kern, P.dp, M, N);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mtx);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return dflt;   // timing would synchronise a capturing stream
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return dflt;
+  }
+  int best = dflt;
+  float best_ms = 1e30f;
+  int last = -1;
+  for (int waves : {2, 4, 8, 16, 32}) {
+    const int splits = choose_splits(row_tiles, N, KMV_TJ, 2, waves);
+    if (splits == last) continue;
+    last = splits;
+    int64_t chunk = (N + splits - 1) / splits;
+    chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
+    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const size_t need = (size_t)nsplit * M * N;
+    if (part.n < need && part.alloc(need, s) != KRR_OK) break;
+    Kmv32Args a = base;
+    a.chunk = chunk;
+    a.part = part.p;
+    float ms = 0.0f;
+    bool ok = cudaEventRecord(e0, s) == cudaSuccess;
+    ok = ok && launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a) ==
+                   cudaSuccess;
+    count_launch();
+    ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+         cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = splits;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mtx);
+  g_tuned[key] = best;
+  return best;
+}
+
 krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv, int m,
                    float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
   const int64_t N = P.N;
@@ -244,7 +327,9 @@ krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv
     const int M = pad_m(mg);
     const int rows = KMV_THREADS * kmv32_rows_per_thread(P.dp, M);
     const int64_t row_tiles = (N + rows - 1) / rows;
-    const int splits = choose_splits(row_tiles, N, KMV_TJ, 2, 8);
+    const Kmv32Args base{P.xt.p, P.cn.p, N, P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg,
+                         0, nullptr};
+    const int splits = kmv32_splits(P, M, row_tiles, base, part, s);
     int64_t chunk = (N + splits - 1) / splits;
     chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
     const int nsplit = (int)((N + chunk - 1) / chunk);

@@ -60,6 +60,11 @@ krr_status kmv_ff(const PointsFF &P, double lambda, const double *V, int64_t ldv
                   double *Y, int64_t ldy, cudaStream_t s, DevBuf<double> &part,
                   DevBuf<float> &vsplit);
 
+// Autotuning of the float32 product's column tile (see krr_set_autotune);
+// tuned_splits returns the cached split count of a shape, 0 if not tuned.
+void set_autotune(bool on);
+int tuned_splits(int kern, int dp, int M, int64_t N);
+
 // Y (m x ldy, float32) = (A + lambda I) V (m x ldv, float32).
 krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv,
                    int m, float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part);

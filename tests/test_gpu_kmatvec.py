@@ -170,3 +170,25 @@ def test_batched_settings_product(K, N, d, ms):
             ref = O.kmatvec(X, kerns[q], sigmas[q], lams[col], V[col])
             bound = O.kmatvec(X, kerns[q], sigmas[q], lams[col], np.abs(V[col]))
             assert np.all(np.abs(got[col] - ref[0]) <= 2e-5 * bound[0]), (q, c)
+
+
+def test_autotuned_product(K):
+    """With autotuning on, the first float32 product of a shape times the
+    candidate column tiles and keeps one; the product still meets the float32
+    bound, repeats bit for bit, and the choice is reported."""
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((20011, 8))
+    V = rng.standard_normal((3, 20011))
+    ref = O.kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, np.arange(0, 20011, 97))
+    bound = f32_product_bound(X, O.GAUSSIAN, 1.1, 0.5, V, np.arange(0, 20011, 97))
+    assert K.krr_autotune_choice(O.GAUSSIAN, 8, 3, 20011) == 0
+    K.krr_set_autotune(True)
+    try:
+        a = K.krr_kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, prec="mixed")
+        b = K.krr_kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, prec="mixed")
+    finally:
+        K.krr_set_autotune(False)
+    splits = K.krr_autotune_choice(O.GAUSSIAN, 8, 3, 20011)
+    assert 1 <= splits <= (20011 + 63) // 64
+    np.testing.assert_array_equal(a, b)
+    assert np.all(np.abs(a[:, ::97] - ref) <= 2e-5 * bound)
