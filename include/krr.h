@@ -88,7 +88,11 @@ typedef struct {
                                 mixed path, summed over refinement steps)    */
     int outer_refinements;   /* float64 residual recomputations (mixed path)  */
     int rank;                /* factor rank used                              */
-    int reserved;
+    int escalated;           /* mixed path: 1 if the float32 inner iterations
+                                stalled (an inner solve ran into half the
+                                iteration budget or refinement stopped
+                                improving) and the solve finished with float64
+                                CG vectors and float-float products           */
     double rel_residual;     /* max over columns of ||y - M x|| / ||y||,
                                 recomputed in float64 after the solve         */
     double kernel_entries;   /* kernel entries kappa(x_i, x_j) evaluated      */

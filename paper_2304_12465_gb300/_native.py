@@ -23,7 +23,7 @@ PIVOT_RPCHOLESKY, PIVOT_UNIFORM, PIVOT_GREEDY = 0, 1, 2
 
 class KrrInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer_refinements", C.c_int), ("rank", C.c_int),
-                ("reserved", C.c_int), ("rel_residual", C.c_double),
+                ("escalated", C.c_int), ("rel_residual", C.c_double),
                 ("kernel_entries", C.c_double), ("t_build_s", C.c_double),
                 ("t_solve_s", C.c_double), ("kmv_ms", C.c_double),
                 ("kmv_launches", C.c_int), ("kmv64_launches", C.c_int),

@@ -29,6 +29,7 @@
 #include "pcg.cuh"
 #include "rpc.cuh"
 #include "serve.cuh"
+#include "solve.cuh"
 
 namespace krr {
 
@@ -501,13 +502,6 @@ __global__ void __launch_bounds__(1024) serve_sumsq_kernel(const double *__restr
   }
 }
 
-__global__ void serve_add_f64_kernel(double *__restrict__ x, const double *__restrict__ d,
-                                     int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    x[e] += d[e];
-}
-
 static unsigned serve_vec_grid() { return (unsigned)(num_sms() * 4); }
 
 // Optional per-kernel timing of a step (events after every launch).
@@ -948,105 +942,44 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
 static double worst_rel(const Slot *sl);
 
 // Higher-precision continuation of a solve whose float32 inner iterations
-// stopped making progress (the float32 product's rounding exceeds the shift
-// lambda for very small mu): the same refinement loop with float64 CG
-// vectors, the float-float product inside the inner PCG and the Woodbury
-// preconditioner applied in float64 to the float32 factor it was built from.
-// Runs on a worker thread; the slot's data are not used by anything else.
+// stopped making progress (escalate_refine: float64 CG vectors, float-float
+// products, float64 residuals if needed).  Runs on a worker thread; the
+// slot's data are not used by anything else meanwhile.
 static krr_status escalate_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   (void)S;
-  const int64_t N = sl->N, nm = N * sl->m;
-  const int m = sl->m;
-  const double lambda = sl->mu * (double)N;
-  DevBuf<double> b64, d64, F64;
-  KRR_TRY(b64.alloc((size_t)nm, s));
-  KRR_TRY(d64.alloc((size_t)nm, s));
-  krr_factor view;   // float64 copy of the float32 factor (exactly representable)
-  view.N = N;
-  NystromCore identity;
-  identity.lambda = lambda;
-  const NystromCore *core = sl->core ? sl->core : &identity;
-  if (sl->core && sl->core->rank > 0) {
-    KRR_TRY(F64.alloc((size_t)N * sl->core->rank, s));
-    KRR_TRY(convert_f32_to_f64(sl->core->F32, F64.p, N * sl->core->rank, s));
-    view.F = F64.p;
-  }
-  PcgOps<double> ops;
-  ops.product = [&](const double *in, double *out, cudaStream_t st) {
-    return kmv_ff(sl->Pff, lambda, in, N, m, out, N, st, sl->ffpart, sl->ffvsplit);
-  };
-  ops.precond = [&](const double *in, double *out, cudaStream_t st) {
-    return nystrom_apply_f64(&view, core, in, m, out, st);
-  };
-  // second stage: when even these residuals stall (the float-float product's
-  // own rounding, about 2^-48 of sum_j |a_ij x_j|, is then of the order of
-  // the residual), residuals come from the float64 product on the caller's X
-  DevBuf<double> X64, part64;
-  bool res64 = false;
-  auto residual64 = [&]() -> krr_status {
-    KRR_TRY(kmv_f64(X64.p, N, sl->d, sl->kern, sl->sigma, lambda, sl->alpha64, N, m, sl->mx64,
-                    N, s, part64));
-    sl->entries += kmv_entries(N);
-    KRR_TRY(residual_f64(sl->Y64, sl->mx64, sl->r64, nm, s));
-    return column_norms(sl->r64, N, m, sl->rn.data(), s);
-  };
+  Escalation e;
+  e.Pff = &sl->Pff;
+  e.X = sl->X;
+  e.N = sl->N;
+  e.d = sl->d;
+  e.kern = sl->kern;
+  e.m = sl->m;
+  e.sigma = sl->sigma;
+  e.lambda = sl->mu * (double)sl->N;
+  e.tol = sl->tol;
+  e.core = sl->core;
+  e.Y = sl->Y64;
+  e.alpha = sl->alpha64;
+  e.r64 = sl->r64;
+  e.mx = sl->mx64;
+  e.yn = sl->yn;
+  e.rn = sl->rn;
+  e.budget = sl->budget;
+  e.iters = sl->iters;
+  e.outer = sl->outer;
+  e.entries = sl->entries;
+  e.ffpart = &sl->ffpart;
+  e.ffvsplit = &sl->ffvsplit;
   sl->escalated = true;
-  krr_status final_status = KRR_ENOCONV;
-  double prev = 1e300;
-  for (int outer = 0;; ++outer) {
-    double worst = worst_rel(sl);
-    sl->relres = worst;
-    if (worst <= sl->tol) { final_status = KRR_OK; break; }
-    if (outer >= 10 || sl->budget <= 0) break;
-    if (outer > 0 && worst > 0.5 * prev) {
-      if (res64) break;
-      res64 = true;
-      KRR_TRY(X64.alloc((size_t)N * sl->d, s));
-      KRR_CUDA_TRY(cudaMemcpyAsync(X64.p, sl->X, sizeof(double) * N * sl->d, cudaMemcpyDefault,
-                                   s));
-      KRR_TRY(residual64());
-      worst = worst_rel(sl);
-      sl->relres = worst;
-      if (worst <= sl->tol) { final_status = KRR_OK; break; }
-    }
-    prev = worst;
-    std::vector<double> itol(m);
-    KRR_CUDA_TRY(cudaMemcpyAsync(b64.p, sl->r64, sizeof(double) * nm, cudaMemcpyDeviceToDevice,
-                                 s));
-    for (int c = 0; c < m; ++c) {
-      const double rel = sl->yn[c] > 0 ? sl->rn[c] / sl->yn[c] : 0.0;
-      itol[c] = rel > sl->tol ? std::max(0.3 * sl->tol / rel, 1e-12) : 1.0;
-      if (!(rel > sl->tol))
-        KRR_CUDA_TRY(cudaMemsetAsync(b64.p + (int64_t)c * N, 0, sizeof(double) * N, s));
-    }
-    PcgStats st;
-    KRR_TRY(pcg_run<double>(ops, N, m, b64.p, d64.p, itol.data(), sl->budget, s, &st));
-    sl->iters += st.iters_max;
-    sl->budget -= st.iters_max;
-    sl->entries += kmv_entries(N) * (st.products + 1);
-    serve_add_f64_kernel<<<serve_vec_grid(), 256, 0, s>>>(sl->alpha64, d64.p, nm);
-    KRR_LAUNCH_CHECK();
-    if (res64) {
-      KRR_TRY(residual64());
-    } else {
-      KRR_TRY(kmv_ff(sl->Pff, lambda, sl->alpha64, N, m, sl->mx64, N, s, sl->ffpart,
-                     sl->ffvsplit));
-      KRR_TRY(residual_f64(sl->Y64, sl->mx64, sl->r64, nm, s));
-      KRR_TRY(column_norms(sl->r64, N, m, sl->rn.data(), s));
-    }
-    sl->outer += 1;
-    if (st.breakdown) {
-      final_status = KRR_EBREAKDOWN;
-      break;
-    }
-  }
-  if (final_status != KRR_OK) {
-    sl->relres = worst_rel(sl);
-    if (sl->relres <= sl->tol) final_status = KRR_OK;
-  }
-  view.F = nullptr;
-  sl->status = final_status;
-  return KRR_OK;
+  const krr_status st = escalate_refine(e, s);
+  sl->rn = e.rn;
+  sl->budget = e.budget;
+  sl->iters = e.iters;
+  sl->outer = e.outer;
+  sl->entries = e.entries;
+  sl->relres = e.relres;
+  sl->status = e.status;
+  return st;
 }
 
 static void builder_main(krr_server *S, int b) {

@@ -63,7 +63,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
   (void)t0;
   std::vector<double> tolv(m, tol);
   double entries = 0.0;
-  int outer = 0, iters_total = 0;
+  int outer = 0, iters_total = 0, escalated = 0;
   double relres = 0.0;
   krr_status final_status = KRR_OK;
 
@@ -124,12 +124,53 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     relres = rs.relres;
     final_status = rs.status;
     entries += kmv_entries(N) * (rs.products32 + rs.products64);
+    if (final_status != KRR_OK && maxit - rs.iters > 0) {
+      // the float32 inner iterations stalled: continue in higher precision
+      DevBuf<double> r64, mx;
+      KRR_TRY(r64.alloc((size_t)N * m, s));
+      KRR_TRY(mx.alloc((size_t)N * m, s));
+      Escalation e;
+      e.Pff = &Pff;
+      e.X = Xd;
+      e.N = N;
+      e.d = d;
+      e.kern = kern;
+      e.m = m;
+      e.sigma = sigma;
+      e.lambda = lambda;
+      e.tol = tol;
+      e.core = core;
+      e.Y = Y;
+      e.alpha = alpha;
+      e.r64 = r64.p;
+      e.mx = mx.p;
+      e.yn.resize(m);
+      e.rn.resize(m);
+      KRR_TRY(column_norms(Y, N, m, e.yn.data(), s));
+      KRR_TRY(kmv_ff(Pff, lambda, alpha, N, m, mx.p, N, s, part64, vsplit));
+      KRR_TRY(residual_f64(Y, mx.p, r64.p, (int64_t)N * m, s));
+      KRR_TRY(column_norms(r64.p, N, m, e.rn.data(), s));
+      e.budget = maxit - rs.iters;
+      e.iters = rs.iters;
+      e.outer = rs.outer;
+      e.entries = kmv_entries(N);
+      e.ffpart = &part64;
+      e.ffvsplit = &vsplit;
+      KRR_TRY(escalate_refine(e, s));
+      iters_total = e.iters;
+      outer = e.outer;
+      relres = e.relres;
+      final_status = e.status;
+      entries += e.entries;
+      escalated = 1;
+    }
   }
   KRR_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) {
     info->iters = iters_total;
     info->outer_refinements = outer;
     info->rank = F ? F->rank : 0;
+    info->escalated = escalated;
     info->rel_residual = relres;
     info->kernel_entries = entries;
     info->t_build_s = t_build;
@@ -192,17 +233,22 @@ krr_status refine_solve(const PcgOps<float> &ops,
       if (!(rel > tol))
         KRR_CUDA_TRY(cudaMemsetAsync(b32.p + (int64_t)c * N, 0, sizeof(float) * N, s));
     }
+    // one float32 inner solve may use at most half the iteration budget: one
+    // that runs into this cap has stalled (see escalate_refine)
+    const int limit = std::min(budget, std::max(1, maxit / 2));
     PcgStats st;
-    KRR_TRY(pcg_run<float>(ops, N, m, b32.p, d32.p, inner_tol.data(), budget, s, &st));
+    KRR_TRY(pcg_run<float>(ops, N, m, b32.p, d32.p, inner_tol.data(), limit, s, &st));
     iters += st.iters_max;
     budget -= st.iters_max;
     prod32 += st.products;
+    const bool capped = st.iters_max >= limit && !st.converged;
     KRR_TRY(add_f32_to_f64(alpha, d32.p, N * m, s));
     KRR_TRY(product64(alpha, mx.p, s));
     KRR_TRY(residual_f64(Y, mx.p, r64.p, N * m, s));
     KRR_TRY(column_norms(r64.p, N, m, rn.data(), s));
     ++outer;
     if (st.breakdown) { final_status = KRR_EBREAKDOWN; break; }
+    if (capped && worst_rel() > tol) break;
   }
   if (final_status != KRR_OK && final_status != KRR_EBREAKDOWN) {
     relres = worst_rel();
@@ -293,6 +339,7 @@ krr_status pcg_solve_batched_device(const double *Xd, int64_t N, int d, int S,
     info->iters = rs.iters;
     info->outer_refinements = rs.outer;
     info->rank = 0;
+    info->escalated = 0;
     for (int q = 0; q < S; ++q)
       if (factors && factors[q]) info->rank = std::max(info->rank, factors[q]->rank);
     info->rel_residual = rs.relres;
@@ -392,6 +439,7 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
     info->iters = iters_total;
     info->outer_refinements = outer;
     info->rank = k;
+    info->escalated = 0;
     info->rel_residual = relres;
     info->kernel_entries = entries;
     info->t_build_s = P->build_s;
@@ -405,6 +453,103 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
     set_error("KRILL PCG did not reach the tolerance (%.3e > %.3e)", relres, tol);
     return KRR_ENOCONV;
   }
+  return KRR_OK;
+}
+
+}  // namespace krr
+
+namespace krr {
+
+static double escalation_worst(const Escalation &e) {
+  double w = 0.0;
+  for (int c = 0; c < e.m; ++c) w = std::max(w, e.yn[c] > 0 ? e.rn[c] / e.yn[c] : 0.0);
+  return w;
+}
+
+krr_status escalate_refine(Escalation &e, cudaStream_t s) {
+  const int64_t N = e.N, nm = N * e.m;
+  const int m = e.m;
+  DevBuf<double> b64, d64, F64, X64, part64;
+  KRR_TRY(b64.alloc((size_t)nm, s));
+  KRR_TRY(d64.alloc((size_t)nm, s));
+  // the float32 factor in float64 (exactly representable), consistent with
+  // the mixed core W that was built from it
+  krr_factor view;
+  view.N = N;
+  NystromCore identity;
+  identity.lambda = e.lambda;
+  const NystromCore *core = (e.core && e.core->rank > 0) ? e.core : &identity;
+  if (core != &identity) {
+    KRR_TRY(F64.alloc((size_t)N * core->rank, s));
+    KRR_TRY(convert_f32_to_f64(core->F32, F64.p, N * core->rank, s));
+    view.F = F64.p;
+  }
+  PcgOps<double> ops;
+  ops.product = [&](const double *in, double *out, cudaStream_t st) {
+    return kmv_ff(*e.Pff, e.lambda, in, N, m, out, N, st, *e.ffpart, *e.ffvsplit);
+  };
+  ops.precond = [&](const double *in, double *out, cudaStream_t st) {
+    return nystrom_apply_f64(&view, core, in, m, out, st);
+  };
+  // second stage: the float-float product's own rounding (about 2^-48 of
+  // sum_j |a_ij x_j|) can reach the order of the residual; residuals then come
+  // from the float64 product
+  bool res64 = false;
+  const double *Xdev = nullptr;
+  auto residual = [&]() -> krr_status {
+    if (res64)
+      KRR_TRY(kmv_f64(Xdev, N, e.d, e.kern, e.sigma, e.lambda, e.alpha, N, m, e.mx, N, s,
+                      part64));
+    else
+      KRR_TRY(kmv_ff(*e.Pff, e.lambda, e.alpha, N, m, e.mx, N, s, *e.ffpart, *e.ffvsplit));
+    e.entries += kmv_entries(N);
+    KRR_TRY(residual_f64(e.Y, e.mx, e.r64, nm, s));
+    return column_norms(e.r64, N, m, e.rn.data(), s);
+  };
+  e.status = KRR_ENOCONV;
+  double prev = 1e300;
+  for (int outer = 0;; ++outer) {
+    double worst = escalation_worst(e);
+    e.relres = worst;
+    if (worst <= e.tol) { e.status = KRR_OK; break; }
+    if (outer >= 10 || e.budget <= 0) break;
+    if (outer > 0 && worst > 0.5 * prev) {
+      if (res64) break;
+      res64 = true;
+      KRR_TRY(device_view(e.X, (size_t)N * e.d, s, X64, &Xdev));
+      KRR_TRY(residual());
+      worst = escalation_worst(e);
+      e.relres = worst;
+      if (worst <= e.tol) { e.status = KRR_OK; break; }
+    }
+    prev = worst;
+    std::vector<double> itol(m);
+    KRR_CUDA_TRY(cudaMemcpyAsync(b64.p, e.r64, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    for (int c = 0; c < m; ++c) {
+      const double rel = e.yn[c] > 0 ? e.rn[c] / e.yn[c] : 0.0;
+      itol[c] = rel > e.tol ? std::max(0.3 * e.tol / rel, 1e-12) : 1.0;
+      if (!(rel > e.tol))
+        KRR_CUDA_TRY(cudaMemsetAsync(b64.p + (int64_t)c * N, 0, sizeof(double) * N, s));
+    }
+    PcgStats st;
+    KRR_TRY(pcg_run<double>(ops, N, m, b64.p, d64.p, itol.data(), e.budget, s, &st));
+    e.iters += st.iters_max;
+    e.budget -= st.iters_max;
+    e.entries += kmv_entries(N) * st.products;
+    add_f64_kernel<<<ceil_div(nm, 256), 256, 0, s>>>(e.alpha, d64.p, nm);
+    KRR_LAUNCH_CHECK();
+    KRR_TRY(residual());
+    e.outer += 1;
+    if (st.breakdown) {
+      e.status = KRR_EBREAKDOWN;
+      break;
+    }
+  }
+  if (e.status != KRR_OK) {
+    e.relres = escalation_worst(e);
+    if (e.relres <= e.tol) e.status = KRR_OK;
+  }
+  view.F = nullptr;
   return KRR_OK;
 }
 

@@ -148,3 +148,29 @@ def test_batched_settings_solve(K):
             assert rr.max() <= 1e-8, (q, c, rr)
     one, _ = K.krr_pcg_solve(w.X, kerns[1], sigmas[1], Y[2:3], mus[0], factors[1], tol=1e-8)
     assert rel_err(alpha[2], one[0]) < 1e-5
+
+
+def smooth_tiny_mu_problem(seed):
+    """x ~ N(0, I_4), a wide Gaussian (sigma = 3) and mu = 1e-8: lambda = 3e-5
+    is far below the float32 product's rounding (about 1e-7 of sum_j a_ij |v_j|),
+    so float32 inner iterations cannot converge."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((3000, 4))
+    Y = np.stack([np.sin(X @ rng.standard_normal(4)) for _ in range(2)])
+    return X, Y
+
+
+def test_mixed_solve_escalates_when_float32_stalls(K):
+    """The mixed path hands a stalled float32 refinement to the float64-vector,
+    float-float continuation and still meets the tolerance (oracle residual)."""
+    X, Y = smooth_tiny_mu_problem(5)
+    f = K.krr_rpcholesky(X, O.GAUSSIAN, 3.0, 300, seed=1)
+    a, info = K.krr_pcg_solve(X, O.GAUSSIAN, 3.0, Y, 1e-8, f, tol=1e-6, maxit=2000,
+                              prec="mixed")
+    f.free()
+    assert info["status"] == "KRR_OK", info
+    assert info["escalated"] == 1
+    R = Y - O.kmatvec(X, O.GAUSSIAN, 3.0, 1e-8 * 3000, a)
+    rel = np.linalg.norm(R, axis=1) / np.linalg.norm(Y, axis=1)
+    assert rel.max() <= 1e-6 * 1.001, rel
+    assert abs(info["rel_residual"] - rel.max()) <= 1e-9

@@ -229,3 +229,27 @@ def test_evict_resume_and_checkpoint(K, data, alone):
     np.testing.assert_array_equal(res["alpha"], alone[i]["alpha"])
     assert res["iters"] == alone[i]["iters"]
     assert res["outer_refinements"] == alone[i]["outer_refinements"]
+
+
+def test_escalated_request(K):
+    """A request whose float32 inner iterations stall (wide Gaussian, mu =
+    1e-8) is continued in higher precision by the server and meets the
+    tolerance against the oracle; its result is the same alone and in a mix."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((3000, 4))
+    Y = np.stack([np.sin(X @ rng.standard_normal(4)) for _ in range(2)])
+    hard = dict(N=3000, d=4, kernel=O.GAUSSIAN, sigma=3.0, mu=1e-8, m=2, seed=1, k=300)
+    with K.KrrServer(max_slots=4) as srv:
+        submit(srv, hard, X, Y)
+        (res,) = srv.drain()
+    assert res["status_name"] == "KRR_OK" and res["escalated"] == 1
+    R = Y - O.kmatvec(X, O.GAUSSIAN, 3.0, 1e-8 * 3000, res["alpha"])
+    rel = np.linalg.norm(R, axis=1) / np.linalg.norm(Y, axis=1)
+    assert rel.max() <= TOL * 1.001
+    easy = dict(N=2000, d=8, kernel=O.LAPLACE_L1, sigma=1.0, mu=1e-5, m=3, seed=2, k=200)
+    Xe, Ye = make_serving_request(easy)
+    with K.KrrServer(max_slots=4) as srv:
+        ids = {submit(srv, hard, X, Y): "hard", submit(srv, easy, Xe, Ye): "easy"}
+        done = {ids[d["id"]]: d for d in srv.drain()}
+    np.testing.assert_array_equal(done["hard"]["alpha"], res["alpha"])
+    assert done["easy"]["status_name"] == "KRR_OK"
