@@ -85,6 +85,19 @@ def dist_setup(n_gpus):
     return None, 0, 1
 
 
+def aggregate_ranks(dist, total_ms: float, work: float, device="cpu"):
+    """Whole-job figures of the replicas: the slowest rank's time and the work
+    of all ranks (identity without a process group)."""
+    if dist is None:
+        return total_ms, work
+    import torch
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    tsum = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -197,12 +210,7 @@ def run_native(args):
 
     total_ms = float(sum(step_ms))
     entries = float(sum(i["entries"] for i in infos))
-    if dist:
-        t = torch.tensor([total_ms, entries], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, entries = float(tmax[0]), float(t[1])
+    total_ms, entries = aggregate_ranks(dist, total_ms, entries, dev)
     value = entries / (total_ms / 1e3)
 
     # roofline of the dominant kernel: the float32 fused product
@@ -423,10 +431,8 @@ def run_serving(args):
     clk = clocks.stop()
     head = runs[f"{rates[0]:g}x"]
     wall = head["wall_s"]
-    if dist:
-        t = torch.tensor([wall], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t[0])
+    wall, _ = aggregate_ranks(dist, wall * 1e3, 0.0, "cuda")
+    wall /= 1e3
     value = world * args.requests / wall
     if rank == 0:
         print(json.dumps({
@@ -548,12 +554,7 @@ def run_config(args):
     launches = K.krr_launch_count() - launches0
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms, entries], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, entries = float(tmax[0]), float(t[1])
+    total_ms, entries = aggregate_ranks(dist, total_ms, entries, dev)
     if rank == 0:
         res = {"metric": METRIC, "value": entries / (total_ms / 1e3), "unit": UNIT,
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -363,10 +363,13 @@ KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
 /* (krr_server_footprint) stays within the server's HBM budget.  Builder      */
 /* threads, each with its own stream, copy X and Y to the device and build the*/
 /* factor, the Woodbury core and the prepared points; the solve then keeps    */
-/* them and its CG state resident.  Each krr_server_step advances the inner   */
-/* PCG iteration of every iterating request by iters_per_step iterations,     */
-/* one grouped launch per phase for all of them (replayed as one CUDA graph   */
-/* when use_graph is set), while inner-solve starts, float-float refinement   */
+/* them and its CG state resident.  Iterating requests step in two lanes     */
+/* that advance independently: a fast lane for requests whose float32 product */
+/* costs at most 4e10 flop per iteration (N^2 (2 d' + 2 m' + 5), d' and m'   */
+/* the padded sizes) and a bulk lane for the rest.  A step of a lane advances */
+/* each of its requests by iters_per_step inner PCG iterations with one       */
+/* grouped launch per phase for all of them (replayed as one CUDA graph when  */
+/* use_graph is set), while inner-solve starts, float-float refinement        */
 /* residuals and result copies run on per-slot streams.  A result does not    */
 /* depend on which other requests are being served: every per-request work    */
 /* decomposition and sum order is fixed by that request alone.                */
@@ -447,8 +450,9 @@ KRR_API krr_status krr_server_submit(krr_server *S, const double *X, int64_t N, 
                                      double mu, int k, uint64_t seed, double tol, int maxit,
                                      double *alpha_out, int64_t *id_out);
 
-/* Admits what fits, takes finished builds and slot events, and runs one step */
-/* for the iterating requests (returns when that step's status is back).      */
+/* Admits what fits, takes finished builds and slot events, launches a step  */
+/* in every idle lane that has iterating requests, and returns when a lane's  */
+/* step has completed (at once when nothing is in flight).                    */
 /* *unfinished (optional): queued plus admitted requests not yet reported.    */
 KRR_API krr_status krr_server_step(krr_server *S, int64_t *unfinished);
 

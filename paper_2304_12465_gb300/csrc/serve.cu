@@ -688,6 +688,7 @@ struct Slot {
   double t_submit = 0, t_admit = 0, t_built = 0;
   // engine state
   int id = -1;
+  int lane = 1;                // stepping lane (0: fast, 1: bulk)
   Phase phase = Phase::Queued;
   krr_status build_status = KRR_OK;
   std::string error;
@@ -732,37 +733,52 @@ constexpr char kCheckpointMagic[8] = {'K', 'R', 'R', 'C', 'K', 'P', 'T', '1'};
 
 }  // namespace
 
+namespace krr {
+// Slots step in two lanes that advance independently: a fast lane for slots
+// whose float32 product is cheap and a bulk lane for the rest, so a small
+// solve's steps are not paced by the largest slot's iterations.
+constexpr int SERVE_LANES = 2;
+constexpr double SERVE_FAST_LANE_FLOP = 4e10;   // float32 product flop per iteration
+
+struct Lane {
+  cudaStream_t s = nullptr;
+  ServeTable *table_dev = nullptr;      // work table of the lane's steps
+  ServeTable *table_host = nullptr;     // pinned
+  ServeStatus *status_host = nullptr;   // pinned copy of the status array
+  ProductBranches branches;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  PhaseEvents phase_ev;
+  bool dirty = true;                    // slot set changed since the table was written
+  bool busy = false;                    // a step is in flight
+  std::vector<Slot *> members;          // slots of the step in flight
+};
+}  // namespace krr
+
 struct krr_server {
   krr_server_config cfg{};
   int device = 0;
   Clock::time_point t0;
-  cudaStream_t s_iter = nullptr, s_free = nullptr;
+  cudaStream_t s_free = nullptr;
+  krr::Lane lanes[krr::SERVE_LANES];
   cudaStream_t s_build[krr::SERVE_MAX_BUILDERS] = {};
   int nbuilders = 0;
   cudaStream_t s_slot[krr::SERVE_MAX_SLOTS] = {};
   cudaEvent_t ev_slot[krr::SERVE_MAX_SLOTS] = {};
-  cudaEvent_t ev_step = nullptr;
-  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // device time of a step
   // device
-  ServeTable *table_dev = nullptr;
   ServeTable *init_dev = nullptr;      // one single-slot table per slot index
   ServeScalars *scalars_dev = nullptr;
   ServeStatus *status_dev = nullptr;
-  krr::ProductBranches branches;
   int64_t captures = 0;
   // pinned host
-  ServeTable *table_host = nullptr;
   ServeTable *init_host = nullptr;
-  ServeStatus *status_host = nullptr;
   ServeControl *ctl_host = nullptr;
   double *sumsq_host = nullptr;
-  cudaGraphExec_t graph = nullptr;
   // slots
   std::unique_ptr<Slot> slots[krr::SERVE_MAX_SLOTS];
   std::deque<std::unique_ptr<Slot>> queue;
   std::vector<std::unique_ptr<Slot>> parked;   // evicted, waiting for resume / export
   std::vector<krr_request_result> done;
-  bool table_dirty = true;
   // builders
   std::vector<std::thread> builders;
   std::mutex mtx;
@@ -777,7 +793,6 @@ struct krr_server {
   int max_concurrent = 0;
   double step_ms = 0, build_s = 0, escalate_s = 0;
   double phase_ms[krr::SERVE_KERNELS_PER_ITER] = {};
-  krr::PhaseEvents phase_ev;
   int64_t escalations = 0;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -874,6 +889,7 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   D.Wt = sl->core ? sl->core->Wt : nullptr;
   D.sc = S->scalars_dev + sl->id;
   D.status = S->status_dev + sl->id;
+  sl->lane = (double)N * (double)N * (2.0 * dp + 2.0 * M + 5.0) <= SERVE_FAST_LANE_FLOP ? 0 : 1;
 
   // one arena for the slot's solve state, 256-byte aligned pieces
   size_t off = 0;
@@ -1214,7 +1230,7 @@ static krr_status on_event(krr_server *S, Slot *sl) {
       return decide(S, sl);
     case Phase::Init:
       sl->phase = Phase::Inner;
-      S->table_dirty = true;
+      S->lanes[sl->lane].dirty = true;
       return KRR_OK;
     case Phase::Refine:
       sl->rn.assign(sl->m, 0.0);
@@ -1256,35 +1272,35 @@ static void admit(krr_server *S) {
   }
 }
 
-static krr_status launch_step(krr_server *S, int nslots) {
+static krr_status launch_step(krr_server *S, Lane &L) {
   const int U = S->cfg.iters_per_step;
-  const ServeTable *Th = S->table_host;
+  const ServeTable *Th = L.table_host;
   const unsigned long long kernels =
       (unsigned long long)U * (SERVE_KERNELS_PER_ITER - 1 + Th->nclasses);
   if (S->cfg.use_graph) {
-    if (!S->graph) {
+    if (!L.graph) {
       // the launch sequence depends on the variants present: captured again
-      // whenever the slot set changes
+      // whenever the lane's slot set changes
       cudaGraph_t g = nullptr;
       set_launch_counting(false);
-      KRR_CUDA_TRY(cudaStreamBeginCapture(S->s_iter, cudaStreamCaptureModeThreadLocal));
-      krr_status st = serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter);
-      cudaError_t e = cudaStreamEndCapture(S->s_iter, &g);
+      KRR_CUDA_TRY(cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal));
+      krr_status st = serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s);
+      cudaError_t e = cudaStreamEndCapture(L.s, &g);
       set_launch_counting(true);
       if (st != KRR_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
       }
       KRR_CUDA_TRY(e);
-      e = cudaGraphInstantiate(&S->graph, g, 0);
+      e = cudaGraphInstantiate(&L.graph, g, 0);
       cudaGraphDestroy(g);
       KRR_CUDA_TRY(e);
       S->captures += 1;
     }
-    KRR_CUDA_TRY(cudaGraphLaunch(S->graph, S->s_iter));
+    KRR_CUDA_TRY(cudaGraphLaunch(L.graph, L.s));
     count_launches(kernels);
   } else if (profiling_on()) {
-    PhaseEvents &pe = S->phase_ev;
+    PhaseEvents &pe = L.phase_ev;
     const size_t need = (size_t)U * SERVE_KERNELS_PER_ITER + 1;
     while (pe.ev.size() < need) {
       cudaEvent_t e;
@@ -1292,13 +1308,42 @@ static krr_status launch_step(krr_server *S, int nslots) {
       pe.ev.push_back(e);
     }
     pe.next = 0;
-    KRR_TRY(serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter, &pe));
+    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s, &pe));
   } else {
-    KRR_TRY(serve_launch_iterations(S->table_dev, Th, S->branches, U, S->s_iter));
+    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s));
   }
   S->steps += 1;
   S->step_kernels += (int64_t)kernels;
-  S->max_concurrent = std::max(S->max_concurrent, nslots);
+  return KRR_OK;
+}
+
+// A lane's step has completed: device times, then every slot whose inner
+// solve ended goes on to its refinement residual.
+static krr_status finish_step(krr_server *S, Lane &L) {
+  L.busy = false;
+  float ms = 0.0f;
+  KRR_CUDA_TRY(cudaEventElapsedTime(&ms, L.ev_t0, L.ev_t1));
+  S->step_ms += ms;
+  if (L.phase_ev.next > 1) {
+    for (size_t e = 1; e < L.phase_ev.next; ++e) {
+      float pm = 0.0f;
+      KRR_CUDA_TRY(cudaEventElapsedTime(&pm, L.phase_ev.ev[e - 1], L.phase_ev.ev[e]));
+      S->phase_ms[(e - 1) % SERVE_KERNELS_PER_ITER] += pm;
+    }
+    L.phase_ev.next = 0;
+  }
+  for (Slot *sl : L.members) {
+    const ServeStatus &st = L.status_host[sl->id];
+    if (st.live) continue;
+    sl->iters += st.iters_max;
+    sl->budget -= st.iters_max;
+    sl->entries += kmv_entries(sl->N) * st.iters_max;
+    sl->breakdown = st.breakdown != 0;
+    sl->inner_capped = st.iters_max >= sl->inner_limit;
+    L.dirty = true;
+    KRR_TRY(start_refine(S, sl));
+  }
+  L.members.clear();
   return KRR_OK;
 }
 
@@ -1330,60 +1375,63 @@ static krr_status service(krr_server *S) {
 
 static krr_status server_step(krr_server *S, int64_t *unfinished) {
   KRR_TRY(service(S));
-  std::vector<Slot *> inner;
+  // launch a step in every idle lane that has iterating slots
+  int iterating = 0;
   for (int i = 0; i < SERVE_MAX_SLOTS; ++i)
-    if (S->slots[i] && S->slots[i]->phase == Phase::Inner) inner.push_back(S->slots[i].get());
-  if (!inner.empty()) {
-    if (S->table_dirty) {
-      ServeTable *T = S->table_host;
+    if (S->slots[i] && S->slots[i]->phase == Phase::Inner) ++iterating;
+  bool launched = false;
+  for (int l = 0; l < SERVE_LANES; ++l) {
+    Lane &L = S->lanes[l];
+    if (L.busy) continue;
+    std::vector<Slot *> inner;
+    for (int i = 0; i < SERVE_MAX_SLOTS; ++i)
+      if (S->slots[i] && S->slots[i]->phase == Phase::Inner && S->slots[i]->lane == l)
+        inner.push_back(S->slots[i].get());
+    if (inner.empty()) continue;
+    if (L.dirty) {
+      ServeTable *T = L.table_host;
       T->nslots = 0;
       for (Slot *sl : inner) table_add(T, sl->desc);
-      KRR_CUDA_TRY(cudaMemcpyAsync(S->table_dev, T, table_bytes(T->nslots),
-                                   cudaMemcpyHostToDevice, S->s_iter));
-      S->table_dirty = false;
-      if (S->graph) {
-        KRR_CUDA_TRY(cudaGraphExecDestroy(S->graph));
-        S->graph = nullptr;
+      KRR_CUDA_TRY(cudaMemcpyAsync(L.table_dev, T, table_bytes(T->nslots),
+                                   cudaMemcpyHostToDevice, L.s));
+      L.dirty = false;
+      if (L.graph) {
+        KRR_CUDA_TRY(cudaGraphExecDestroy(L.graph));
+        L.graph = nullptr;
       }
     }
-    KRR_CUDA_TRY(cudaEventRecord(S->ev_t0, S->s_iter));
-    KRR_TRY(launch_step(S, (int)inner.size()));
-    KRR_CUDA_TRY(cudaEventRecord(S->ev_t1, S->s_iter));
-    KRR_CUDA_TRY(cudaMemcpyAsync(S->status_host, S->status_dev,
+    KRR_CUDA_TRY(cudaEventRecord(L.ev_t0, L.s));
+    KRR_TRY(launch_step(S, L));
+    KRR_CUDA_TRY(cudaEventRecord(L.ev_t1, L.s));
+    KRR_CUDA_TRY(cudaMemcpyAsync(L.status_host, S->status_dev,
                                  sizeof(ServeStatus) * SERVE_MAX_SLOTS, cudaMemcpyDeviceToHost,
-                                 S->s_iter));
-    KRR_CUDA_TRY(cudaEventRecord(S->ev_step, S->s_iter));
-    // keep the other slots moving while the step runs
+                                 L.s));
+    KRR_CUDA_TRY(cudaEventRecord(L.ev_done, L.s));
+    L.busy = true;
+    L.members = inner;
+    launched = true;
+  }
+  S->max_concurrent = std::max(S->max_concurrent, iterating);
+  bool any_busy = false;
+  for (int l = 0; l < SERVE_LANES; ++l) any_busy = any_busy || S->lanes[l].busy;
+  if (any_busy) {
+    // keep the other slots moving until a lane's step completes
     for (;;) {
-      const cudaError_t e = cudaEventQuery(S->ev_step);
-      if (e == cudaSuccess) break;
-      if (e != cudaErrorNotReady) KRR_CUDA_TRY(e);
+      bool finished = false;
+      for (int l = 0; l < SERVE_LANES; ++l) {
+        Lane &L = S->lanes[l];
+        if (!L.busy) continue;
+        const cudaError_t e = cudaEventQuery(L.ev_done);
+        if (e == cudaErrorNotReady) continue;
+        KRR_CUDA_TRY(e);
+        KRR_TRY(finish_step(S, L));
+        finished = true;
+      }
+      if (finished) break;
       KRR_TRY(service(S));
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
-    float ms = 0.0f;
-    KRR_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev_t0, S->ev_t1));
-    S->step_ms += ms;
-    if (S->phase_ev.next > 1) {
-      for (size_t e = 1; e < S->phase_ev.next; ++e) {
-        float pm = 0.0f;
-        KRR_CUDA_TRY(cudaEventElapsedTime(&pm, S->phase_ev.ev[e - 1], S->phase_ev.ev[e]));
-        S->phase_ms[(e - 1) % SERVE_KERNELS_PER_ITER] += pm;
-      }
-      S->phase_ev.next = 0;
-    }
-    for (Slot *sl : inner) {
-      const ServeStatus &st = S->status_host[sl->id];
-      if (st.live) continue;
-      sl->iters += st.iters_max;
-      sl->budget -= st.iters_max;
-      sl->entries += kmv_entries(sl->N) * st.iters_max;
-      sl->breakdown = st.breakdown != 0;
-      sl->inner_capped = st.iters_max >= sl->inner_limit;
-      S->table_dirty = true;
-      KRR_TRY(start_refine(S, sl));
-    }
-  } else {
+  } else if (!launched) {
     bool busy = false;
     for (int i = 0; i < SERVE_MAX_SLOTS; ++i) busy = busy || (bool)S->slots[i];
     if (busy) std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -1417,30 +1465,33 @@ static void server_free(krr_server *S) {
   cudaDeviceSynchronize();
   S->queue.clear();
   S->parked.clear();
-  if (S->graph) cudaGraphExecDestroy(S->graph);
-  cudaFree(S->table_dev);
+  for (int l = 0; l < SERVE_LANES; ++l) {
+    Lane &L = S->lanes[l];
+    if (L.graph) cudaGraphExecDestroy(L.graph);
+    cudaFree(L.table_dev);
+    cudaFreeHost(L.table_host);
+    cudaFreeHost(L.status_host);
+    for (int b = 0; b < SERVE_BRANCHES; ++b) {
+      if (L.branches.side[b]) cudaStreamDestroy(L.branches.side[b]);
+      if (L.branches.join[b]) cudaEventDestroy(L.branches.join[b]);
+    }
+    if (L.branches.fork) cudaEventDestroy(L.branches.fork);
+    for (cudaEvent_t e : L.phase_ev.ev) cudaEventDestroy(e);
+    if (L.ev_done) cudaEventDestroy(L.ev_done);
+    if (L.ev_t0) cudaEventDestroy(L.ev_t0);
+    if (L.ev_t1) cudaEventDestroy(L.ev_t1);
+    if (L.s) cudaStreamDestroy(L.s);
+  }
   cudaFree(S->init_dev);
   cudaFree(S->scalars_dev);
   cudaFree(S->status_dev);
-  for (int b = 0; b < SERVE_BRANCHES; ++b) {
-    if (S->branches.side[b]) cudaStreamDestroy(S->branches.side[b]);
-    if (S->branches.join[b]) cudaEventDestroy(S->branches.join[b]);
-  }
-  if (S->branches.fork) cudaEventDestroy(S->branches.fork);
-  cudaFreeHost(S->table_host);
   cudaFreeHost(S->init_host);
-  cudaFreeHost(S->status_host);
   cudaFreeHost(S->ctl_host);
   cudaFreeHost(S->sumsq_host);
   for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
     if (S->ev_slot[i]) cudaEventDestroy(S->ev_slot[i]);
     if (S->s_slot[i]) cudaStreamDestroy(S->s_slot[i]);
   }
-  if (S->ev_step) cudaEventDestroy(S->ev_step);
-  for (cudaEvent_t e : S->phase_ev.ev) cudaEventDestroy(e);
-  if (S->ev_t0) cudaEventDestroy(S->ev_t0);
-  if (S->ev_t1) cudaEventDestroy(S->ev_t1);
-  if (S->s_iter) cudaStreamDestroy(S->s_iter);
   for (int b = 0; b < SERVE_MAX_BUILDERS; ++b)
     if (S->s_build[b]) cudaStreamDestroy(S->s_build[b]);
   if (S->s_free) cudaStreamDestroy(S->s_free);
@@ -1451,7 +1502,25 @@ static krr_status server_init(krr_server *S) {
   KRR_CUDA_TRY(cudaGetDevice(&S->device));
   int lo = 0, hi = 0;
   KRR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-  KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_iter, cudaStreamNonBlocking, hi));
+  for (int l = 0; l < SERVE_LANES; ++l) {
+    Lane &L = S->lanes[l];
+    // the fast lane gets the highest priority, the bulk lane the next one
+    const int prio = (l == 0 || hi == lo) ? hi : hi + 1;
+    KRR_CUDA_TRY(cudaStreamCreateWithPriority(&L.s, cudaStreamNonBlocking, prio));
+    KRR_CUDA_TRY(cudaEventCreateWithFlags(&L.ev_done, cudaEventDisableTiming));
+    KRR_CUDA_TRY(cudaEventCreate(&L.ev_t0));
+    KRR_CUDA_TRY(cudaEventCreate(&L.ev_t1));
+    KRR_CUDA_TRY(cudaMalloc(&L.table_dev, sizeof(ServeTable)));
+    KRR_CUDA_TRY(cudaMemset(L.table_dev, 0, sizeof(ServeTable)));
+    KRR_CUDA_TRY(cudaMallocHost(&L.table_host, sizeof(ServeTable)));
+    std::memset(L.table_host, 0, sizeof(ServeTable));
+    KRR_CUDA_TRY(cudaMallocHost(&L.status_host, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
+    for (int b = 0; b < SERVE_BRANCHES; ++b) {
+      KRR_CUDA_TRY(cudaStreamCreateWithPriority(&L.branches.side[b], cudaStreamNonBlocking, prio));
+      KRR_CUDA_TRY(cudaEventCreateWithFlags(&L.branches.join[b], cudaEventDisableTiming));
+    }
+    KRR_CUDA_TRY(cudaEventCreateWithFlags(&L.branches.fork, cudaEventDisableTiming));
+  }
   S->nbuilders = S->cfg.build_threads > 0 ? S->cfg.build_threads : 4;
   for (int b = 0; b < S->nbuilders; ++b)
     KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_build[b], cudaStreamNonBlocking, lo));
@@ -1460,27 +1529,14 @@ static krr_status server_init(krr_server *S) {
     KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->s_slot[i], cudaStreamNonBlocking, hi));
     KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_slot[i], cudaEventDisableTiming));
   }
-  KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_step, cudaEventDisableTiming));
-  KRR_CUDA_TRY(cudaEventCreate(&S->ev_t0));
-  KRR_CUDA_TRY(cudaEventCreate(&S->ev_t1));
-  KRR_CUDA_TRY(cudaMalloc(&S->table_dev, sizeof(ServeTable)));
   KRR_CUDA_TRY(cudaMalloc(&S->init_dev, sizeof(ServeTable) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMalloc(&S->scalars_dev, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMalloc(&S->status_dev, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
-  for (int b = 0; b < SERVE_BRANCHES; ++b) {
-    KRR_CUDA_TRY(cudaStreamCreateWithPriority(&S->branches.side[b], cudaStreamNonBlocking, hi));
-    KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->branches.join[b], cudaEventDisableTiming));
-  }
-  KRR_CUDA_TRY(cudaEventCreateWithFlags(&S->branches.fork, cudaEventDisableTiming));
   KRR_CUDA_TRY(cudaMemset(S->scalars_dev, 0, sizeof(ServeScalars) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMemset(S->status_dev, 0, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
-  KRR_CUDA_TRY(cudaMemset(S->table_dev, 0, sizeof(ServeTable)));
-  KRR_CUDA_TRY(cudaMallocHost(&S->table_host, sizeof(ServeTable)));
   KRR_CUDA_TRY(cudaMallocHost(&S->init_host, sizeof(ServeTable) * SERVE_MAX_SLOTS));
-  KRR_CUDA_TRY(cudaMallocHost(&S->status_host, sizeof(ServeStatus) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMallocHost(&S->ctl_host, sizeof(ServeControl) * SERVE_MAX_SLOTS));
   KRR_CUDA_TRY(cudaMallocHost(&S->sumsq_host, sizeof(double) * SERVE_MAX_SLOTS * SERVE_MAX_M));
-  std::memset(S->table_host, 0, sizeof(ServeTable));
   if (S->cfg.hbm_budget_bytes > 0) {
     S->budget = (int64_t)S->cfg.hbm_budget_bytes;
   } else {

@@ -1,13 +1,13 @@
 // Device-side layout of the serving engine (serve.cu, serve_kmv.cu).
 //
 // Every admitted solve ("slot") keeps its prepared points, its Nystrom
-// preconditioner and its float32 CG state resident in HBM.  A step of the
-// engine advances the inner PCG iteration of every slot that is iterating
-// with one grouped launch per phase of Alg. 1's loop: each launch is a fixed
-// grid of CTAs that walks a work list spanning all slots (product tiles, row
-// blocks, triangular rows, CG columns).  The work list lives in a device
-// table, so the launch sequence of a step never changes with the slot set and
-// is captured once as a CUDA graph.
+// preconditioner and its float32 CG state resident in HBM.  A step advances
+// the inner PCG iteration of the iterating slots of one lane with one product
+// launch per variant present and one grouped launch per other phase of
+// Alg. 1's loop: each is a grid of CTAs that walks a work list spanning the
+// slots (product tiles, row blocks, triangular rows, CG columns).  The work
+// list lives in a device table; the launch sequence only changes with the
+// set of variants present, and is captured as a CUDA graph.
 //
 // A slot's work decomposition (tile shape, column splits, row blocks) is a
 // function of that slot alone, and every sum is taken in a fixed order, so a
