@@ -512,6 +512,15 @@ def run_config(args):
                 f"{{0.5,1,2,4}} (8 settings) x mu in {w.mus} sharing one tile generation")
         dtype = "f32"
         extra["entries_counted"] = "N^2 kernel evaluations per setting (8 per product)"
+        # per pair of points: d differences, d squares-and-adds, d |.|-adds; per
+        # Matern setting sqrt, scale, ex2, 2-FMA polynomial, product (6 flop +
+        # 2 MUFU); per Laplace setting scale + ex2 (1 flop + 1 MUFU); 2 FMA per
+        # shift column (4 flop) for every setting
+        nmat = sum(1 for k in kerns if k == 2)
+        nlap = len(kerns) - nmat
+        flop_pair = 4 * w.d + nmat * 6 + nlap * 1 + len(kerns) * 2 * ms * 2
+        mufu_pair = 2 * nmat + nlap
+        extra["roofline_model"] = {"flop_per_pair": flop_pair, "mufu_per_pair": mufu_pair}
     else:
         w = make_c4_krill()
         X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
@@ -564,6 +573,23 @@ def run_config(args):
                           "l2": "flushed between timed steps (512 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single GPU", **extra},
                "clocks": clk, "gpu_launches": int(launches)}
+        if args.workload == "c3":
+            pairs = float(w.N) * w.N
+            sec = total_ms / args.steps / 1e3
+            sm_max = clk.get("sm_max_mhz") or 2070.0
+            peak_flop = 152 * 128 * 2 * sm_max * 1e6
+            peak_mufu = 152 * 32 * sm_max * 1e6
+            t_flop = pairs * extra["roofline_model"]["flop_per_pair"] / peak_flop
+            t_mufu = pairs * extra["roofline_model"]["mufu_per_pair"] / peak_mufu
+            res["roofline"] = {
+                "kernel": "kmvb_kernel (batched 8-setting product)", "bound": "alu",
+                "achieved": pairs * extra["roofline_model"]["flop_per_pair"] / sec / 1e12,
+                "peak": peak_flop / 1e12, "unit": "TFLOP/s",
+                "frac": max(t_flop, t_mufu) / sec, "traffic": None,
+                "peak_basis": f"FP32 152 x 128 x 2 x {sm_max:.0f} MHz and MUFU 152 x 32 "
+                              f"x {sm_max:.0f} MHz (derived); frac = the larger of the FP32 "
+                              f"and MUFU times over the measured time",
+                "fp32_time_s": t_flop, "mufu_time_s": t_mufu}
         if infos and infos[0]:
             res["solve"] = {k: [i.get(k) for i in infos] for k in
                             ("iters", "outer_refinements", "rel_residual", "t_build_s",
