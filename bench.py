@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--fp64-path", action="store_true",
                     help="also time the plain float64 path (one step, slow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma"],
+                    help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "serving"],
                     help="c2: one RPCholesky + refined PCG solve per step (headline); "
@@ -148,14 +150,56 @@ class ClockSampler:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # float32 product, mean of three launches from one ncu capture of this bench's
-# default workload, keyed by (kernel, N, d, m, autotuned column splits).  Any
-# other shape or tile has no capture and reports None; a change to the kernel
-# invalidates the entry until it is captured again.
-KMV32_TRAFFIC = {(0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768}
+# default workload, keyed by (path, kernel, N, d, m, autotuned column splits).
+# Any other shape or tile has no capture and reports None; a change to the
+# kernel invalidates the entry until it is captured again.
+KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768}
 
 
-def kmv32_traffic(w, splits):
-    return KMV32_TRAFFIC.get((w.kernel, w.N, w.d, w.m, splits))
+def kmv32_traffic(path, w, splits):
+    return KMV32_TRAFFIC.get((path, w.kernel, w.N, w.d, w.m, splits))
+
+
+def measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json beside this file, else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+def product_roofline(path, w, per_launch_ms, splits, sm_max):
+    """Roofline of the float32 product.  Tensor path: the three fp16 MMAs per
+    16 coordinates (2 x 16 x 3 flop per entry and block) against the dense
+    16-bit tensor peak; FMA path: (2d + 1 + 2m) flop per entry against the FP32
+    FMA peak at the maximum SM clock."""
+    entries = float(w.N) * w.N
+    sec = per_launch_ms / 1e3
+    traffic = kmv32_traffic(path, w, splits)
+    if path == "tensor" and w.kernel != 1:
+        blocks = (w.d + 15) // 16
+        flop_per_entry = 2 * 16 * 3 * blocks
+        peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
+        achieved = flop_per_entry * entries / sec / 1e12
+        mufu = 1 if w.kernel == 0 else 2
+        return {"kernel": "kmvtc_kernel (tensor-core product, fp16 two-half split)",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_basis": f"dense 16-bit tensor peak, {basis} (bf16 cuBLAS, sustained; "
+                              "fp16 has the same nominal rate)",
+                "flop_per_entry": flop_per_entry, "entries_per_launch": entries,
+                "other_pipes_per_entry": {"ex2": mufu, "fp32_lane_ops": 2 + 2 * w.m}}
+    flop_per_entry = 2 * w.d + 1 + 2 * w.m          # dot (d FMA) + c_i + c_j + m FMA
+    achieved = flop_per_entry * entries / sec / 1e12
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA units x clock
+    return {"kernel": "kmv32_kernel (fused float32 product)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_basis": f"152 SM x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                          "(max SM clock); derived, not measured",
+            "flop_per_entry": flop_per_entry, "entries_per_launch": entries}
 
 
 def entries_rpcholesky(N, k):
@@ -170,6 +214,7 @@ def run_native(args):
 
     dist, rank, world = dist_setup(args.gpus)
     K.load()
+    K.krr_set_product_path(args.product_path)
     w = make_c2_mixed(n=args.n)
     dev = torch.device("cuda", torch.cuda.current_device())
     X = torch.from_numpy(w.X).to(dev)
@@ -229,11 +274,8 @@ def run_native(args):
     kmv_ms = sum(i["kmv_ms"] for i in infos)
     kmv_n = sum(i["kmv_launches"] for i in infos)
     per_launch_ms = kmv_ms / max(kmv_n, 1)
-    flop_per_entry = 2 * w.d + 1 + 2 * w.m          # dot (d FMA) + c_i + c_j + m FMA
-    flop_per_launch = flop_per_entry * float(w.N) * w.N
-    achieved = flop_per_launch / (per_launch_ms / 1e3) / 1e12
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA units x clock
+    splits = K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)
     kmv64_ms = sum(i["kmv64_ms"] for i in infos)
     kmv64_n = sum(i["kmv64_launches"] for i in infos)
     kmvff_ms = sum(i["kmvff_ms"] for i in infos)
@@ -264,15 +306,9 @@ def run_native(args):
                 "kmv64_launches": kmv64_n,
                 "kmvff_ms_per_launch": kmvff_ms / max(kmvff_n, 1),
                 "kmvff_launches": kmvff_n,
-                "kmv32_splits_autotuned": K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)},
-        "roofline": {"kernel": "kmv32_kernel (fused float32 product)", "bound": "alu",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": kmv32_traffic(w, K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)),
-                     "peak_basis": f"152 SM x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                                   "(max SM clock); derived, not measured",
-                     "flop_per_entry": flop_per_entry,
-                     "entries_per_launch": float(w.N) * w.N},
+                "kmv32_splits_autotuned": splits,
+                "product_path": args.product_path},
+        "roofline": product_roofline(args.product_path, w, per_launch_ms, splits, sm_max),
         "clocks": clk,
         "gpu_launches": int(launches),
     }

@@ -536,9 +536,25 @@ KRR_API void krr_server_destroy(krr_server *S);
 KRR_API void krr_set_autotune(int on);
 
 /* Split count chosen by the autotuner for a float32 product shape, or 0 if   */
-/* that shape has not been tuned.                                             */
+/* that shape has not been tuned (for the path krr_set_product_path selects). */
 KRR_API krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N,
                                        int *splits);
+
+/* Path of the float32 fused product (the product of Alg. 1 inside the mixed  */
+/* solve, and krr_kmatvec with KRR_PREC_MIXED) for the Gaussian and Matern    */
+/* kernels (Sec. 2.1: both are functions of |x_i - x_j|^2):                   */
+/*   KRR_PRODUCT_TENSOR (0, default): the inner products x_i . x_j on the     */
+/*     tensor cores from a two-half split of each centred, scaled coordinate  */
+/*     (x = h + l, |x - h - l| <= 2^-22 |x|; three fp16 MMAs with float32     */
+/*     accumulation), kernel values and sums over V in float32.  Points whose */
+/*     centred, scaled coordinates exceed 16384 in magnitude, and the Laplace */
+/*     kernel, take the FMA path.                                             */
+/*   KRR_PRODUCT_FMA (1): every entry on the float32 FMA pipe.                */
+/* Both paths meet the float32 error bound of krr_kmatvec; their results      */
+/* differ at the rounding level.  Process-wide; not thread-safe with solves   */
+/* in flight.  KRR_EINVAL for another value.                                  */
+typedef enum { KRR_PRODUCT_TENSOR = 0, KRR_PRODUCT_FMA = 1 } krr_product_path;
+KRR_API krr_status krr_set_product_path(int path);
 
 /* Timing instrumentation: while on (non-zero), solves record CUDA events
  * around every fused-product launch on the caller's stream and report the

@@ -25,6 +25,7 @@ from .api import (  # noqa: F401
     krr_server_footprint,
     krr_autotune_choice,
     krr_set_autotune,
+    krr_set_product_path,
     krr_set_profiling,
     krr_sparse_sign,
     krr_version,

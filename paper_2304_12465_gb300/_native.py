@@ -19,6 +19,8 @@ STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA",
 GAUSSIAN, LAPLACE_L1, MATERN52 = 0, 1, 2
 PREC_FP64, PREC_MIXED, PREC_FLOAT_FLOAT = 0, 1, 2
 PIVOT_RPCHOLESKY, PIVOT_UNIFORM, PIVOT_GREEDY = 0, 1, 2
+# float32 product path (krr_set_product_path)
+PRODUCT_TENSOR, PRODUCT_FMA = 0, 1
 
 
 class KrrInfo(C.Structure):
@@ -134,6 +136,7 @@ SIGNATURES = {
     "krr_server_destroy": (None, [_vp]),
     "krr_set_autotune": (None, [_int]),
     "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
+    "krr_set_product_path": (_int, [_int]),
     "krr_set_profiling": (None, [_int]),
     "krr_last_error": (C.c_char_p, []),
     "krr_version": (C.c_char_p, []),

@@ -382,6 +382,13 @@ def krr_autotune_choice(kern, d: int, m: int, N: int) -> int:
     return v.value
 
 
+def krr_set_product_path(path) -> None:
+    """Path of the float32 product for the Gaussian and Matern kernels:
+    "tensor" (inner products on the tensor cores, the default) or "fma"."""
+    code = {"tensor": 0, "fma": 1}.get(path, path)
+    check(load().krr_set_product_path(int(code)), "krr_set_product_path")
+
+
 def krr_set_profiling(on: bool) -> None:
     load().krr_set_profiling(1 if on else 0)
 

@@ -227,6 +227,14 @@ krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N, int *sp
   return KRR_OK;
 }
 
+krr_status krr_set_product_path(int path) {
+  clear_error();
+  KRR_REQUIRE(path == KRR_PRODUCT_TENSOR || path == KRR_PRODUCT_FMA, "unknown product path %d",
+              path);
+  set_product_path(path);
+  return KRR_OK;
+}
+
 const char *krr_version(void) { return "krr-gb300 0.1 (sm_103a)"; }
 
 uint64_t krr_launch_count(void) { return g_launches.load(); }
@@ -265,6 +273,7 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
   } else {
     PointsF32 P;
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
+    KRR_TRY(prepare_points_tc(Xd, s, P));
     DevBuf<float> v32, y32, part;
     KRR_TRY(v32.alloc((size_t)N * m, s));
     KRR_TRY(y32.alloc((size_t)N * m, s));

@@ -7,6 +7,7 @@
 
 #include "kmv.cuh"
 #include "kmv_dispatch.cuh"
+#include "kmvtc_kernels.cuh"
 
 namespace krr {
 
@@ -241,31 +242,52 @@ static int choose_splits(int64_t row_tiles, int64_t N, int tj, int per_sm, int w
 }
 
 // ------------------------------------------------------------ autotuner
-// The column tile of the float32 product (the columns one CTA covers, set by
-// the number of column splits) is chosen per (kernel, padded dimension,
-// padded m, N) by timing candidate split counts -- the grid at 2, 4, 8, 16
-// and 32 waves of two CTAs per SM -- once, on the caller's stream and data,
-// when autotuning is on.  The choice is cached for the process; the default
-// rule is 8 waves.  Summation order depends on the split count, so a tuned
+// The column tile of the float32 products (the columns one CTA covers, set by
+// the number of column splits) is chosen per (path, kernel, padded
+// dimension, padded m, N) by timing candidate split counts -- the grid at 2,
+// 4, 8, 16 and 32 waves -- once, on the caller's stream and data, when
+// autotuning is on.  The choice is cached for the process; the default rule
+// is 8 waves.  Summation order depends on the split count, so a tuned
 // product can differ from an untuned one at the rounding level.
 static std::atomic<bool> g_autotune{false};
+static std::atomic<int> g_product_path{0};
 static std::mutex g_tune_mtx;
-static std::map<std::tuple<int, int, int, int64_t>, int> g_tuned;
+static std::map<std::tuple<int, int, int, int, int64_t>, int> g_tuned;
 
 void set_autotune(bool on) { g_autotune.store(on); }
+void set_product_path(int path) { g_product_path.store(path); }
+int product_path() { return g_product_path.load(); }
+
+// Path a float32 product of this shape takes: 1 tensor cores, 0 FMA.
+static int path_of(int kern, int dp) {
+  return (g_product_path.load() == 0 && kern != KLAPLACE && dp <= 32) ? 1 : 0;
+}
 
 int tuned_splits(int kern, int dp, int M, int64_t N) {
+  const int path = path_of(kern, dp);
+  const int dim = path ? (dp + 15) / 16 : dp;
+  const int Mk = path ? (M > 8 ? 8 : M) : M;
   std::lock_guard<std::mutex> lk(g_tune_mtx);
-  auto it = g_tuned.find(std::make_tuple(kern, dp, M, N));
+  auto it = g_tuned.find(std::make_tuple(path, kern, dim, Mk, N));
   return it == g_tuned.end() ? 0 : it->second;
 }
 
-static int kmv32_splits(const PointsF32 &P, int M, int64_t row_tiles, const Kmv32Args &base,
-                        DevBuf<float> &part, cudaStream_t s) {
-  const int64_t N = P.N;
-  const int dflt = choose_splits(row_tiles, N, KMV_TJ, 2, 8);
+// chunk (a multiple of tj) and split count for `splits` requested splits
+static void split_shape(int64_t N, int splits, int tj, int64_t *chunk, int *nsplit) {
+  int64_t c = (N + splits - 1) / splits;
+  c = (c + tj - 1) / tj * tj;
+  *chunk = c;
+  *nsplit = (int)((N + c - 1) / c);
+}
+
+// launch(chunk, nsplit, part) issues one product with that column split.
+template <typename Launch>
+static int choose_product_splits(int path, int kern, int dim, int M, int64_t N,
+                                 int64_t row_tiles, int tj, int per_sm, DevBuf<float> &part,
+                                 cudaStream_t s, Launch launch) {
+  const int dflt = choose_splits(row_tiles, N, tj, per_sm, 8);
   if (!g_autotune.load()) return dflt;
-  const auto key = std::make_tuple(P.kern, P.dp, M, N);
+  const auto key = std::make_tuple(path, kern, dim, M, N);
   {
     std::lock_guard<std::mutex> lk(g_tune_mtx);
     auto it = g_tuned.find(key);
@@ -284,21 +306,17 @@ static int kmv32_splits(const PointsF32 &P, int M, int64_t row_tiles, const Kmv3
   float best_ms = 1e30f;
   int last = -1;
   for (int waves : {2, 4, 8, 16, 32}) {
-    const int splits = choose_splits(row_tiles, N, KMV_TJ, 2, waves);
+    const int splits = choose_splits(row_tiles, N, tj, per_sm, waves);
     if (splits == last) continue;
     last = splits;
-    int64_t chunk = (N + splits - 1) / splits;
-    chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
-    const int nsplit = (int)((N + chunk - 1) / chunk);
+    int64_t chunk;
+    int nsplit;
+    split_shape(N, splits, tj, &chunk, &nsplit);
     const size_t need = (size_t)nsplit * M * N;
     if (part.n < need && part.alloc(need, s) != KRR_OK) break;
-    Kmv32Args a = base;
-    a.chunk = chunk;
-    a.part = part.p;
     float ms = 0.0f;
     bool ok = cudaEventRecord(e0, s) == cudaSuccess;
-    ok = ok && launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a) ==
-                   cudaSuccess;
+    ok = ok && launch(chunk, nsplit, part.p) == cudaSuccess;
     count_launch();
     ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
          cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
@@ -318,28 +336,69 @@ static int kmv32_splits(const PointsF32 &P, int M, int64_t row_tiles, const Kmv3
   return best;
 }
 
+// Tensor-core product over right-hand-side groups of at most 8.
+static krr_status kmv_tc(const PointsF32 &P, float lambda, const float *V, int64_t ldv, int m,
+                         float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
+  const int64_t N = P.N;
+  const int KC = P.kc16;
+  for (int c0 = 0; c0 < m; c0 += 8) {
+    const int mg = (m - c0 < 8) ? (m - c0) : 8;
+    const int M = pad_m(mg);
+    const int64_t row_tiles = (N + kmvtc_rows_per_cta(KC, M) - 1) / kmvtc_rows_per_cta(KC, M);
+    const float *Vg = V + (int64_t)c0 * ldv;
+    auto launch = [&](int64_t chunk, int nsplit, float *pp) {
+      const KmvTcArgs a{P.xs16.p, P.cs16.p, Vg, ldv, N, mg, chunk, pp};
+      return launch_kmvtc(P.kern, KC, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    };
+    const int splits =
+        choose_product_splits(1, P.kern, KC, M, N, row_tiles, KTC_TJ, 1, part, s, launch);
+    int64_t chunk;
+    int nsplit;
+    split_shape(N, splits, KTC_TJ, &chunk, &nsplit);
+    const size_t need = (size_t)nsplit * M * N;
+    if (part.n < need) KRR_TRY(part.alloc(need, s));
+    KmvTimer tm;
+    tm.begin(s);
+    cudaError_t e = launch(chunk, nsplit, part.p);
+    tm.end(s);
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("tensor-core product launch failed: %s", cudaGetErrorString(e));
+      return KRR_ECUDA;
+    }
+    kmv_reduce_kernel<float, 16><<<ceil_div(N, 256), 256, 0, s>>>(
+        part.p, nsplit, M, N, mg, lambda, Vg, ldv, Y + (int64_t)c0 * ldy, ldy);
+    KRR_LAUNCH_CHECK();
+  }
+  return KRR_OK;
+}
+
 krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv, int m,
                    float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
   const int64_t N = P.N;
   if (N == 0 || m == 0) return KRR_OK;
+  if (P.kc16 > 0 && path_of(P.kern, P.dp) == 1)
+    return kmv_tc(P, lambda, V, ldv, m, Y, ldy, s, part);
   for (int c0 = 0; c0 < m; c0 += 16) {
     const int mg = (m - c0 < 16) ? (m - c0) : 16;
     const int M = pad_m(mg);
     const int rows = KMV_THREADS * kmv32_rows_per_thread(P.dp, M);
     const int64_t row_tiles = (N + rows - 1) / rows;
-    const Kmv32Args base{P.xt.p, P.cn.p, N, P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg,
-                         0, nullptr};
-    const int splits = kmv32_splits(P, M, row_tiles, base, part, s);
-    int64_t chunk = (N + splits - 1) / splits;
-    chunk = (chunk + KMV_TJ - 1) / KMV_TJ * KMV_TJ;
-    const int nsplit = (int)((N + chunk - 1) / chunk);
+    const float *Vg = V + (int64_t)c0 * ldv;
+    auto launch = [&](int64_t chunk, int nsplit, float *pp) {
+      const Kmv32Args a{P.xt.p, P.cn.p, N, P.xt.p, P.cn.p, Vg, ldv, N, mg, chunk, pp};
+      return launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    };
+    const int splits =
+        choose_product_splits(0, P.kern, P.dp, M, N, row_tiles, KMV_TJ, 2, part, s, launch);
+    int64_t chunk;
+    int nsplit;
+    split_shape(N, splits, KMV_TJ, &chunk, &nsplit);
     const size_t need = (size_t)nsplit * M * N;
     if (part.n < need) KRR_TRY(part.alloc(need, s));
-    Kmv32Args a{P.xt.p, P.cn.p, N, P.xt.p, P.cn.p, V + (int64_t)c0 * ldv, ldv, N, mg, chunk,
-                part.p};
     KmvTimer tm;
     tm.begin(s);
-    cudaError_t e = launch_kmv32_any(P.kern, P.dp, M, dim3((unsigned)row_tiles, nsplit), s, a);
+    cudaError_t e = launch(chunk, nsplit, part.p);
     tm.end(s);
     count_launch();
     if (e != cudaSuccess) {
@@ -347,8 +406,7 @@ krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv
       return KRR_ECUDA;
     }
     kmv_reduce_kernel<float, 16><<<ceil_div(N, 256), 256, 0, s>>>(
-        part.p, nsplit, M, N, mg, lambda, V + (int64_t)c0 * ldv, ldv,
-        Y + (int64_t)c0 * ldy, ldy);
+        part.p, nsplit, M, N, mg, lambda, Vg, ldv, Y + (int64_t)c0 * ldy, ldy);
     KRR_LAUNCH_CHECK();
   }
   return KRR_OK;

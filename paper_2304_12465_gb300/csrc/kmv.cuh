@@ -16,6 +16,11 @@ struct PointsF32 {
   int64_t N = 0;
   int kern = 0;
   double sigma = 0.0;
+  // half-split layout of the tensor-core product (kmvtc_kernels.cuh), present
+  // when kc16 > 0: N x kc16 x 4 groups of 16 bytes, and c_i
+  DevBuf<uint4> xs16;
+  DevBuf<float> cs16;
+  int kc16 = 0;
 };
 
 // mean_dev (optional, d doubles on the device): centre to use instead of the
@@ -25,6 +30,30 @@ struct PointsF32 {
 krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
                               double sigma, cudaStream_t s, PointsF32 &P,
                               const double *mean_dev = nullptr, int dp = 0);
+
+// Adds the half-split layout of the tensor-core product to P (prepared by
+// prepare_points_f32 from the same Xd) for the Gaussian and Matern kernels;
+// leaves P.kc16 = 0 (FMA product) for Laplace or when a centred, scaled
+// coordinate exceeds the half-precision split's range.  Synchronises s.
+krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P);
+
+struct KmvTcArgs {
+  const uint4 *xs;
+  const float *cs;
+  const float *V;
+  int64_t ldv, N;
+  int m;
+  int64_t chunk;
+  float *part;
+};
+cudaError_t launch_kmvtc(int kern, int KC, int M, dim3 grid, cudaStream_t s,
+                         const KmvTcArgs &a);
+int kmvtc_rows_per_cta(int KC, int M);
+
+// Product path of kmv_f32 when P has the half-split layout: 0 tensor cores
+// (default), 1 the FMA kernel (see krr_set_product_path).
+void set_product_path(int path);
+int product_path();
 
 // Prediction products (no shift): Y (Nr x m) = K(rows, columns) V.
 krr_status kcross_f32(const PointsF32 &R, const PointsF32 &P, const float *V, int64_t ldv,

@@ -101,6 +101,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     // iterative refinement: float64 outer loop around a float32 inner PCG
     PointsF32 P;
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
+    KRR_TRY(prepare_points_tc(Xd, s, P));
     PointsFF Pff;
     KRR_TRY(prepare_points_ff(Xd, N, d, kern, sigma, s, Pff));
     DevBuf<float> part32, vsplit;

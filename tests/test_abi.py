@@ -92,6 +92,15 @@ def test_argument_validation_before_any_launch(lib):
             "ndraw")
 
 
+def test_product_path_selection(lib):
+    """krr_set_product_path takes the two documented paths (host state only)
+    and refuses anything else."""
+    _einval(lib.krr_set_product_path(2), lib, "product path")
+    _einval(lib.krr_set_product_path(-1), lib, "product path")
+    assert lib.krr_set_product_path(1) == 0
+    assert lib.krr_set_product_path(0) == 0
+
+
 def test_server_footprint_is_host_only_and_monotone(lib):
     """The admission estimate needs no device and grows with every size."""
     def fp(N, d, m, k):

@@ -52,6 +52,50 @@ def test_fp32_product(K, kern, N, d, m):
 
 
 @pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,d,m", [(1, 1, 1), (130, 16, 11), (1031, 16, 4), (777, 24, 8),
+                                   (2049, 5, 2)])
+def test_fp32_product_paths(K, kern, N, d, m):
+    """Both float32 product paths (inner products on the tensor cores from
+    the two-half split, or every entry on the FMA pipe) meet the float32
+    bound; the Gaussian and Matern results differ between the paths (the
+    tensor path ran), the Laplace results do not (it has no tensor path)."""
+    rng = np.random.default_rng(N * 17 + d + kern)
+    X = rng.standard_normal((N, d))
+    V = rng.standard_normal((m, N))
+    ref = O.kmatvec(X, kern, 0.9, 0.5, V)
+    bound = f32_product_bound(X, kern, 0.9, 0.5, V)
+    try:
+        K.krr_set_product_path("fma")
+        fma = K.krr_kmatvec(X, kern, 0.9, 0.5, V, prec="mixed")
+    finally:
+        K.krr_set_product_path("tensor")
+    tc = K.krr_kmatvec(X, kern, 0.9, 0.5, V, prec="mixed")
+    assert np.all(np.abs(fma - ref) <= 2e-5 * bound)
+    assert np.all(np.abs(tc - ref) <= 2e-5 * bound)
+    if kern == O.LAPLACE_L1:
+        np.testing.assert_array_equal(tc, fma)
+    elif N > 1:
+        assert not np.array_equal(tc, fma)
+
+
+def test_fp32_product_large_coordinates(K):
+    """Centred, scaled coordinates beyond the half split's range (|x| / sigma
+    ~ 1e5) take the FMA path: the result equals the FMA path bit for bit."""
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((500, 6)) * 1e3
+    V = rng.standard_normal((2, 500))
+    try:
+        K.krr_set_product_path("fma")
+        fma = K.krr_kmatvec(X, O.GAUSSIAN, 0.02, 0.5, V, prec="mixed")
+    finally:
+        K.krr_set_product_path("tensor")
+    tc = K.krr_kmatvec(X, O.GAUSSIAN, 0.02, 0.5, V, prec="mixed")
+    np.testing.assert_array_equal(tc, fma)
+    with pytest.raises(K.KrrError):
+        K.krr_set_product_path(2)
+
+
+@pytest.mark.parametrize("kern", KERNS)
 @pytest.mark.parametrize("N,d,m", [(1, 1, 1), (65, 3, 1), (700, 8, 4), (2500, 16, 4),
                                    (1029, 20, 16), (513, 32, 2), (300, 5, 9)])
 def test_float_float_product(K, kern, N, d, m):
