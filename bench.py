@@ -153,7 +153,8 @@ class ClockSampler:
 # default workload, keyed by (path, kernel, N, d, m, autotuned column splits).
 # Any other shape or tile has no capture and reports None; a change to the
 # kernel invalidates the entry until it is captured again.
-KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768}
+KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768,
+                 ("tensor", 0, 100_000, 16, 4, 50): 8_515_584 + 21_109_333}
 
 
 def kmv32_traffic(path, w, splits):
