@@ -563,7 +563,8 @@ static krr_status serve_launch_product(const ServeTable *T, const ServeTable *Th
     const int items = C.off[C.nslots];
     cudaStream_t bs = B.side[c % nb];
     cudaError_t e = cudaErrorInvalidValue;
-    if (d0.kern == KGAUSS) e = serve_launch_product_gauss(d0.dp, d0.M, items, T, c, bs);
+    if (d0.kc > 0) e = serve_launch_product_tc(d0.kern, d0.kc, d0.M, items, T, c, bs);
+    else if (d0.kern == KGAUSS) e = serve_launch_product_gauss(d0.dp, d0.M, items, T, c, bs);
     else if (d0.kern == KLAPLACE) e = serve_launch_product_laplace(d0.dp, d0.M, items, T, c, bs);
     else if (d0.kern == KMATERN) e = serve_launch_product_matern(d0.dp, d0.M, items, T, c, bs);
     count_launch();
@@ -647,8 +648,9 @@ double serve_footprint(int64_t N, int d, int m, int k) {
   // build: X, the float64 factor and its scratch, float32 factor, core
   b += n * d * 8 + n * k * 8 + n * k * 4 + n * 8 + k * 8.0;
   b += 2.0 * n * B * 8 + (double)B * k * 8 + 3.0 * k * k * 8;
-  // prepared points (float32 and float-float)
-  b += n * dp * 4 + n * 4 + 2.0 * n * dpff * 4 + 2.0 * n * 4;
+  // prepared points (float32, half split of the tensor-core product, float-float)
+  b += n * dp * 4 + n * 4 + n * 64.0 * ((d + 15) / 16) + n * 4 + 2.0 * n * dpff * 4 +
+       2.0 * n * 4;
   // float64 blocks (y, x, r, M x) and float32 CG vectors
   b += 4.0 * n * m * 8 + 5.0 * n * m * 4;
   // product partials, preconditioner partials, reductions
@@ -864,18 +866,25 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
 
   ServeSlotDesc &D = sl->desc;
   const int M = serve_pad_m(m);
+  // inner products on the tensor cores where the tile code has a variant and
+  // the coordinates fit the half split
+  if (M <= 8 && product_path() == 0) KRR_TRY(prepare_points_tc(Xd, s, sl->P32));
+  const int kc = sl->P32.kc16;
   const int rank = sl->core ? sl->core->rank : 0;
   const int64_t chunk = serve_chunk(N);
-  const int rows = KMV_THREADS * kmv32_rows_per_thread(dp, M);
+  const int rows = kc > 0 ? kmvtc_rows_per_cta(kc, M) : KMV_THREADS * kmv32_rows_per_thread(dp, M);
   D.xt = sl->P32.xt.p;
   D.cn = sl->P32.cn.p;
+  D.xs = kc > 0 ? sl->P32.xs16.p : nullptr;
+  D.cs = kc > 0 ? sl->P32.cs16.p : nullptr;
+  D.kc = kc;
   D.N = N;
   D.chunk = chunk;
   D.m = m;
   D.M = M;
   D.dp = dp;
   D.kern = sl->kern;
-  D.variant = serve_variant(sl->kern, dp, M);
+  D.variant = kc > 0 ? serve_variant_tc(sl->kern, kc, M) : serve_variant(sl->kern, dp, M);
   D.row_tiles = (int)((N + rows - 1) / rows);
   D.splits = (int)((N + chunk - 1) / chunk);
   const double lambda = sl->mu * (double)N;
@@ -947,6 +956,8 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   rebind(sl->P32.xt, S->s_free);
   rebind(sl->P32.cn, S->s_free);
   rebind(sl->P32.mean, S->s_free);
+  rebind(sl->P32.xs16, S->s_free);
+  rebind(sl->P32.cs16, S->s_free);
   rebind(sl->Pff.xh, S->s_free);
   rebind(sl->Pff.xl, S->s_free);
   rebind(sl->Pff.ch, S->s_free);
@@ -1050,6 +1061,9 @@ static void release_device(krr_server *S, Slot *sl) {
   sl->P32.xt.release();
   sl->P32.cn.release();
   sl->P32.mean.release();
+  sl->P32.xs16.release();
+  sl->P32.cs16.release();
+  sl->P32.kc16 = 0;
   sl->Pff.xh.release();
   sl->Pff.xl.release();
   sl->Pff.ch.release();

@@ -62,6 +62,10 @@ struct ServeSlotDesc {
   // fused float32 product (A + lambda I) p
   const float *xt;   // N x dp prepared points
   const float *cn;   // N per-point constants
+  // tensor-core product (kc > 0): half-split points and their constants
+  const uint4 *xs;   // N x kc x 4 fragment groups
+  const float *cs;   // N
+  int kc;            // 16-coordinate blocks, 0 for the FMA product
   float *part;       // splits x M x N partial sums
   int64_t N;
   int64_t chunk;     // columns per split
@@ -88,7 +92,10 @@ struct ServeSlotDesc {
   ServeStatus *status;
 };
 
-constexpr int SERVE_NUM_VARIANTS = 60;  // 3 kernels x 4 DP classes x 5 M classes
+// FMA products: 3 kernels x 4 DP classes x 5 M classes; tensor-core products:
+// (Gaussian, Matern) x 1 or 2 coordinate blocks x M in 1, 2, 4, 8
+constexpr int SERVE_NUM_FMA_VARIANTS = 60;
+constexpr int SERVE_NUM_VARIANTS = SERVE_NUM_FMA_VARIANTS + 16;
 
 // The slots of one product variant: the product launch of that variant
 // covers their (row tile, split) items, item i of slot slot[j] being
@@ -135,6 +142,12 @@ __host__ __device__ inline int serve_variant(int kern, int dp, int M) {
   if (di < 0 || mi < 0 || kern < 0 || kern > 2) return -1;
   return (kern * 4 + di) * 5 + mi;
 }
+__host__ __device__ inline int serve_variant_tc(int kern, int kc, int M) {
+  const int ki = kern == KGAUSS ? 0 : kern == KMATERN ? 1 : -1;
+  const int mi = M == 1 ? 0 : M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : -1;
+  if (ki < 0 || mi < 0 || kc < 1 || kc > 2) return -1;
+  return SERVE_NUM_FMA_VARIANTS + (ki * 2 + kc - 1) * 4 + mi;
+}
 
 // Grouped product of class `cls` of the table at T (device pointer): one CTA
 // per item, `items` of them (serve_kmv_*.cu, one file per kernel function).
@@ -144,5 +157,9 @@ cudaError_t serve_launch_product_laplace(int dp, int M, int items, const ServeTa
                                          cudaStream_t s);
 cudaError_t serve_launch_product_matern(int dp, int M, int items, const ServeTable *T, int cls,
                                         cudaStream_t s);
+// Tensor-core variants (serve_kmv_tc.cu): kern KGAUSS or KMATERN, kc 1 or 2,
+// M 1, 2, 4 or 8.
+cudaError_t serve_launch_product_tc(int kern, int kc, int M, int items, const ServeTable *T,
+                                    int cls, cudaStream_t s);
 
 }  // namespace krr
