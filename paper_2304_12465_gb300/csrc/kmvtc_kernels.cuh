@@ -65,13 +65,13 @@ __device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)
 // xs : N x KC x 4 uint4, the split layout above (rows and columns: the same
 //      points)
 // cs : N             c_i
-// V  : m x ldv       right-hand sides, float32
-// part: splits x M x N partial products
+// V  : m x ldv       right-hand sides, float32 (m <= M)
+// part: partial products, column c of split s at part + s * split_stride + c N
 template <int KERN, int KC, int M, int R>
 __device__ __forceinline__ void
 kmvtc_tile(const uint4 *__restrict__ xs, const float *__restrict__ cs,
            const float *__restrict__ V, int64_t ldv, int64_t N, int m, int64_t chunk,
-           float *__restrict__ part, int64_t row_tile, int64_t split) {
+           float *__restrict__ part, int64_t split_stride, int64_t row_tile, int64_t split) {
   constexpr int ROWS = KTC_WARPS * 16 * R;
   constexpr int GX = KTC_TJ * KC * 4;             // uint4 per column tile
   constexpr int XPT = (GX + KTC_THREADS - 1) / KTC_THREADS;
@@ -214,7 +214,7 @@ kmvtc_tile(const uint4 *__restrict__ xs, const float *__restrict__ cs,
       a.y += __shfl_xor_sync(0xffffffffu, a.y, 2);
       acc[f][c] = a;
     }
-  float *out = part + split * M * N;
+  float *out = part + split * split_stride;
 #pragma unroll
   for (int f = 0; f < R; ++f) {
     const int64_t r0 = row_base + 16 * f + g, r1 = r0 + 8;

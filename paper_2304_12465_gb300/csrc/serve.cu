@@ -824,7 +824,7 @@ static void table_add(ServeTable *T, const ServeSlotDesc &d) {
   }
   ServeClass &C = T->cls[c];
   C.slot[C.nslots] = s;
-  C.off[C.nslots + 1] = C.off[C.nslots] + d.row_tiles * d.splits;
+  C.off[C.nslots + 1] = C.off[C.nslots] + d.row_tiles * d.splits * d.halves;
   C.nslots += 1;
   T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
   T->tt_off[s + 1] = T->tt_off[s] + d.nbt * ((d.rank + SERVE_TT_COLS - 1) / SERVE_TT_COLS);
@@ -868,11 +868,14 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   const int M = serve_pad_m(m);
   // inner products on the tensor cores where the tile code has a variant and
   // the coordinates fit the half split
-  if (M <= 8 && product_path() == 0) KRR_TRY(prepare_points_tc(Xd, s, sl->P32));
+  if (product_path() == 0) KRR_TRY(prepare_points_tc(Xd, s, sl->P32));
   const int kc = sl->P32.kc16;
   const int rank = sl->core ? sl->core->rank : 0;
   const int64_t chunk = serve_chunk(N);
-  const int rows = kc > 0 ? kmvtc_rows_per_cta(kc, M) : KMV_THREADS * kmv32_rows_per_thread(dp, M);
+  // a tensor-core M = 16 slot runs its product as two halves of 8 columns
+  const int rows = kc > 0 ? kmvtc_rows_per_cta(kc, M > 8 ? 8 : M)
+                          : KMV_THREADS * kmv32_rows_per_thread(dp, M);
+  D.halves = (kc > 0 && M > 8) ? 2 : 1;
   D.xt = sl->P32.xt.p;
   D.cn = sl->P32.cn.p;
   D.xs = kc > 0 ? sl->P32.xs16.p : nullptr;

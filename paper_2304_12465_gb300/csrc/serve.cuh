@@ -66,6 +66,7 @@ struct ServeSlotDesc {
   const uint4 *xs;   // N x kc x 4 fragment groups
   const float *cs;   // N
   int kc;            // 16-coordinate blocks, 0 for the FMA product
+  int halves;        // product items per (row tile, split): 2 for a tensor-core M = 16
   float *part;       // splits x M x N partial sums
   int64_t N;
   int64_t chunk;     // columns per split
@@ -93,9 +94,10 @@ struct ServeSlotDesc {
 };
 
 // FMA products: 3 kernels x 4 DP classes x 5 M classes; tensor-core products:
-// (Gaussian, Matern) x 1 or 2 coordinate blocks x M in 1, 2, 4, 8
+// (Gaussian, Matern) x 1 or 2 coordinate blocks x 5 M classes (M = 16 runs as
+// two halves of 8)
 constexpr int SERVE_NUM_FMA_VARIANTS = 60;
-constexpr int SERVE_NUM_VARIANTS = SERVE_NUM_FMA_VARIANTS + 16;
+constexpr int SERVE_NUM_VARIANTS = SERVE_NUM_FMA_VARIANTS + 20;
 
 // The slots of one product variant: the product launch of that variant
 // covers their (row tile, split) items, item i of slot slot[j] being
@@ -144,9 +146,9 @@ __host__ __device__ inline int serve_variant(int kern, int dp, int M) {
 }
 __host__ __device__ inline int serve_variant_tc(int kern, int kc, int M) {
   const int ki = kern == KGAUSS ? 0 : kern == KMATERN ? 1 : -1;
-  const int mi = M == 1 ? 0 : M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : -1;
+  const int mi = M == 1 ? 0 : M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : M == 16 ? 4 : -1;
   if (ki < 0 || mi < 0 || kc < 1 || kc > 2) return -1;
-  return SERVE_NUM_FMA_VARIANTS + (ki * 2 + kc - 1) * 4 + mi;
+  return SERVE_NUM_FMA_VARIANTS + (ki * 2 + kc - 1) * 5 + mi;
 }
 
 // Grouped product of class `cls` of the table at T (device pointer): one CTA
@@ -158,7 +160,7 @@ cudaError_t serve_launch_product_laplace(int dp, int M, int items, const ServeTa
 cudaError_t serve_launch_product_matern(int dp, int M, int items, const ServeTable *T, int cls,
                                         cudaStream_t s);
 // Tensor-core variants (serve_kmv_tc.cu): kern KGAUSS or KMATERN, kc 1 or 2,
-// M 1, 2, 4 or 8.
+// M 1, 2, 4, 8 or 16 (items: row tiles x splits, twice for M = 16).
 cudaError_t serve_launch_product_tc(int kern, int kc, int M, int items, const ServeTable *T,
                                     int cls, cudaStream_t s);
 

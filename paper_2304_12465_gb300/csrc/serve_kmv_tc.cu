@@ -7,6 +7,9 @@
 
 namespace krr {
 
+// A slot with m > 8 (M = 16) runs as two halves of 8 right-hand sides: item
+// h * (row_tiles * splits) + r of the slot covers columns 8h .. 8h + 7 of its
+// p, writing them into the slot's 16-column partial layout.
 template <int KERN, int KC, int M>
 __global__ void __launch_bounds__(KTC_THREADS, 1)
 serve_product_tc_kernel(const ServeTable *__restrict__ T, int cls) {
@@ -17,8 +20,12 @@ serve_product_tc_kernel(const ServeTable *__restrict__ T, int cls) {
   const ServeSlotDesc &d = T->slot[C.slot[j]];
   if (!d.sc->live) return;
   const int local = item - C.off[j];
-  kmvtc_tile<KERN, KC, M, kmvtc_frags(KC, M)>(d.xs, d.cs, d.p, d.N, d.N, d.m, d.chunk, d.part,
-                                              local % d.row_tiles, local / d.row_tiles);
+  const int per_half = d.row_tiles * d.splits;
+  const int h = local / per_half, rem = local - h * per_half;
+  const int mh = d.m - 8 * h < M ? d.m - 8 * h : M;
+  kmvtc_tile<KERN, KC, M, kmvtc_frags(KC, M)>(
+      d.xs, d.cs, d.p + (int64_t)8 * h * d.N, d.N, d.N, mh, d.chunk,
+      d.part + (int64_t)8 * h * d.N, (int64_t)d.M * d.N, rem % d.row_tiles, rem / d.row_tiles);
 }
 
 template <int KERN, int KC>
@@ -30,6 +37,9 @@ static cudaError_t launch_m(int M, int items, const ServeTable *T, int cls, cuda
     break;
     KRR_CASE(1) KRR_CASE(2) KRR_CASE(4) KRR_CASE(8)
 #undef KRR_CASE
+    case 16:   // two halves of 8 right-hand sides
+      serve_product_tc_kernel<KERN, KC, 8><<<items, KTC_THREADS, 0, s>>>(T, cls);
+      break;
     default:
       return cudaErrorInvalidValue;
   }
