@@ -114,7 +114,9 @@ typedef struct {
 /*   Y = (A + lambda I) V,  A_ij = kappa(x_i, x_j), never stored.            */
 /* precision KRR_PREC_FP64 evaluates in float64 with direct differences;     */
 /* KRR_PREC_MIXED evaluates kernel tiles in float32 (distances from row      */
-/* norms of centred points) and accumulates in float32;                      */
+/* norms of centred points) and accumulates in float32 -- for the Gaussian   */
+/* and Matern kernels by default with the inner products on the tensor cores */
+/* (see krr_set_product_path), prepared once per call (synchronises stream);  */
 /* KRR_PREC_FLOAT_FLOAT evaluates entries and sums in float-float arithmetic */
 /* (error-free transformations on the float32 pipes, ~2^-46 per entry).     */
 /* V, Y: N x m column-major float64.  Y may not alias V.                     */
@@ -525,9 +527,10 @@ KRR_API krr_status krr_server_import(krr_server *S, const void *buf, size_t size
 KRR_API void krr_server_destroy(krr_server *S);
 
 /* Autotuning of the float32 fused product (not in the paper).  While on     */
-/* (non-zero), the first float32 product of each (kernel, d rounded up to 4,  */
-/* m rounded up to 1/2/4/8/16, N) times candidate column tiles -- the split   */
-/* counts that make the grid 2, 4, 8, 16 and 32 waves of two CTAs per SM --   */
+/* (non-zero), the first float32 product of each (path, kernel, d rounded up  */
+/* to 4 -- or to 16 on the tensor path --, m rounded up to 1/2/4/8/16, N)     */
+/* times candidate column tiles -- the split counts that make the grid 2, 4,  */
+/* 8, 16 and 32 waves of the path's CTAs per SM --                            */
 /* once on the caller's stream (it synchronises that stream; a stream that is */
 /* being captured is not tuned) and keeps the fastest for the process.  Off   */
 /* (the default): 8 waves.  The split count sets the summation order, so a    */
