@@ -172,35 +172,57 @@ def measured_peak(key, fallback):
 
 
 def product_roofline(path, w, per_launch_ms, splits, sm_max):
-    """Roofline of the float32 product.  Tensor path: the three fp16 MMAs per
-    16 coordinates (2 x 16 x 3 flop per entry and block) against the dense
-    16-bit tensor peak; FMA path: (2d + 1 + 2m) flop per entry against the FP32
-    FMA peak at the maximum SM clock."""
+    """Roofline of the float32 product: its roofline time is the largest of the
+    ideal times of the pipes it uses (FP32 ops, MUFU ops, tensor ops, each at
+    its peak) and frac = that time / the measured launch time.
+
+    FMA path, per entry: (2d + 1 + 2m) flop on the FP32 pipe (d FMA distance,
+    c_i + c_j, m FMA) and 1 ex2 (Matern 2).  Tensor path: 96 flop per 16
+    coordinates on the tensor cores (three fp16 MMAs), 1 + 2m flop on the FP32
+    pipe (c_i + c_j, m FMA) and the same MUFU work.  FP32 peak: 152 SM x 128
+    lanes x 2 flop x the maximum SM clock; MUFU: 32 ex2 per clock per SM (the
+    measured rate); tensor: the measured dense 16-bit peak, sustained."""
     entries = float(w.N) * w.N
     sec = per_launch_ms / 1e3
     traffic = kmv32_traffic(path, w, splits)
-    if path == "tensor" and w.kernel != 1:
-        blocks = (w.d + 15) // 16
-        flop_per_entry = 2 * 16 * 3 * blocks
-        peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
-        achieved = flop_per_entry * entries / sec / 1e12
-        mufu = 1 if w.kernel == 0 else 2
-        return {"kernel": "kmvtc_kernel (tensor-core product, fp16 two-half split)",
-                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_basis": f"dense 16-bit tensor peak, {basis} (bf16 cuBLAS, sustained; "
-                              "fp16 has the same nominal rate)",
-                "flop_per_entry": flop_per_entry, "entries_per_launch": entries,
-                "other_pipes_per_entry": {"ex2": mufu, "fp32_lane_ops": 2 + 2 * w.m}}
-    flop_per_entry = 2 * w.d + 1 + 2 * w.m          # dot (d FMA) + c_i + c_j + m FMA
-    achieved = flop_per_entry * entries / sec / 1e12
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA units x clock
-    return {"kernel": "kmv32_kernel (fused float32 product)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic,
-            "peak_basis": f"152 SM x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                          "(max SM clock); derived, not measured",
-            "flop_per_entry": flop_per_entry, "entries_per_launch": entries}
+    mufu_per_entry = 2 if w.kernel == 2 else 1
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s
+    mufu_peak = 152 * 32 * sm_max * 1e6 / 1e12                # T ex2/s
+    tensor_path = path == "tensor" and w.kernel != 1
+    if tensor_path:
+        tc_flop = 2 * 16 * 3 * ((w.d + 15) // 16)
+        fp32_flop = 1 + 2 * w.m
+        tc_peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
+        kernel = "kmvtc_kernel (tensor-core product, fp16 two-half split)"
+    else:
+        tc_flop = 0
+        fp32_flop = 2 * w.d + 1 + 2 * w.m
+        tc_peak, basis = None, None
+        kernel = "kmv32_kernel (fused float32 product)"
+    pipes = {"fp32": {"ideal_ms": fp32_flop * entries / fp32_peak / 1e9,
+                      "achieved": fp32_flop * entries / sec / 1e12, "peak": fp32_peak,
+                      "unit": "TFLOP/s", "per_entry": fp32_flop},
+             "mufu": {"ideal_ms": mufu_per_entry * entries / mufu_peak / 1e9,
+                      "achieved": mufu_per_entry * entries / sec / 1e12, "peak": mufu_peak,
+                      "unit": "T ex2/s", "per_entry": mufu_per_entry}}
+    if tensor_path:
+        pipes["tensor"] = {"ideal_ms": tc_flop * entries / tc_peak / 1e9,
+                           "achieved": tc_flop * entries / sec / 1e12, "peak": tc_peak,
+                           "unit": "TFLOP/s", "per_entry": tc_flop,
+                           "peak_basis": f"dense 16-bit tensor peak, {basis} (bf16 cuBLAS, "
+                                         "sustained; fp16 has the same nominal rate)"}
+    for p in pipes.values():
+        p["frac"] = p["achieved"] / p["peak"]
+    top = max(pipes, key=lambda k: pipes[k]["ideal_ms"])
+    t = pipes[top]
+    return {"kernel": kernel, "bound": "tensor" if top == "tensor" else "alu", "pipe": top,
+            "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
+            "frac": t["ideal_ms"] / per_launch_ms, "traffic": traffic,
+            "peak_basis": t.get("peak_basis",
+                                f"152 SM x {'128 FP32 lanes x 2 flop' if top == 'fp32' else '32 ex2'}"
+                                f" x {sm_max:.0f} MHz (max SM clock); derived from unit counts"),
+            "roofline_ms": t["ideal_ms"], "measured_ms": per_launch_ms,
+            "entries_per_launch": entries, "pipes": pipes}
 
 
 def entries_rpcholesky(N, k):
