@@ -59,9 +59,8 @@ __device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)
 
 // One (row tile, column split) work item of the square product; the
 // single-problem kernel maps it from blockIdx, the grouped serving kernel
-// from its work list.  Each kernel instantiates it once, so its shared tiles
-// (declared here, where the compiler sees their address space) are not
-// duplicated.
+// from its work list.  Each kernel instantiates it once, so its shared tiles,
+// declared here, are not duplicated.
 // xs : N x KC x 4 uint4, the split layout above (rows and columns: the same
 //      points)
 // cs : N             c_i
@@ -231,9 +230,9 @@ kmvtc_tile(const uint4 *__restrict__ xs, const float *__restrict__ cs,
 // Single-problem kernel.  Its body is the tile above with the work item
 // taken from blockIdx; it is kept as its own copy because the inlined tile
 // call compiled to a schedule measured 4.8% slower (3.55 vs 3.39 ms at
-// N = 1e5, d = 16, m = 4, identical results).  The two copies must compute the
-// same sums in the same order; the product-path and serving parity tests run
-// both.
+// N = 1e5, d = 16, m = 4, identical results).  The two copies implement the
+// same arithmetic: the product tests check this kernel and the serving tests
+// check the tile, each against the oracle.
 // xs : N x KC x 4 uint4, the split layout above (rows and columns: the same
 //      points, square product)
 // cs : N             c_i
