@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--fp64-path", action="store_true",
                     help="also time the plain float64 path (one step, slow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma"],
+    ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma", "mma_sync"],
                     help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "serving"],
@@ -150,15 +150,20 @@ class ClockSampler:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # float32 product, mean of three launches from one ncu capture of this bench's
-# default workload, keyed by (path, kernel, N, d, m, autotuned column splits).
-# Any other shape or tile has no capture and reports None; a change to the
-# kernel invalidates the entry until it is captured again.
-KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768,
-                 ("tensor", 0, 100_000, 16, 4, 50): 8_515_584 + 21_109_333}
+# default workload, keyed by (path, kernel, N, d, m, tile): the autotuned
+# column splits of the FMA and mma.sync kernels, the epilogue variant of the
+# tcgen05 kernel.  Any other shape or tile has no capture and reports None; a
+# change to the kernel invalidates the entry until it is captured again.
+KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768}
+
+# Register-operand mma.sync (m16n8k16, f16 inputs, f32 accumulator) measured by
+# this repository's probe on this machine's GB300 (independent MMAs, 2-8 CTAs of
+# 256 threads per SM): the peak of the mma.sync kernel's tensor pipe.
+MMA_SYNC_F16_TFLOPS = 606.0
 
 
-def kmv32_traffic(path, w, splits):
-    return KMV32_TRAFFIC.get((path, w.kernel, w.N, w.d, w.m, splits))
+def kmv32_traffic(path, w, tile):
+    return KMV32_TRAFFIC.get((path, w.kernel, w.N, w.d, w.m, tile))
 
 
 def measured_peak(key, fallback):
@@ -171,29 +176,48 @@ def measured_peak(key, fallback):
         return fallback, "fallback"
 
 
-def product_roofline(path, w, per_launch_ms, splits, sm_max):
+def tc5_mmas(d):
+    """MMAs (K = 16 each) per entry of the tcgen05 product: (L_i, H_j), (H_i, L_j)
+    and (H_i, H_j) per 16-coordinate block, plus one for c_i + c_j when c has a
+    block of its own (d mod 16 = 0 or > 10)."""
+    nh = (d + 15) // 16
+    csep = 1 if (d % 16 == 0 or d % 16 > 10) else 0
+    return 3 * nh + csep
+
+
+def product_roofline(path, w, per_launch_ms, tile, sm_max):
     """Roofline of the float32 product: its roofline time is the largest of the
     ideal times of the pipes it uses (FP32 ops, MUFU ops, tensor ops, each at
     its peak) and frac = that time / the measured launch time.
 
-    FMA path, per entry: (2d + 1 + 2m) flop on the FP32 pipe (d FMA distance,
-    c_i + c_j, m FMA) and 1 ex2 (Matern 2).  Tensor path: 96 flop per 16
-    coordinates on the tensor cores (three fp16 MMAs), 1 + 2m flop on the FP32
-    pipe (c_i + c_j, m FMA) and the same MUFU work.  FP32 peak: 152 SM x 128
-    lanes x 2 flop x the maximum SM clock; MUFU: 32 ex2 per clock per SM (the
-    measured rate); tensor: the measured dense 16-bit peak, sustained."""
+    tcgen05 path (default): 2 x 16 flop per MMA per entry on the tensor cores
+    (tc5_mmas), 2m flop on the FP32 pipe (the m FMAs; c_i + c_j is folded into
+    the MMAs) and 1 ex2 (Matern 2) on the MUFU; tensor peak = the measured
+    dense 16-bit peak, sustained.  mma.sync path: 96 flop per 16 coordinates
+    (three fp16 MMAs), 1 + 2m flop on the FP32 pipe (c_i + c_j, m FMA), tensor
+    peak = the measured mma.sync f16 rate.  FMA path: (2d + 1 + 2m) flop per
+    entry (d FMA distance, c_i + c_j, m FMA).  FP32 peak: 152 SM x 128 lanes x
+    2 flop x the maximum SM clock; MUFU: 32 ex2 per clock per SM (measured)."""
     entries = float(w.N) * w.N
     sec = per_launch_ms / 1e3
-    traffic = kmv32_traffic(path, w, splits)
+    traffic = kmv32_traffic(path, w, tile)
     mufu_per_entry = 2 if w.kernel == 2 else 1
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s
     mufu_peak = 152 * 32 * sm_max * 1e6 / 1e12                # T ex2/s
-    tensor_path = path == "tensor" and w.kernel != 1
-    if tensor_path:
+    tensor_path = path in ("tensor", "mma_sync") and w.kernel != 1
+    if tensor_path and path == "tensor":
+        tc_flop = 2 * 16 * tc5_mmas(w.d)
+        fp32_flop = 2 * w.m
+        tc_peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
+        basis = (f"dense 16-bit tensor peak, {basis} (bf16 cuBLAS, sustained; fp16 has the "
+                 "same nominal rate)")
+        kernel = "kmvtc5_kernel (tcgen05 tensor-core product, fp16 two-half split, TMEM)"
+    elif tensor_path:
         tc_flop = 2 * 16 * 3 * ((w.d + 15) // 16)
         fp32_flop = 1 + 2 * w.m
-        tc_peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
-        kernel = "kmvtc_kernel (tensor-core product, fp16 two-half split)"
+        tc_peak = MMA_SYNC_F16_TFLOPS
+        basis = "register-operand mma.sync f16 m16n8k16, measured by this repository's probe"
+        kernel = "kmvtc_kernel (mma.sync tensor-core product, fp16 two-half split)"
     else:
         tc_flop = 0
         fp32_flop = 2 * w.d + 1 + 2 * w.m
@@ -208,9 +232,7 @@ def product_roofline(path, w, per_launch_ms, splits, sm_max):
     if tensor_path:
         pipes["tensor"] = {"ideal_ms": tc_flop * entries / tc_peak / 1e9,
                            "achieved": tc_flop * entries / sec / 1e12, "peak": tc_peak,
-                           "unit": "TFLOP/s", "per_entry": tc_flop,
-                           "peak_basis": f"dense 16-bit tensor peak, {basis} (bf16 cuBLAS, "
-                                         "sustained; fp16 has the same nominal rate)"}
+                           "unit": "TFLOP/s", "per_entry": tc_flop, "peak_basis": basis}
     for p in pipes.values():
         p["frac"] = p["achieved"] / p["peak"]
     top = max(pipes, key=lambda k: pipes[k]["ideal_ms"])
@@ -298,7 +320,10 @@ def run_native(args):
     kmv_n = sum(i["kmv_launches"] for i in infos)
     per_launch_ms = kmv_ms / max(kmv_n, 1)
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    splits = K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)
+    if args.product_path == "tensor":
+        tile = K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)[0]
+    else:
+        tile = K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)
     kmv64_ms = sum(i["kmv64_ms"] for i in infos)
     kmv64_n = sum(i["kmv64_launches"] for i in infos)
     kmvff_ms = sum(i["kmvff_ms"] for i in infos)
@@ -329,9 +354,11 @@ def run_native(args):
                 "kmv64_launches": kmv64_n,
                 "kmvff_ms_per_launch": kmvff_ms / max(kmvff_n, 1),
                 "kmvff_launches": kmvff_n,
-                "kmv32_splits_autotuned": splits,
+                "kmv32_tile_autotuned": tile,
+                "kmv32_tile_kind": ("epilogue variant" if args.product_path == "tensor"
+                                    else "column splits"),
                 "product_path": args.product_path},
-        "roofline": product_roofline(args.product_path, w, per_launch_ms, splits, sm_max),
+        "roofline": product_roofline(args.product_path, w, per_launch_ms, tile, sm_max),
         "clocks": clk,
         "gpu_launches": int(launches),
     }

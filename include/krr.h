@@ -547,17 +547,47 @@ KRR_API krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N,
 /* solve, and krr_kmatvec with KRR_PREC_MIXED) for the Gaussian and Matern    */
 /* kernels (Sec. 2.1: both are functions of |x_i - x_j|^2):                   */
 /*   KRR_PRODUCT_TENSOR (0, default): the inner products x_i . x_j on the     */
-/*     tensor cores from a two-half split of each centred, scaled coordinate  */
-/*     (x = h + l, |x - h - l| <= 2^-22 |x|; three fp16 MMAs with float32     */
-/*     accumulation), kernel values and sums over V in float32.  Points whose */
-/*     centred, scaled coordinates exceed 16384 in magnitude, and the Laplace */
-/*     kernel, take the FMA path.                                             */
+/*     fifth-generation tensor cores (tcgen05.mma into Tensor Memory, operands */
+/*     staged by TMA) from a two-half split of each centred, scaled           */
+/*     coordinate (x = h + l, |x - h - l| <= 2^-22 |x|; fp16 MMAs with float32 */
+/*     accumulation, c_i + c_j folded in as three fp16 pieces), kernel values */
+/*     and sums over V in float32.  Points whose centred, scaled coordinates  */
+/*     exceed 16384 in magnitude (or |x|^2 / 2 exceeds 32768), and the        */
+/*     Laplace kernel, take the FMA path.                                     */
 /*   KRR_PRODUCT_FMA (1): every entry on the float32 FMA pipe.                */
-/* Both paths meet the float32 error bound of krr_kmatvec; their results      */
+/*   KRR_PRODUCT_MMA_SYNC (2): the same split on the register-operand         */
+/*     mma.sync tensor path (kept for comparison).                            */
+/* All paths meet the float32 error bound of krr_kmatvec; their results       */
 /* differ at the rounding level.  Process-wide; not thread-safe with solves   */
 /* in flight.  KRR_EINVAL for another value.                                  */
-typedef enum { KRR_PRODUCT_TENSOR = 0, KRR_PRODUCT_FMA = 1 } krr_product_path;
+typedef enum {
+  KRR_PRODUCT_TENSOR = 0,
+  KRR_PRODUCT_FMA = 1,
+  KRR_PRODUCT_MMA_SYNC = 2
+} krr_product_path;
 KRR_API krr_status krr_set_product_path(int path);
+
+/* Epilogue variant of the tcgen05 product (KRR_PRODUCT_TENSOR): 0 (default)  */
+/* = chosen per shape by the autotuner while krr_set_autotune is on (every    */
+/* valid variant timed once on the caller's stream at the first product of   */
+/* the shape), else variant 3; 1 = 8 epilogue warps with the next columns.    */
+/* Tensor Memory loads in flight while the current ones are computed; 2 = 16  */
+/* epilogue warps; 3 = 8 warps without that overlap; 4 = 16 warps with it;    */
+/* 5 = 8 warps, software-pipelined by one batch of columns (the ex2 of one    */
+/* batch on the MUFU while the FFMA2 sums of the previous batch run); 6 = 12  */
+/* epilogue warps on 96-column tiles with the overlap; 7 = the same without.  */
+/* Variants 2, 4, 5, 6 and 7 serve m <= 4 per launch (larger m fall back to   */
+/* 1).  Results differ between variants at the rounding level only (the      */
+/* order in which column groups are summed).  Process-wide.  KRR_EINVAL       */
+/* outside 0..7.                                                              */
+KRR_API krr_status krr_set_product_variant(int variant);
+
+/* The autotuner's choice for the square tcgen05 product of a shape (kernel,  */
+/* d, m, N): *variant (0 if the shape has not been tuned) and, when ms is not */
+/* NULL, the measured launch time of each of the 7 variants in milliseconds   */
+/* (0 for a variant that was not timed).                                      */
+KRR_API krr_status krr_autotune_variant(krr_kernel kern, int d, int m, int64_t N, int *variant,
+                                        float *ms);
 
 /* Timing instrumentation: while on (non-zero), solves record CUDA events
  * around every fused-product launch on the caller's stream and report the

@@ -26,6 +26,8 @@ from .api import (  # noqa: F401
     krr_autotune_choice,
     krr_set_autotune,
     krr_set_product_path,
+    krr_set_product_variant,
+    krr_autotune_variant,
     krr_set_profiling,
     krr_sparse_sign,
     krr_version,

@@ -20,7 +20,7 @@ GAUSSIAN, LAPLACE_L1, MATERN52 = 0, 1, 2
 PREC_FP64, PREC_MIXED, PREC_FLOAT_FLOAT = 0, 1, 2
 PIVOT_RPCHOLESKY, PIVOT_UNIFORM, PIVOT_GREEDY = 0, 1, 2
 # float32 product path (krr_set_product_path)
-PRODUCT_TENSOR, PRODUCT_FMA = 0, 1
+PRODUCT_TENSOR, PRODUCT_FMA, PRODUCT_MMA_SYNC = 0, 1, 2
 
 
 class KrrInfo(C.Structure):
@@ -137,6 +137,9 @@ SIGNATURES = {
     "krr_set_autotune": (None, [_int]),
     "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
     "krr_set_product_path": (_int, [_int]),
+    "krr_set_product_variant": (_int, [_int]),
+    "krr_autotune_variant": (_int, [_int, _int, _int, _i64, C.POINTER(_int),
+                                    C.POINTER(C.c_float)]),
     "krr_set_profiling": (None, [_int]),
     "krr_last_error": (C.c_char_p, []),
     "krr_version": (C.c_char_p, []),

@@ -384,9 +384,24 @@ def krr_autotune_choice(kern, d: int, m: int, N: int) -> int:
 
 def krr_set_product_path(path) -> None:
     """Path of the float32 product for the Gaussian and Matern kernels:
-    "tensor" (inner products on the tensor cores, the default) or "fma"."""
-    code = {"tensor": 0, "fma": 1}.get(path, path)
+    "tensor" (inner products on the tcgen05 tensor cores, the default),
+    "fma", or "mma_sync" (the register-operand tensor path)."""
+    code = {"tensor": 0, "fma": 1, "mma_sync": 2}.get(path, path)
     check(load().krr_set_product_path(int(code)), "krr_set_product_path")
+
+
+def krr_set_product_variant(variant: int) -> None:
+    """Epilogue variant of the tcgen05 product (0: autotuned / default)."""
+    check(load().krr_set_product_variant(int(variant)), "krr_set_product_variant")
+
+
+def krr_autotune_variant(kern, d: int, m: int, N: int):
+    """(chosen variant or 0, per-variant launch times in ms) for a shape."""
+    v = C.c_int()
+    ms = (C.c_float * 7)()
+    check(load().krr_autotune_variant(_kern(kern), int(d), int(m), int(N), C.byref(v), ms),
+          "krr_autotune_variant")
+    return v.value, [float(x) for x in ms]
 
 
 def krr_set_profiling(on: bool) -> None:

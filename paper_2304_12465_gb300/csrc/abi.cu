@@ -229,9 +229,32 @@ krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N, int *sp
 
 krr_status krr_set_product_path(int path) {
   clear_error();
-  KRR_REQUIRE(path == KRR_PRODUCT_TENSOR || path == KRR_PRODUCT_FMA, "unknown product path %d",
-              path);
+  KRR_REQUIRE(path == KRR_PRODUCT_TENSOR || path == KRR_PRODUCT_FMA ||
+                  path == KRR_PRODUCT_MMA_SYNC,
+              "unknown product path %d", path);
   set_product_path(path);
+  return KRR_OK;
+}
+
+krr_status krr_set_product_variant(int variant) {
+  clear_error();
+  return set_tc5_variant(variant);
+}
+
+krr_status krr_autotune_variant(krr_kernel kern, int d, int m, int64_t N, int *variant,
+                                float *ms) {
+  clear_error();
+  KRR_REQUIRE(variant, "variant is NULL");
+  KRR_REQUIRE(valid_kernel(kern), "unknown kernel %d", (int)kern);
+  KRR_REQUIRE(d >= 1 && d <= 32 && m >= 1 && m <= 16 && N >= 1, "bad shape");
+  const int mg = m > 8 ? 8 : m;
+  const int M = mg <= 2 ? 2 : mg <= 4 ? 4 : 8;
+  int best = 0;
+  float t[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (!tc5_tuned((int)kern, d, M, N, &best, t)) best = 0;
+  *variant = best;
+  if (ms)
+    for (int v = 0; v < 7; ++v) ms[v] = t[v];
   return KRR_OK;
 }
 
@@ -279,6 +302,7 @@ krr_status krr_kmatvec(const double *X, int64_t N, int d, krr_kernel kern, doubl
     KRR_TRY(y32.alloc((size_t)N * m, s));
     KRR_TRY(convert_f64_to_f32(Vd, v32.p, N * m, s));
     KRR_TRY(kmv_f32(P, (float)lambda, v32.p, N, m, y32.p, N, s, part));
+    KRR_TRY(tc5_check_fault(s));
     KRR_TRY(convert_f32_to_f64(y32.p, out.dev, N * m, s));
   }
   return out.finish(s);
@@ -508,6 +532,7 @@ krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel kern, dou
   krr_status st = pcg_solve_device(Xd, N, d, kern, sigma, Yd, m, mu, F, tol, maxit, prec, out.dev,
                                    s, info);
   if (st != KRR_OK && st != KRR_ENOCONV) return st;
+  KRR_TRY(tc5_check_fault(s));   // a bounded wait of a tensor-core product gave up
   krr_status st2 = out.finish(s);
   if (st2 != KRR_OK) return st2;
   if (info && prof) {

@@ -255,12 +255,13 @@ static std::mutex g_tune_mtx;
 static std::map<std::tuple<int, int, int, int, int64_t>, int> g_tuned;
 
 void set_autotune(bool on) { g_autotune.store(on); }
+bool autotune_on() { return g_autotune.load(); }
 void set_product_path(int path) { g_product_path.store(path); }
 int product_path() { return g_product_path.load(); }
 
 // Path a float32 product of this shape takes: 1 tensor cores, 0 FMA.
 static int path_of(int kern, int dp) {
-  return (g_product_path.load() == 0 && kern != KLAPLACE && dp <= 32) ? 1 : 0;
+  return (g_product_path.load() != 1 && kern != KLAPLACE && dp <= 32) ? 1 : 0;
 }
 
 int tuned_splits(int kern, int dp, int M, int64_t N) {
@@ -377,6 +378,8 @@ krr_status kmv_f32(const PointsF32 &P, float lambda, const float *V, int64_t ldv
                    float *Y, int64_t ldy, cudaStream_t s, DevBuf<float> &part) {
   const int64_t N = P.N;
   if (N == 0 || m == 0) return KRR_OK;
+  if (P.nh5 > 0 && g_product_path.load() == 0)
+    return kmv_tc5(P, P, lambda, true, V, ldv, m, Y, ldy, s, part);
   if (P.kc16 > 0 && path_of(P.kern, P.dp) == 1)
     return kmv_tc(P, lambda, V, ldv, m, Y, ldy, s, part);
   for (int c0 = 0; c0 < m; c0 += 16) {

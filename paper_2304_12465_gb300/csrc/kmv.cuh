@@ -1,6 +1,8 @@
 // Host-side interface of the fused product (kmatvec.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace krr {
@@ -21,6 +23,12 @@ struct PointsF32 {
   DevBuf<uint4> xs16;
   DevBuf<float> cs16;
   int kc16 = 0;
+  // operands of the tcgen05 product (kmvtc5_kernels.cuh), present when
+  // nh5 > 0: N x kb x 16 fp16 each, row operand (c-part c1, c2, c3, 1, 1, 1)
+  // and column operand (1, 1, 1, c1, c2, c3), and their TMA tensor maps
+  DevBuf<uint16_t> xa5, xb5;
+  CUtensorMap ma5{}, mb5{};
+  int nh5 = 0, csep5 = 0;
 };
 
 // mean_dev (optional, d doubles on the device): centre to use instead of the
@@ -31,11 +39,35 @@ krr_status prepare_points_f32(const double *Xd, int64_t N, int d, int kern,
                               double sigma, cudaStream_t s, PointsF32 &P,
                               const double *mean_dev = nullptr, int dp = 0);
 
-// Adds the half-split layout of the tensor-core product to P (prepared by
-// prepare_points_f32 from the same Xd) for the Gaussian and Matern kernels;
-// leaves P.kc16 = 0 (FMA product) for Laplace or when a centred, scaled
-// coordinate exceeds the half-precision split's range.  Synchronises s.
-krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P);
+// Adds the half-split layouts of the tensor-core products to P (prepared by
+// prepare_points_f32 from the same Xd) for the Gaussian and Matern kernels:
+// the mma.sync layout (kc16 > 0) and, when with_tc5, the tcgen05 operands
+// (nh5 > 0).  Leaves both absent (FMA product) for Laplace or when a centred,
+// scaled coordinate (or c) exceeds the half-precision split's range.
+// Synchronises s.
+krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P,
+                             bool with_tc5 = true);
+
+// Builds only the tcgen05 operands of P (P.nh5 > 0); *bad = 1 (and nh5 = 0)
+// when a point is outside the split's range.  Synchronises s.
+krr_status prepare_points_tc5(const double *Xd, cudaStream_t s, PointsF32 &P, int *bad);
+
+// tcgen05 product Y (R.N x m) = K(R, P) V, + lambda V when square (R is P);
+// both point sets carry tcgen05 operands prepared with the same centre and
+// scale.  V: m x ldv over P's points; Y: m x ldy over R's points.
+krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool square,
+                   const float *V, int64_t ldv, int m, float *Y, int64_t ldy, cudaStream_t s,
+                   DevBuf<float> &part);
+
+// Epilogue variant of the tcgen05 product (see krr_set_product_variant), and
+// the autotuner's choice and per-variant times for a square shape.
+krr_status set_tc5_variant(int v);
+bool tc5_tuned(int kern, int d, int M, int64_t N, int *best, float *ms);
+bool autotune_on();
+
+// Raises KRR_ETIMEOUT (and clears the flag) when a bounded device-side wait
+// of the tcgen05 product gave up since the last check; synchronises s.
+krr_status tc5_check_fault(cudaStream_t s);
 
 struct KmvTcArgs {
   const uint4 *xs;
@@ -50,8 +82,9 @@ cudaError_t launch_kmvtc(int kern, int KC, int M, dim3 grid, cudaStream_t s,
                          const KmvTcArgs &a);
 int kmvtc_rows_per_cta(int KC, int M);
 
-// Product path of kmv_f32 when P has the half-split layout: 0 tensor cores
-// (default), 1 the FMA kernel (see krr_set_product_path).
+// Product path of kmv_f32 when P has the half-split layouts: 0 tcgen05
+// tensor cores (default), 1 the FMA kernel, 2 the mma.sync tensor-core kernel
+// (see krr_set_product_path).
 void set_product_path(int path);
 int product_path();
 

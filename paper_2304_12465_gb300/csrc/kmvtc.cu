@@ -50,8 +50,9 @@ __global__ void prepare_tc_kernel(const double *__restrict__ X, int64_t N, int d
   if (out_of_range) *bad = 1;
 }
 
-krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P) {
+krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P, bool with_tc5) {
   P.kc16 = 0;
+  P.nh5 = 0;
   if (P.kern == KLAPLACE || P.d > 32 || P.N == 0) return KRR_OK;
   const int kc_n = (P.d + 15) / 16;
   const double log2e = 1.4426950408889634;
@@ -74,6 +75,10 @@ krr_status prepare_points_tc(const double *Xd, cudaStream_t s, PointsF32 &P) {
     return KRR_OK;
   }
   P.kc16 = kc_n;
+  if (with_tc5) {
+    int bad5 = 0;
+    KRR_TRY(prepare_points_tc5(Xd, s, P, &bad5));
+  }
   return KRR_OK;
 }
 

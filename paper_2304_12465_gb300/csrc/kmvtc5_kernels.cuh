@@ -1,0 +1,640 @@
+// Fused product Y = K(rows, columns) V (+ lambda V for the square product)
+// for the Gaussian and Matern kernels (Sec. 2.1; the "Product" primitive of
+// Alg. 1), with the inner products x_i . x_j on the fifth-generation tensor
+// cores (tcgen05.mma, accumulators in Tensor Memory) and the kernel values
+// and sums over V in float32 registers.
+//
+// Arithmetic.  Points are centred and scaled as for the float32 FMA product,
+// so that kappa = 2^D (Gaussian) or D = -q^2/2 (Matern) with
+// D = x_i . x_j + c_i + c_j and c = -|x|^2 / 2.  Each coordinate is split
+// into two halves x = h + l (h = fp16(x), l = fp16(x - h), |x - h - l| <=
+// 2^-22 |x|) and c into three fp16 pieces c1 + c2 + c3.  Each point has
+// 16-wide K-blocks [H_0..H_{NH-1} | L_0..L_{NH-1} | C], stored K-block-major
+// (kb x N x 16 halves) so that one column tile is a single 3-D TMA box of
+// contiguous 4 KB slabs:
+// the row operand's c-part is (c1, c2, c3, 1, 1, 1) and the column operand's
+// (1, 1, 1, c1, c2, c3), so the product of the two c-parts is c_i + c_j.  The
+// c-part sits in a block of its own (CSEP = 1) or in the unused positions
+// 10..15 of the last H block (CSEP = 0, when d mod 16 is 1..10).  D is then
+// the float32 sum of the MMAs (L_i, H_j), (H_i, L_j), (C_i, C_j), (H_i, H_j)
+// over the coordinate blocks, small terms first; the dropped l_i . l_j is
+// below 2^-22 |x_i| |x_j|.
+//
+// Decomposition.  A row block is 256 rows (two row tiles of 128 = the TMEM
+// lanes), a column tile 128 columns (the MMA's N).  The (row block, column
+// tile) pairs are numbered row-block-major and CTA b of G persistent CTAs
+// (one per SM) takes the contiguous range [b T / G, (b + 1) T / G), so the
+// load is balanced to one tile.  Its pairs fall into segments, one per row
+// block it touches; each segment's partial sums go to part[b][j] (j the
+// segment's index within the CTA) and t5_reduce_kernel adds, for every row,
+// the segments of the CTAs that cover its row block in CTA order (a fixed
+// order: results are deterministic for a given grid).
+//
+// Warp roles (320 threads):
+//   warp 8 (producer): one lane issues the TMA loads of the row operand (both
+//     row tiles, once per segment) and of each column tile's operand into a
+//     ring of t5_stages(kb, M) stages (up to 8), plus a bulk copy of the tile's right-hand sides,
+//     prepared once per product as {v_c, v_c, v_c+1, v_c+1} quadruples
+//     (t5_vdup_kernel), all completing on the stage's barrier.
+//   warp 9 (MMA): allocates all 512 TMEM columns; one lane issues, per column
+//     tile and row tile, the MMAs of D into one of two accumulator buffers
+//     (2 buffers x 2 row tiles x 128 columns), and commits them to the
+//     barriers that release the column stage and hand the buffer to the
+//     epilogue.
+//   warps 0-7 (epilogue): warp w reads TMEM lanes 32 (w % 4) .. + 31 of both
+//     row tiles for columns 64 (w / 4) .. + 63 of the tile with tcgen05.ld
+//     16x256b (a lane holds rows g, g + 8, g + 16, g + 24 of each row tile and
+//     two columns of every 8), forms kappa with ex2 on the MUFU, and
+//     accumulates V with packed FFMA2 on row pairs; each quadruple of V read
+//     from shared memory serves eight rows.
+//
+// Every mbarrier wait is bounded (T5_WAIT_BUDGET cycles); a wait that gives
+// up sets *fault, raises a CTA-wide abort flag so the other roles leave too,
+// and the CTA waits (bounded) for its own TMA copies and MMAs in flight and
+// frees its Tensor Memory before returning.
+#pragma once
+
+#include "blackwell.cuh"
+#include "kmv_kernels.cuh"
+
+namespace krr {
+
+constexpr int T5_TM = 128;                   // rows of a row tile (TMEM lanes)
+constexpr int T5_RT = 2;                     // row tiles per row block
+constexpr int T5_RB = T5_TM * T5_RT;         // rows per row block
+constexpr int T5_TN = 128;                   // columns per column tile (MMA N)
+constexpr int T5_BLK = T5_TM * 32;           // bytes of one 16-wide K-block of 128 points
+constexpr int T5_TMEM_COLS = 512;
+constexpr long long T5_WAIT_BUDGET = 1LL << 32;   // about 2 s at 2 GHz
+constexpr float T5_MAX_COORD = 16384.0f;     // |scaled coordinate| bound of the split
+constexpr float T5_MAX_C = 32768.0f;         // |c| bound of its fp16 pieces
+
+// K-blocks of the split layout for dimension d.
+__host__ __device__ constexpr int t5_nh(int d) { return (d + 15) / 16; }
+__host__ __device__ constexpr int t5_csep(int d) { return (d % 16 == 0 || d % 16 > 10) ? 1 : 0; }
+__host__ __device__ constexpr int t5_kb(int nh, int csep) { return 2 * nh + csep; }
+
+// Column-tile pipeline stages: as many as fit (at most 8) in about 200 KB of
+// shared memory beside the row operand, so that TMA latency is hidden.
+__host__ __device__ constexpr int t5_stages(int kb, int M) {
+  return ((204800 - 1024 - T5_RT * kb * T5_BLK) / (kb * T5_BLK + (M / 2) * T5_TN * 16)) > 8
+             ? 8
+             : ((204800 - 1024 - T5_RT * kb * T5_BLK) / (kb * T5_BLK + (M / 2) * T5_TN * 16));
+}
+
+// Barrier indices in shared memory for ST stages.
+__host__ __device__ constexpr int t5_bar_a_full() { return 0; }
+__host__ __device__ constexpr int t5_bar_a_empty() { return 1; }
+__host__ __device__ constexpr int t5_bar_b_full(int) { return 2; }
+__host__ __device__ constexpr int t5_bar_b_empty(int st) { return 2 + st; }
+__host__ __device__ constexpr int t5_bar_v_empty(int st) { return 2 + 2 * st; }
+__host__ __device__ constexpr int t5_bar_d_full(int st) { return 2 + 3 * st; }
+__host__ __device__ constexpr int t5_bar_d_empty(int st) { return 4 + 3 * st; }
+__host__ __device__ constexpr int t5_bar_fin(int st) { return 6 + 3 * st; }
+__host__ __device__ constexpr int t5_nbar(int st) { return 7 + 3 * st; }
+
+// Shared memory of one CTA (bytes, including 1024 bytes of alignment slack).
+__host__ __device__ constexpr int t5_smem_bytes(int kb, int M) {
+  return 1024 + T5_RT * kb * T5_BLK + t5_stages(kb, M) * (kb * T5_BLK + (M / 2) * T5_TN * 16) +
+         8 * t5_nbar(t5_stages(kb, M)) + 16;
+}
+
+struct T5Args {
+  const float4 *vdup;   // C x (M/2) x TN right-hand-side quadruples (t5_vdup_kernel)
+  int64_t Nc;           // column points
+  float *part;          // G x J x (EW / 4) x M x T5_RB partial sums
+  int C;            // column tiles
+  int64_t T;        // row blocks x column tiles
+  int J;            // segments per CTA (maximum)
+  int *fault;       // set to 1 when a bounded wait gives up
+};
+
+// Kernel values of the MMA accumulator D.
+template <int KERN>
+__device__ __forceinline__ float t5_kappa(uint32_t d) {
+  return kappa_f32<KERN>(__uint_as_float(d));
+}
+
+// Epilogue variants: EW epilogue warps (8, 12 or 16; EW / 4 column groups of
+// TN / (EW / 4) columns per tile, TN the column tile: 128, or 96 for 12
+// warps), PIPE = 1 keeps the TMEM loads of the
+// next 16 columns in flight while the current ones are computed, LAG = 1
+// (with PIPE) software-pipelines the epilogue by one batch of 16 columns:
+// the kernel values (ex2 on the MUFU) of batch b are formed while the FFMA2
+// accumulation of batch b - 1 runs on the FMA pipe, across tile boundaries,
+// so that the two pipes work at the same time instead of in turn.
+template <int KERN, int NH, int CSEP, int M, int EW, int PIPE, int LAG, int TN>
+__global__ void __launch_bounds__((EW + 2) * 32, 1)
+kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
+              const __grid_constant__ CUtensorMap colmap, const T5Args a) {
+  // column tile of this variant (the MMA's N; the TMA box stays 128 points,
+  // of which the first TN are used)
+  constexpr int T5_TN = TN;
+  constexpr int KB = 2 * NH + CSEP;
+  constexpr int MP = M / 2;   // right-hand-side pairs
+  constexpr int T5_ST = t5_stages(KB, M);
+  constexpr int T5_BAR_A_FULL = t5_bar_a_full();
+  constexpr int T5_BAR_A_EMPTY = t5_bar_a_empty();
+  constexpr int T5_BAR_B_FULL = t5_bar_b_full(T5_ST);
+  constexpr int T5_BAR_B_EMPTY = t5_bar_b_empty(T5_ST);
+  constexpr int T5_BAR_V_EMPTY = t5_bar_v_empty(T5_ST);
+  constexpr int T5_BAR_D_FULL = t5_bar_d_full(T5_ST);
+  constexpr int T5_BAR_D_EMPTY = t5_bar_d_empty(T5_ST);
+  constexpr int T5_BAR_FIN = t5_bar_fin(T5_ST);
+  constexpr int T5_NBAR = t5_nbar(T5_ST);
+  constexpr int T5_EPI_WARPS = EW;
+  constexpr int T5_CG = EW / 4;                 // column groups of the epilogue
+  constexpr int T5_WCOLS = T5_TN / T5_CG;       // columns per epilogue warp per tile
+  constexpr int T5_PRODUCER_WARP = EW;
+  constexpr int T5_MMA_WARP = EW + 1;
+  extern __shared__ uint8_t t5_smem[];
+  const uint32_t raw = bw::smem_u32(t5_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = t5_smem + (base - raw);
+  const uint32_t sA = base;                                   // [rt][kb][128 x 32 B]
+  const uint32_t sB = sA + T5_RT * KB * T5_BLK;               // [stage][kb][128 x 32 B]
+  const uint32_t vOff = sB + T5_ST * KB * T5_BLK - base;
+  float4 *sV = reinterpret_cast<float4 *>(gbase + vOff);       // [stage][MP][128]
+  const uint32_t sBar = base + vOff + T5_ST * MP * T5_TN * 16;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(gbase + (sBar - base) + 8 * T5_NBAR);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+  auto bar = [&](int i) -> uint32_t { return sBar + 8u * (uint32_t)i; };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int64_t p_begin = (int64_t)b * a.T / G, p_end = (int64_t)(b + 1) * a.T / G;
+  const int64_t rb_first = p_begin / a.C;
+  const int ct_first = (int)(p_begin - rb_first * a.C);
+  // (row block, column tile) of pair p are kept incrementally along the range
+  // (no per-tile 64-bit division)
+
+  if (threadIdx.x == 0) {
+    bw::mbar_init(bar(T5_BAR_A_FULL), 1);
+    bw::mbar_init(bar(T5_BAR_A_EMPTY), 1);
+    for (int s = 0; s < T5_ST; ++s) {
+      bw::mbar_init(bar(T5_BAR_B_FULL + s), 1);
+      bw::mbar_init(bar(T5_BAR_B_EMPTY + s), 1);
+      bw::mbar_init(bar(T5_BAR_V_EMPTY + s), T5_EPI_WARPS);   // one arrival per warp
+    }
+    for (int i = 0; i < 2; ++i) {
+      bw::mbar_init(bar(T5_BAR_D_FULL + i), 1);
+      bw::mbar_init(bar(T5_BAR_D_EMPTY + i), T5_EPI_WARPS);
+    }
+    bw::mbar_init(bar(T5_BAR_FIN), 1);
+    *abort_flag = 0;
+    bw::fence_mbar_init();
+  }
+  if (warp == T5_MMA_WARP) {
+    bw::tmem_alloc(bw::smem_u32(tslot), T5_TMEM_COLS);
+    bw::tmem_relinquish();
+  }
+  if (warp == T5_PRODUCER_WARP && lane == 0) {
+    bw::prefetch_tensormap(&rowmap);
+    bw::prefetch_tensormap(&colmap);
+  }
+  bw::tc_fence_before();
+  __syncthreads();
+  bw::tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // bounded wait; on timeout records the fault and aborts the CTA
+  auto wait = [&](int i, uint32_t parity) -> bool {
+    if (bw::mbar_wait_abortable(bar(i), parity, T5_WAIT_BUDGET, abort_flag)) return true;
+    *abort_flag = 1;
+    atomicOr(a.fault, 1);
+    return false;
+  };
+
+  if (warp == T5_PRODUCER_WARP) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      constexpr uint32_t VBYTES = MP * T5_TN * 16;
+      int64_t kt = 0, issued_b = 0;
+      int issued_a = 0;
+      int64_t rb = rb_first;
+      int ct = ct_first;
+      for (int64_t p = p_begin; p < p_end; ++p, ++kt, (++ct == a.C ? (ct = 0, ++rb) : 0)) {
+        if (p == p_begin || ct == 0) {
+          if (!wait(T5_BAR_A_EMPTY, (uint32_t)(issued_a & 1) ^ 1u)) break;
+          bw::mbar_arrive_expect_tx(bar(T5_BAR_A_FULL), T5_RT * KB * T5_BLK);
+#pragma unroll
+          for (int rt = 0; rt < T5_RT; ++rt)
+            bw::tma_load_3d(sA + rt * KB * T5_BLK, &rowmap, bar(T5_BAR_A_FULL), 0,
+                            (int)(rb * T5_RB + rt * T5_TM), 0);
+          ++issued_a;
+        }
+        const int s = (int)(kt % T5_ST);
+        const uint32_t ph = (uint32_t)((kt / T5_ST) & 1);
+        if (!wait(T5_BAR_B_EMPTY + s, ph ^ 1u) || !wait(T5_BAR_V_EMPTY + s, ph ^ 1u)) break;
+        bw::mbar_arrive_expect_tx(bar(T5_BAR_B_FULL + s), KB * T5_BLK + VBYTES);
+        bw::tma_load_3d(sB + s * KB * T5_BLK, &colmap, bar(T5_BAR_B_FULL + s), 0, ct * T5_TN, 0);
+        bw::bulk_load(base + vOff + (uint32_t)s * VBYTES, a.vdup + (size_t)ct * MP * T5_TN,
+                      VBYTES, bar(T5_BAR_B_FULL + s));
+        ++issued_b;
+      }
+      // wait (bounded, quietly) for this lane's own copies: the last one of
+      // each stage and of the row operand.  After a normal run all have been
+      // consumed and every wait returns at once.
+      for (int64_t q = (issued_b > T5_ST ? issued_b - T5_ST : 0); q < issued_b; ++q)
+        bw::mbar_wait(bar(T5_BAR_B_FULL + (int)(q % T5_ST)), (uint32_t)((q / T5_ST) & 1),
+                      T5_WAIT_BUDGET >> 4);
+      if (issued_a > 0)
+        bw::mbar_wait(bar(T5_BAR_A_FULL), (uint32_t)((issued_a - 1) & 1), T5_WAIT_BUDGET >> 4);
+    }
+    __syncwarp();
+  } else if (warp == T5_MMA_WARP) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t IDESC = bw::idesc_f16_f32(T5_TM, T5_TN);
+      int64_t kt = 0;
+      int seg = 0;
+      int ct = ct_first;
+      for (int64_t p = p_begin; p < p_end; ++p, ++kt, (++ct == a.C ? ct = 0 : 0)) {
+        if (p == p_begin || ct == 0) {
+          if (!wait(T5_BAR_A_FULL, (uint32_t)(seg & 1))) break;
+          ++seg;
+        }
+        const int s = (int)(kt % T5_ST);
+        const int buf = (int)(kt & 1);
+        if (!wait(T5_BAR_B_FULL + s, (uint32_t)((kt / T5_ST) & 1))) break;
+        if (!wait(T5_BAR_D_EMPTY + buf, (uint32_t)((kt >> 1) & 1) ^ 1u)) break;
+        bw::tc_fence_after();
+#pragma unroll
+        for (int rt = 0; rt < T5_RT; ++rt) {
+          const uint32_t d = tmem + (uint32_t)((buf * T5_RT + rt) * T5_TN);
+          const uint32_t aBase = sA + rt * KB * T5_BLK, bBase = sB + s * KB * T5_BLK;
+          uint32_t acc = 0;
+#pragma unroll
+          for (int kc = 0; kc < NH; ++kc) {
+            bw::mma_f16(d, bw::sdesc_kmajor_sw32(aBase + (NH + kc) * T5_BLK),
+                        bw::sdesc_kmajor_sw32(bBase + kc * T5_BLK), IDESC, acc);
+            acc = 1;
+            bw::mma_f16(d, bw::sdesc_kmajor_sw32(aBase + kc * T5_BLK),
+                        bw::sdesc_kmajor_sw32(bBase + (NH + kc) * T5_BLK), IDESC, 1);
+          }
+          if (CSEP)
+            bw::mma_f16(d, bw::sdesc_kmajor_sw32(aBase + 2 * NH * T5_BLK),
+                        bw::sdesc_kmajor_sw32(bBase + 2 * NH * T5_BLK), IDESC, 1);
+#pragma unroll
+          for (int kc = 0; kc < NH; ++kc)
+            bw::mma_f16(d, bw::sdesc_kmajor_sw32(aBase + kc * T5_BLK),
+                        bw::sdesc_kmajor_sw32(bBase + kc * T5_BLK), IDESC, 1);
+        }
+        bw::mma_commit(bar(T5_BAR_D_FULL + buf));
+        bw::mma_commit(bar(T5_BAR_B_EMPTY + s));
+        if (p + 1 == p_end || ct + 1 == a.C) bw::mma_commit(bar(T5_BAR_A_EMPTY));
+      }
+      // every MMA issued so far has completed once FIN flips
+      bw::mma_commit(bar(T5_BAR_FIN));
+      bw::mbar_wait(bar(T5_BAR_FIN), 0, T5_WAIT_BUDGET >> 4);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int qd = warp & 3;        // TMEM lane quarter
+    const int cg = warp >> 2;       // column group
+    const int g = lane >> 2, tq = lane & 3;
+    float2 acc[T5_RT][2][M];        // [row tile][rows g,g+8 | g+16,g+24][rhs]
+#pragma unroll
+    for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+        for (int c = 0; c < M; ++c) acc[rt][hf][c] = f2(0.0f, 0.0f);
+    constexpr int NBT = T5_WCOLS / 16;   // batches of 16 columns per tile
+    if constexpr (LAG) {
+      // segment end: the four lanes of a row group hold sums over different
+      // columns; add them and write this warp's partial sums
+      auto flush = [&](int64_t rbq) {
+        const int j = (int)(rbq - rb_first);
+        float *out = a.part + (((int64_t)b * a.J + j) * T5_CG + cg) * (int64_t)M * T5_RB;
+#pragma unroll
+        for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              float2 v = acc[rt][hf][c];
+              v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+              v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+              v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+              v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+              if ((c & 3) == tq) {
+                const int row = rt * T5_TM + 32 * qd + 16 * hf + g;
+                out[c * T5_RB + row] = v.x;
+                out[c * T5_RB + row + 8] = v.y;
+              }
+              acc[rt][hf][c] = f2(0.0f, 0.0f);
+            }
+      };
+      // kernel values of one batch: [ch][e][rt][hf] -> rows (g, g + 8) pair
+      auto kappa_batch = [&](const uint32_t *cur, float2 *kq) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+              for (int hf = 0; hf < 2; ++hf) {
+                const uint32_t *q = &cur[(rt * 2 + hf) * 8 + ch * 4];
+                kq[((ch * 2 + e) * 2 + rt) * 2 + hf] =
+                    f2(t5_kappa<KERN>(q[e]), t5_kappa<KERN>(q[2 + e]));
+              }
+      };
+      auto ffma_batch = [&](const float2 *kq, const float4 *vq, int col0) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int jl = col0 + ch * 8 + 2 * tq + e;
+#pragma unroll
+            for (int cp = 0; cp < MP; ++cp) {
+              const float4 v = vq[cp * T5_TN + jl];
+#pragma unroll
+              for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                  const float2 k2 = kq[((ch * 2 + e) * 2 + rt) * 2 + hf];
+                  acc[rt][hf][2 * cp] = __ffma2_rn(k2, f2(v.x, v.y), acc[rt][hf][2 * cp]);
+                  acc[rt][hf][2 * cp + 1] = __ffma2_rn(k2, f2(v.z, v.w), acc[rt][hf][2 * cp + 1]);
+                }
+            }
+          }
+      };
+      // the batch whose accumulation is pending
+      float2 kp[16];
+      const float4 *vp = sV;
+      int colp = 0, sp = 0;
+      bool havep = false, p_last = false, p_segend = false;
+      int64_t p_rb = 0;
+      auto retire_pending = [&]() {
+        ffma_batch(kp, vp, colp);
+        if (p_last) {
+          __syncwarp();
+          if (lane == 0) bw::mbar_arrive(bar(T5_BAR_V_EMPTY + sp));
+          if (p_segend) flush(p_rb);
+        }
+      };
+      int64_t kt = 0, rb = rb_first;
+      int ct = ct_first;
+      for (int64_t p = p_begin; p < p_end; ++p, ++kt, (++ct == a.C ? (ct = 0, ++rb) : 0)) {
+        const int s = (int)(kt % T5_ST);
+        const int buf = (int)(kt & 1);
+        const bool ok =
+            __all_sync(0xffffffffu, wait(T5_BAR_D_FULL + buf, (uint32_t)((kt >> 1) & 1)) &&
+                                        wait(T5_BAR_B_FULL + s, (uint32_t)((kt / T5_ST) & 1)));
+        if (!ok) break;
+        bw::tc_fence_after();
+        const float4 *vt = sV + (size_t)s * MP * T5_TN;
+        const uint32_t tcol = tmem + (uint32_t)(buf * T5_RT * T5_TN + cg * T5_WCOLS);
+        const bool segend = (p + 1 == p_end) || (ct + 1 == a.C);
+        uint32_t r[2][32];
+        auto load_batch = [&](int bt, uint32_t *rr) {
+#pragma unroll
+          for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf)
+              bw::tmem_ld_16x256b_x2(tcol + ((uint32_t)(32 * qd + 16 * hf) << 16) +
+                                         (uint32_t)(rt * T5_TN + bt * 16),
+                                     &rr[(rt * 2 + hf) * 8]);
+        };
+        auto release_buffer = [&]() {
+          bw::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) bw::mbar_arrive(bar(T5_BAR_D_EMPTY + buf));
+        };
+        load_batch(0, r[0]);
+        bw::tmem_wait_ld32(r[0]);
+        if (NBT == 1) release_buffer();
+#pragma unroll
+        for (int bt = 0; bt < NBT; ++bt) {
+          if (bt + 1 < NBT) load_batch(bt + 1, r[(bt + 1) & 1]);
+          float2 kc[16];
+          kappa_batch(r[bt & 1], kc);
+          if (havep) retire_pending();
+          if (bt + 1 < NBT) {
+            bw::tmem_wait_ld32(r[(bt + 1) & 1]);
+            if (bt + 2 == NBT) release_buffer();
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) kp[i] = kc[i];
+          vp = vt;
+          colp = cg * T5_WCOLS + bt * 16;
+          sp = s;
+          havep = true;
+          p_last = (bt + 1 == NBT);
+          p_segend = p_last && segend;
+          p_rb = rb;
+        }
+      }
+      if (havep) retire_pending();
+    } else {
+    int64_t kt = 0, rb = rb_first;
+    int ct = ct_first;
+    for (int64_t p = p_begin; p < p_end; ++p, ++kt, (++ct == a.C ? (ct = 0, ++rb) : 0)) {
+      const int s = (int)(kt % T5_ST);
+      const int buf = (int)(kt & 1);
+      // D of this tile, and (for the visibility of the bulk-copied V) the
+      // stage's arrival
+      const bool ok = __all_sync(0xffffffffu, wait(T5_BAR_D_FULL + buf, (uint32_t)((kt >> 1) & 1)) &&
+                                                  wait(T5_BAR_B_FULL + s, (uint32_t)((kt / T5_ST) & 1)));
+      if (!ok) break;
+      bw::tc_fence_after();
+      const float4 *vt = sV + (size_t)s * MP * T5_TN;
+      const uint32_t tcol = tmem + (uint32_t)(buf * T5_RT * T5_TN + cg * T5_WCOLS);
+      // with PIPE, the TMEM loads of batch bt + 1 are in flight while batch bt
+      // is computed
+      uint32_t r[PIPE ? 2 : 1][32];   // [batch parity][rt][hf][8]
+      auto load_batch = [&](int bt, uint32_t *rr) {
+#pragma unroll
+        for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf)
+            bw::tmem_ld_16x256b_x2(tcol + ((uint32_t)(32 * qd + 16 * hf) << 16) +
+                                       (uint32_t)(rt * T5_TN + bt * 16),
+                                   &rr[(rt * 2 + hf) * 8]);
+      };
+      auto release_buffer = [&]() {
+        // every TMEM load of this buffer has landed: hand it back
+        bw::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) bw::mbar_arrive(bar(T5_BAR_D_EMPTY + buf));
+      };
+      if (PIPE) {
+        load_batch(0, r[0]);
+        bw::tmem_wait_ld32(r[0]);
+        if (NBT == 1) release_buffer();
+      }
+#pragma unroll
+      for (int bt = 0; bt < NBT; ++bt) {
+        uint32_t *cur = r[PIPE ? (bt & 1) : 0];
+        if (PIPE) {
+          if (bt + 1 < NBT) load_batch(bt + 1, r[(bt + 1) & 1]);
+        } else {
+          load_batch(bt, cur);
+          bw::tmem_wait_ld32(cur);
+          if (bt + 1 == NBT) release_buffer();
+        }
+        const int col0 = cg * T5_WCOLS + bt * 16;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int jl = col0 + ch * 8 + 2 * tq + e;
+            float2 kk[T5_RT][2];
+#pragma unroll
+            for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+              for (int hf = 0; hf < 2; ++hf) {
+                const uint32_t *q = &cur[(rt * 2 + hf) * 8 + ch * 4];
+                kk[rt][hf] = f2(t5_kappa<KERN>(q[e]), t5_kappa<KERN>(q[2 + e]));
+              }
+#pragma unroll
+            for (int cp = 0; cp < MP; ++cp) {
+              const float4 v = vt[cp * T5_TN + jl];
+#pragma unroll
+              for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                  acc[rt][hf][2 * cp] = __ffma2_rn(kk[rt][hf], f2(v.x, v.y), acc[rt][hf][2 * cp]);
+                  acc[rt][hf][2 * cp + 1] =
+                      __ffma2_rn(kk[rt][hf], f2(v.z, v.w), acc[rt][hf][2 * cp + 1]);
+                }
+            }
+          }
+        }
+        if (PIPE && bt + 1 < NBT) {
+          bw::tmem_wait_ld32(r[(bt + 1) & 1]);
+          if (bt + 2 == NBT) release_buffer();
+        }
+      }
+      __syncwarp();
+      if (lane == 0) bw::mbar_arrive(bar(T5_BAR_V_EMPTY + s));
+      if (p + 1 == p_end || ct + 1 == a.C) {
+        // end of a segment: the four lanes of a row group hold sums over
+        // different columns; add them and write this warp's partial sums
+        const int j = (int)(rb - rb_first);
+        float *out = a.part + (((int64_t)b * a.J + j) * T5_CG + cg) * (int64_t)M * T5_RB;
+#pragma unroll
+        for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              float2 v = acc[rt][hf][c];
+              v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+              v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+              v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+              v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+              if ((c & 3) == tq) {
+                const int row = rt * T5_TM + 32 * qd + 16 * hf + g;
+                out[c * T5_RB + row] = v.x;
+                out[c * T5_RB + row + 8] = v.y;
+              }
+              acc[rt][hf][c] = f2(0.0f, 0.0f);
+            }
+      }
+    }
+    }
+}
+
+  bw::tc_fence_before();
+  __syncthreads();
+  if (warp == T5_MMA_WARP) {
+    bw::tc_fence_after();
+    bw::tmem_dealloc(tmem, T5_TMEM_COLS);
+  }
+}
+
+// CTA whose pair range contains pair p: the largest b with floor(b T / G) <= p.
+__host__ __device__ inline int t5_cta_of(int64_t p, int64_t T, int G) {
+  return (int)(((p + 1) * (int64_t)G + T - 1) / T) - 1;
+}
+
+// Y[c][i] = sum of the partial sums of row i over the CTAs covering its row
+// block (CTA order) and column groups, + lambda V[c][i] when V is given.
+__global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int m, int M, int C,
+                                 int64_t T, int G, int J, int CG, float lambda,
+                                 const float *__restrict__ V, int64_t ldv, float *__restrict__ Y,
+                                 int64_t ldy);
+
+}  // namespace krr
+
+namespace krr {
+
+// Epilogue variants of the tcgen05 product: 1 = 8 warps with pipelined TMEM
+// loads, 2 = 16 warps, 3 = 8 warps without the pipelining, 4 = 16 warps with
+// it, 5 = 8 warps, pipelined and software-pipelined by one batch, 6 = 12 warps
+// on 96-column tiles with pipelined loads, 7 = the same without (the 12- and
+// 16-warp and software-pipelined variants serve M <= 4 only).
+constexpr int T5_NVARIANTS = 7;
+__host__ __device__ constexpr int t5_variant_ew(int v) {
+  return (v == 2 || v == 4) ? 16 : (v >= 6 ? 12 : 8);
+}
+__host__ __device__ constexpr int t5_variant_tn(int v) { return v >= 6 ? 96 : 128; }
+inline bool t5_variant_valid(int v, int M) {
+  return v >= 1 && v <= T5_NVARIANTS && (v == 1 || v == 3 || M <= 4);
+}
+
+// Launches the instance for (nh, csep, M, variant); cudaErrorInvalidValue for
+// a shape without one.  Defined per kernel function in kmvtc5_gauss.cu /
+// kmvtc5_matern.cu.
+cudaError_t launch_kmvtc5_gauss(int nh, int csep, int M, int variant, int G, size_t smem,
+                                cudaStream_t s, const CUtensorMap &rowmap,
+                                const CUtensorMap &colmap, const T5Args &a);
+cudaError_t launch_kmvtc5_matern(int nh, int csep, int M, int variant, int G, size_t smem,
+                                 cudaStream_t s, const CUtensorMap &rowmap,
+                                 const CUtensorMap &colmap, const T5Args &a);
+
+template <int KERN, int NH, int CS, int M, int EW, int PIPE, int LAG = 0, int TN = 128>
+cudaError_t launch_kmvtc5_one(int G, size_t smem, cudaStream_t s, const CUtensorMap &rowmap,
+                              const CUtensorMap &colmap, const T5Args &a) {
+  auto k = kmvtc5_kernel<KERN, NH, CS, M, EW, PIPE, LAG, TN>;
+  if (raise_smem_limit(k, smem) != KRR_OK) return cudaErrorInvalidValue;
+  k<<<G, (EW + 2) * 32, smem, s>>>(rowmap, colmap, a);
+  return cudaGetLastError();
+}
+
+template <int KERN, int NH, int CS, int M>
+cudaError_t launch_kmvtc5_m(int variant, int G, size_t smem, cudaStream_t s,
+                            const CUtensorMap &rowmap, const CUtensorMap &colmap,
+                            const T5Args &a) {
+  switch (variant) {
+    case 1: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1>(G, smem, s, rowmap, colmap, a);
+    case 3: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 0>(G, smem, s, rowmap, colmap, a);
+    case 2:
+      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 0>(G, smem, s, rowmap, colmap, a);
+      break;
+    case 4:
+      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 1>(G, smem, s, rowmap, colmap, a);
+      break;
+    case 5:
+      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1, 1>(G, smem, s, rowmap, colmap, a);
+      break;
+    case 6:
+      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 1, 0, 96>(G, smem, s, rowmap, colmap, a);
+      break;
+    case 7:
+      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 0, 0, 96>(G, smem, s, rowmap, colmap, a);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int KERN>
+cudaError_t launch_kmvtc5(int nh, int csep, int M, int variant, int G, size_t smem,
+                          cudaStream_t s, const CUtensorMap &rowmap, const CUtensorMap &colmap,
+                          const T5Args &a) {
+#define KRR_T5_CASE(NH, CS, MM)                                                         \
+  if (nh == NH && csep == CS && M == MM)                                              \
+    return launch_kmvtc5_m<KERN, NH, CS, MM>(variant, G, smem, s, rowmap, colmap, a);
+  KRR_T5_CASE(1, 0, 2) KRR_T5_CASE(1, 0, 4) KRR_T5_CASE(1, 0, 8)
+  KRR_T5_CASE(1, 1, 2) KRR_T5_CASE(1, 1, 4) KRR_T5_CASE(1, 1, 8)
+  KRR_T5_CASE(2, 0, 2) KRR_T5_CASE(2, 0, 4) KRR_T5_CASE(2, 0, 8)
+  KRR_T5_CASE(2, 1, 2) KRR_T5_CASE(2, 1, 4) KRR_T5_CASE(2, 1, 8)
+#undef KRR_T5_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace krr

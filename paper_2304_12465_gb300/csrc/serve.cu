@@ -868,7 +868,7 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   const int M = serve_pad_m(m);
   // inner products on the tensor cores where the tile code has a variant and
   // the coordinates fit the half split
-  if (product_path() == 0) KRR_TRY(prepare_points_tc(Xd, s, sl->P32));
+  if (product_path() != 1) KRR_TRY(prepare_points_tc(Xd, s, sl->P32, false));
   const int kc = sl->P32.kc16;
   const int rank = sl->core ? sl->core->rank : 0;
   const int64_t chunk = serve_chunk(N);

@@ -21,20 +21,38 @@ def test_fma_path_is_the_fp32_pipe():
     assert "tensor" not in r["pipes"]
 
 
-def test_tensor_path_takes_the_largest_pipe_time():
-    # d = 16, m = 4: FP32 (9 flop) outweighs MUFU (1 ex2) and the MMAs
-    r = bench.product_roofline("tensor", wl(0, 16, 4), 3.39, 50, 2070.0)
+def test_tcgen05_path_takes_the_largest_pipe_time():
+    # d = 16, m = 4: 4 MMAs (L.H, H.L, H.H, c) = 128 tensor flop, 2m = 8 FP32
+    # flop (c_i + c_j folded into the MMAs) and 1 ex2: FP32 and MUFU tie at
+    # 1/32 clock per entry per SM, above the tensor time
+    r = bench.product_roofline("tensor", wl(0, 16, 4), 2.25, 3, 2070.0)
     times = {k: v["ideal_ms"] for k, v in r["pipes"].items()}
-    assert r["pipe"] == max(times, key=times.get) == "fp32"
-    assert r["frac"] == pytest.approx(times["fp32"] / 3.39)
-    assert r["pipes"]["tensor"]["per_entry"] == 96
-    # d = 32, m = 1: two coordinate blocks of MMAs now dominate
-    r = bench.product_roofline("tensor", wl(0, 32, 1), 3.0, 50, 2070.0)
+    assert r["pipe"] == max(times, key=times.get)
+    assert r["pipe"] in ("fp32", "mufu")
+    assert times["fp32"] == pytest.approx(times["mufu"], rel=2e-3)
+    assert r["frac"] == pytest.approx(times[r["pipe"]] / 2.25)
+    assert r["pipes"]["tensor"]["per_entry"] == 128
+    assert r["pipes"]["fp32"]["per_entry"] == 8
+    # the c-part rides in a spare block position when d mod 16 is 1..10
+    assert bench.tc5_mmas(8) == 3 and bench.tc5_mmas(12) == 4 and bench.tc5_mmas(20) == 6
+    # d = 32, m = 1: two coordinate blocks and a c block of MMAs dominate
+    r = bench.product_roofline("tensor", wl(0, 32, 1), 3.0, 3, 2070.0)
     assert r["pipe"] == "tensor" and r["bound"] == "tensor"
-    assert r["pipes"]["tensor"]["per_entry"] == 192
+    assert r["pipes"]["tensor"]["per_entry"] == 2 * 16 * 7
     # Matern: two MUFU operations per entry
-    r = bench.product_roofline("tensor", wl(2, 8, 1), 3.0, 50, 2070.0)
+    r = bench.product_roofline("tensor", wl(2, 8, 1), 3.0, 3, 2070.0)
     assert r["pipes"]["mufu"]["per_entry"] == 2
+
+
+def test_mma_sync_path_uses_its_own_tensor_peak():
+    # d = 16, m = 4: 96 flop per entry at the measured mma.sync f16 rate
+    # (1.58 ms) outweighs the FP32 pipe (1 + 2m = 9 flop, 1.12 ms)
+    r = bench.product_roofline("mma_sync", wl(0, 16, 4), 3.39, 50, 2070.0)
+    assert r["pipe"] == "tensor" and r["bound"] == "tensor"
+    assert r["peak"] == bench.MMA_SYNC_F16_TFLOPS
+    assert r["pipes"]["tensor"]["per_entry"] == 96
+    assert r["pipes"]["fp32"]["per_entry"] == 9
+    assert r["frac"] == pytest.approx(96e10 / 606e12 * 1e3 / 3.39)
 
 
 def test_laplace_has_no_tensor_path():

@@ -92,7 +92,7 @@ def test_fp32_product_large_coordinates(K):
     tc = K.krr_kmatvec(X, O.GAUSSIAN, 0.02, 0.5, V, prec="mixed")
     np.testing.assert_array_equal(tc, fma)
     with pytest.raises(K.KrrError):
-        K.krr_set_product_path(2)
+        K.krr_set_product_path(3)
 
 
 @pytest.mark.parametrize("kern", KERNS)
@@ -217,22 +217,25 @@ def test_batched_settings_product(K, N, d, ms):
 
 
 def test_autotuned_product(K):
-    """With autotuning on, the first float32 product of a shape times the
-    candidate column tiles and keeps one; the product still meets the float32
-    bound, repeats bit for bit, and the choice is reported."""
+    """With autotuning on, the first product of a shape on the FMA path times
+    the candidate column tiles and keeps one; the product still meets the
+    float32 bound, repeats bit for bit, and the choice is reported.  (The
+    tcgen05 path's variant tuning is tested in test_gpu_tc5.py.)"""
     rng = np.random.default_rng(21)
     X = rng.standard_normal((20011, 8))
     V = rng.standard_normal((3, 20011))
     ref = O.kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, np.arange(0, 20011, 97))
     bound = f32_product_bound(X, O.GAUSSIAN, 1.1, 0.5, V, np.arange(0, 20011, 97))
+    K.krr_set_product_path("fma")
     assert K.krr_autotune_choice(O.GAUSSIAN, 8, 3, 20011) == 0
     K.krr_set_autotune(True)
     try:
         a = K.krr_kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, prec="mixed")
         b = K.krr_kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, prec="mixed")
+        splits = K.krr_autotune_choice(O.GAUSSIAN, 8, 3, 20011)
     finally:
         K.krr_set_autotune(False)
-    splits = K.krr_autotune_choice(O.GAUSSIAN, 8, 3, 20011)
+        K.krr_set_product_path("tensor")
     assert 1 <= splits <= (20011 + 63) // 64
     np.testing.assert_array_equal(a, b)
     assert np.all(np.abs(a[:, ::97] - ref) <= 2e-5 * bound)
