@@ -335,15 +335,18 @@ KRR_API void krill_free(krill_precond *P);
 /* X (N x d), V and Y (N x m, column-major) must be device pointers on the    */
 /* current device; host pointers are rejected with KRR_EINVAL (staging them   */
 /* would allocate).  The split partial sums live in one 16 MiB static device  */
-/* array owned by the library (held by every GPU that loads the library until */
-/* the process exits), so N x padded(m) must be <= 2^21, padded(m) being m    */
+/* array owned by the library (held by every GPU that uses it until the       */
+/* process exits), so N x padded(m) must be <= 2^21, padded(m) being m        */
 /* rounded up to 1, 2, 4, 8 or 16; larger sizes return KRR_EINVAL with a      */
-/* message.  The first call on each device looks up the array's device        */
-/* address and caches it; make that first call before any stream capture.    */
-/* Every call shares the one array and overwrites the partial sums it reads  */
-/* (nothing needs to start at zero), so calls that overlap on the GPU race:   */
-/* serialise them (one stream, or events).  Returns after the stream is       */
-/* synchronised.                                                              */
+/* message.  With CUDA's lazy module loading the array is created on a device */
+/* when the library's device code is first loaded there -- at the latest by   */
+/* the first call of this entry point on that device, which looks up the      */
+/* array's address and caches it.  That first call can therefore allocate     */
+/* (and fail with KRR_ENOMEM on a full device): make it at set-up time, and   */
+/* before any stream capture.  Every call shares the one array and overwrites */
+/* the partial sums it reads (nothing needs to start at zero), so calls that  */
+/* overlap on the GPU race: serialise them (one stream, or events).  Returns  */
+/* after the stream is synchronised.                                          */
 /* ------------------------------------------------------------------------ */
 KRR_API krr_status krr_kmatvec_f64_noalloc(const double *X, int64_t N, int d,
                                            krr_kernel kern, double sigma, double lambda,
