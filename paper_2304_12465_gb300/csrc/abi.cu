@@ -370,11 +370,24 @@ krr_status krr_predict(const double *Xtrain, int64_t N, int d, krr_kernel kern, 
     PointsF32 P, R;
     KRR_TRY(prepare_points_f32(Xd, N, d, kern, sigma, s, P));
     KRR_TRY(prepare_points_f32(Td, Nt, d, kern, sigma, s, R, P.mean.p));
+    // the tcgen05 rectangular product when both point sets have split operands
+    bool tc5 = false;
+    if (product_path() == 0) {
+      int bad_p = 0, bad_r = 0;
+      KRR_TRY(prepare_points_tc5(Xd, s, P, &bad_p));
+      if (P.nh5 > 0) KRR_TRY(prepare_points_tc5(Td, s, R, &bad_r));
+      tc5 = P.nh5 > 0 && R.nh5 > 0;
+    }
     DevBuf<float> a32, y32, part;
     KRR_TRY(a32.alloc((size_t)N * m, s));
     KRR_TRY(y32.alloc((size_t)Nt * m, s));
     KRR_TRY(convert_f64_to_f32(Ad, a32.p, N * m, s));
-    KRR_TRY(kcross_f32(R, P, a32.p, N, m, y32.p, Nt, s, part));
+    if (tc5) {
+      KRR_TRY(kmv_tc5(R, P, 0.0f, false, a32.p, N, m, y32.p, Nt, s, part));
+      KRR_TRY(tc5_check_fault(s));
+    } else {
+      KRR_TRY(kcross_f32(R, P, a32.p, N, m, y32.p, Nt, s, part));
+    }
     KRR_TRY(convert_f32_to_f64(y32.p, o.dev, Nt * m, s));
   }
   return o.finish(s);
@@ -698,6 +711,7 @@ krr_status krill_solve(const krill_precond *P, const double *Y, int m, double to
   if (info) std::memset(info, 0, sizeof(*info));
   krr_status st = krill_solve_device(P, Yd, m, tol, maxit, out.dev, s, info);
   if (st != KRR_OK && st != KRR_ENOCONV) return st;
+  KRR_TRY(tc5_check_fault(s));   // a bounded wait of a tensor-core product gave up
   krr_status st2 = out.finish(s);
   return st2 != KRR_OK ? st2 : st;
 }

@@ -189,13 +189,14 @@ __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int
   const int b_lo = t5_cta_of(rb * C, T, G);
   const int b_hi = t5_cta_of(rb * C + C - 1, T, G);
   for (int c = 0; c < m; ++c) {
-    float acc = 0.0f;
+    double acc = 0.0;   // a row block's segments may come from many CTAs
     for (int b = b_lo; b <= b_hi; ++b) {
       const int64_t j = rb - ((int64_t)b * T / G) / C;
       for (int cg = 0; cg < CG; ++cg)
-        acc += part[((((int64_t)b * J + j) * CG + cg) * M + c) * T5_RB + r];
+        acc += (double)part[((((int64_t)b * J + j) * CG + cg) * M + c) * T5_RB + r];
     }
-    Y[(int64_t)c * ldy + i] = V ? acc + lambda * V[(int64_t)c * ldv + i] : acc;
+    Y[(int64_t)c * ldy + i] =
+        V ? (float)(acc + (double)lambda * (double)V[(int64_t)c * ldv + i]) : (float)acc;
   }
 }
 

@@ -294,13 +294,29 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
     const int qd = warp & 3;        // TMEM lane quarter
     const int cg = warp >> 2;       // column group
     const int g = lane >> 2, tq = lane & 3;
+    // sums over the current tile's columns (acc) and over the segment's
+    // finished tiles (tot): two-level float32 accumulation, so a long segment
+    // (up to about 1e5 columns per row) adds one tile sum at a time to its
+    // running total instead of one entry at a time
     float2 acc[T5_RT][2][M];        // [row tile][rows g,g+8 | g+16,g+24][rhs]
+    float2 tot[T5_RT][2][M];
 #pragma unroll
     for (int rt = 0; rt < T5_RT; ++rt)
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
-        for (int c = 0; c < M; ++c) acc[rt][hf][c] = f2(0.0f, 0.0f);
+        for (int c = 0; c < M; ++c) acc[rt][hf][c] = tot[rt][hf][c] = f2(0.0f, 0.0f);
+    auto fold_tile = [&]() {
+#pragma unroll
+      for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            tot[rt][hf][c] = __fadd2_rn(tot[rt][hf][c], acc[rt][hf][c]);
+            acc[rt][hf][c] = f2(0.0f, 0.0f);
+          }
+    };
     constexpr int NBT = T5_WCOLS / 16;   // batches of 16 columns per tile
     if constexpr (LAG) {
       // segment end: the four lanes of a row group hold sums over different
@@ -314,7 +330,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-              float2 v = acc[rt][hf][c];
+              float2 v = tot[rt][hf][c];
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
               v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
@@ -324,7 +340,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
                 out[c * T5_RB + row] = v.x;
                 out[c * T5_RB + row + 8] = v.y;
               }
-              acc[rt][hf][c] = f2(0.0f, 0.0f);
+              tot[rt][hf][c] = f2(0.0f, 0.0f);
             }
       };
       // kernel values of one batch: [ch][e][rt][hf] -> rows (g, g + 8) pair
@@ -371,6 +387,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
       auto retire_pending = [&]() {
         ffma_batch(kp, vp, colp);
         if (p_last) {
+          fold_tile();
           __syncwarp();
           if (lane == 0) bw::mbar_arrive(bar(T5_BAR_V_EMPTY + sp));
           if (p_segend) flush(p_rb);
@@ -509,6 +526,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           if (bt + 2 == NBT) release_buffer();
         }
       }
+      fold_tile();
       __syncwarp();
       if (lane == 0) bw::mbar_arrive(bar(T5_BAR_V_EMPTY + s));
       if (p + 1 == p_end || ct + 1 == a.C) {
@@ -522,7 +540,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-              float2 v = acc[rt][hf][c];
+              float2 v = tot[rt][hf][c];
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
               v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
@@ -532,7 +550,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
                 out[c * T5_RB + row] = v.x;
                 out[c * T5_RB + row + 8] = v.y;
               }
-              acc[rt][hf][c] = f2(0.0f, 0.0f);
+              tot[rt][hf][c] = f2(0.0f, 0.0f);
             }
       }
     }

@@ -576,4 +576,41 @@ krr_status krill_product64(const krill_precond *P, KrillFF &Q, const double *bet
   return KRR_OK;
 }
 
+// ------------------------------------------- tcgen05 block products
+krr_status krill_points_tc5(const krill_precond *P, cudaStream_t s, KrillTC5 &T) {
+  T.ok = false;
+  if (P->kern == KLAPLACE || product_path() == 1 || P->d > 32) return KRR_OK;
+  KRR_TRY(prepare_points_f32(P->X, P->N, P->d, P->kern, P->sigma, s, T.all));
+  DevBuf<double> xc;
+  KRR_TRY(xc.alloc((size_t)P->k * P->d, s));
+  gather_points_kernel<<<ceil_div((int64_t)P->k * P->d, 256), 256, 0, s>>>(P->X, P->d, P->S,
+                                                                          P->k, xc.p);
+  KRR_LAUNCH_CHECK();
+  KRR_TRY(prepare_points_f32(xc.p, P->k, P->d, P->kern, P->sigma, s, T.centers, T.all.mean.p));
+  int bad_all = 0, bad_c = 0;
+  KRR_TRY(prepare_points_tc5(P->X, s, T.all, &bad_all));
+  KRR_TRY(prepare_points_tc5(xc.p, s, T.centers, &bad_c));
+  T.ok = !bad_all && !bad_c && T.all.nh5 > 0 && T.centers.nh5 > 0;
+  return KRR_OK;
+}
+
+krr_status krill_product_tc5(const krill_precond *P, KrillTC5 &T, const double *beta, int m,
+                             double *out, cudaStream_t s, DevBuf<float> &u) {
+  const int64_t N = P->N;
+  const int k = P->k;
+  if (u.n < (size_t)N * m) KRR_TRY(u.alloc((size_t)N * m, s));
+  if (T.b32.n < (size_t)k * m) KRR_TRY(T.b32.alloc((size_t)k * m, s));
+  if (T.v32.n < (size_t)k * m) KRR_TRY(T.v32.alloc((size_t)k * m, s));
+  if (T.v64.n < (size_t)k * m) KRR_TRY(T.v64.alloc((size_t)k * m, s));
+  KRR_TRY(convert_f64_to_f32(beta, T.b32.p, (int64_t)k * m, s));
+  // u = A(:, S) beta: rows are all points, columns the centers
+  KRR_TRY(kmv_tc5(T.all, T.centers, 0.0f, false, T.b32.p, k, m, u.p, N, s, T.part));
+  // v = A(S, :) u: rows are the centers, columns all points
+  KRR_TRY(kmv_tc5(T.centers, T.all, 0.0f, false, u.p, N, m, T.v32.p, k, s, T.part));
+  KRR_TRY(convert_f32_to_f64(T.v32.p, T.v64.p, (int64_t)k * m, s));
+  sym_gemv_add_kernel<<<ceil_div(k, 8), 256, 0, s>>>(P->H, k, beta, m, T.v64.p, out);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
 }  // namespace krr

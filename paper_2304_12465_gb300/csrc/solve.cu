@@ -381,12 +381,15 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
   KrillFF Q;
   KRR_TRY(krill_points_ff(P, s, Q));
   KRR_TRY(krill_rhs(P, Q, Y, m, b.p, s));
+  KrillTC5 T;
+  KRR_TRY(krill_points_tc5(P, s, T));
   double entries = (double)P->N * k;
   DevBuf<float> u;
   DevBuf<double> v;
   PcgOps<double> ops;
   ops.product = [&](const double *in, double *out, cudaStream_t st) {
-    return krill_product(P, in, m, out, st, u, v);
+    return T.ok ? krill_product_tc5(P, T, in, m, out, st, u)
+                : krill_product(P, in, m, out, st, u, v);
   };
   ops.precond = [&](const double *in, double *out, cudaStream_t st) {
     return krill_precond_apply(P, in, m, tmp.p, out, st);
