@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma", "mma_sync"],
                     help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the composed plain float64 GPU path (about 45 s)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "serving"],
                     help="c2: one RPCholesky + refined PCG solve per step (headline); "
                          "c1: the plain float64 solve; c3: the batched 8-setting x 2-shift "
@@ -252,6 +254,53 @@ def entries_rpcholesky(N, k):
     return float(N) * (k + 1)
 
 
+def fp64_path_composed(K, w, X, Y, mixed_step_s):
+    """The plain float64 GPU path on the same inputs and seed, composed from
+    live measurements (a whole float64 solve at N = 1e5 takes minutes):
+    RPCholesky time + a float64 PCG whose products are the float-float product
+    (float64-accurate entries: the same iterates as the float64 products up to
+    rounding), with the float-float product time replaced by the measured
+    float64 product time per launch times the number of products."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = K.krr_rpcholesky(X, w.kernel, w.sigma, w.k, w.block, seed=w.seed)
+    torch.cuda.synchronize()
+    t_rpc = time.perf_counter() - t0
+    K.krr_set_profiling(True)
+    t1 = time.perf_counter()
+    _, info = K.krr_pcg_solve(X, w.kernel, w.sigma, Y, w.mu, f, tol=w.tol, prec="ff")
+    torch.cuda.synchronize()
+    t_ff = time.perf_counter() - t1
+    K.krr_set_profiling(False)
+    f.free()
+    gen = torch.Generator(device=X.device).manual_seed(11)
+    V = torch.randn((w.m, w.N), dtype=torch.float64, device=X.device, generator=gen)
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec="fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    kmv64_s = times[-1]
+    n_prod = int(info["kmvff_launches"])
+    ff_prod_s = info["kmvff_ms"] / 1e3
+    composed = t_rpc + (t_ff - ff_prod_s) + n_prod * kmv64_s
+    return {"time_to_tol_s": composed, "kind": "composed",
+            "iters": info["iters"], "status": info["status"],
+            "rel_residual_fp64": info["rel_residual"], "products": n_prod,
+            "kmv64_ms_per_launch": kmv64_s * 1e3,
+            "float_float_pcg_s": t_ff, "rpcholesky_s": t_rpc,
+            "speedup_mixed_vs_fp64": composed / mixed_step_s,
+            "composition": "RPCholesky + float64 PCG with float-float products (same iterates "
+                           "to rounding), its product time replaced by products x the measured "
+                           "float64 product launch; all measured in this run on the same inputs"}
+
+
 def run_native(args):
     import torch
     import paper_2304_12465_gb300 as K
@@ -374,6 +423,9 @@ def run_native(args):
                              "closed_loop_solves_per_s": closed["solves_per_s"],
                              "status": runs["0.8x"]["status"],
                              "escalations": runs["0.8x"]["escalations"]}
+
+    if rank == 0 and world == 1 and not args.no_fp64 and not args.fp64_path:
+        result["fp64_path"] = fp64_path_composed(K, w, X, Y, total_ms / args.steps / 1e3)
 
     if rank == 0 and world == 1 and args.fp64_path:
         torch.cuda.synchronize()

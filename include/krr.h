@@ -66,10 +66,11 @@ typedef enum {
     KRR_PREC_MIXED = 1,  /* float32 kernel tiles and inner PCG, float64-accurate
                             outer iterative refinement, float64 CG scalars and
                             k x k core                                         */
-    KRR_PREC_FLOAT_FLOAT = 2  /* krr_kmatvec only: float64-accurate product
-                            (about 2^-46 per entry) evaluated in float-float
-                            arithmetic on the float32 pipes; the product the
-                            mixed path uses for its refinement residuals       */
+    KRR_PREC_FLOAT_FLOAT = 2  /* krr_kmatvec and krr_pcg_solve: float64-accurate
+                            product (about 2^-46 per entry) evaluated in
+                            float-float arithmetic on the float32 pipes; the
+                            product the mixed path uses for its refinement
+                            residuals                                         */
 } krr_precision;
 
 /* Pivot rule of the partial Cholesky factorization: RPCholesky (Alg. 3)    */
@@ -248,6 +249,9 @@ KRR_API krr_status krr_precond_apply(const krr_factor *F, double mu, const doubl
 /*     an inner float32 PCG (float32 kernel tiles, float64 CG scalars) that   */
 /*     solves (A + lambda I) d = r to a loose tolerance; stops when the       */
 /*     float64 relative residual is <= tol.                                   */
+/*   KRR_PREC_FLOAT_FLOAT: float64 PCG as KRR_PREC_FP64 with the float-float  */
+/*     product in place of the float64 one: the same iterates up to rounding  */
+/*     (entries within about 2^-46), at the float32 pipes' speed.             */
 /* F may be NULL (no preconditioner beyond lambda^{-1} I).  maxit bounds the  */
 /* PCG iterations per column (<= 0 selects 1000).  Y, alpha_out: N x m.       */
 /* info (optional) receives iteration counts, the float64 residual and times. */

@@ -528,7 +528,8 @@ krr_status krr_pcg_solve(const double *X, int64_t N, int d, krr_kernel kern, dou
   KRR_REQUIRE(m >= 1 && m <= 16, "m must be in [1, 16]");
   KRR_REQUIRE(mu > 0 && std::isfinite(mu), "mu must be positive and finite");
   KRR_REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
-  KRR_REQUIRE(prec == KRR_PREC_FP64 || prec == KRR_PREC_MIXED, "unknown precision");
+  KRR_REQUIRE(prec == KRR_PREC_FP64 || prec == KRR_PREC_MIXED || prec == KRR_PREC_FLOAT_FLOAT,
+              "unknown precision");
   KRR_REQUIRE(!F || F->N == N, "factor was built for N = %lld, not %lld", (long long)(F ? F->N : 0),
               (long long)N);
   if (maxit <= 0) maxit = 1000;

@@ -57,7 +57,9 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
   const double lambda = mu * (double)N;
   auto t0 = std::chrono::steady_clock::now();
   const NystromCore *core = nullptr;
-  if (F && F->rank > 0) KRR_TRY(nystrom_core(F, mu, prec, s, &core));
+  // the float-float path applies the float64 preconditioner
+  const int core_prec = (prec == KRR_PREC_FLOAT_FLOAT) ? (int)KRR_PREC_FP64 : prec;
+  if (F && F->rank > 0) KRR_TRY(nystrom_core(F, mu, core_prec, s, &core));
   const double t_build = core ? core->build_s : 0.0;
   auto t1 = std::chrono::steady_clock::now();
   (void)t0;
@@ -67,12 +69,20 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
   double relres = 0.0;
   krr_status final_status = KRR_OK;
 
-  if (prec == KRR_PREC_FP64) {
+  if (prec == KRR_PREC_FP64 || prec == KRR_PREC_FLOAT_FLOAT) {
+    // float64 PCG; the products in float64, or (float-float) float64-accurate
+    // products on the float32 pipes -- the same iterates up to rounding
     DevBuf<double> part;
-    PcgOps<double> ops;
-    ops.product = [&](const double *in, double *out, cudaStream_t st) {
+    DevBuf<float> vsplit;
+    PointsFF Pff;
+    const bool ff = (prec == KRR_PREC_FLOAT_FLOAT);
+    if (ff) KRR_TRY(prepare_points_ff(Xd, N, d, kern, sigma, s, Pff));
+    auto product = [&](const double *in, double *out, cudaStream_t st) {
+      if (ff) return kmv_ff(Pff, lambda, in, N, m, out, N, st, part, vsplit);
       return kmv_f64(Xd, N, d, kern, sigma, lambda, in, N, m, out, N, st, part);
     };
+    PcgOps<double> ops;
+    ops.product = product;
     ops.precond = [&](const double *in, double *out, cudaStream_t st) {
       if (core) return nystrom_apply_f64(F, core, in, m, out, st);
       return scale<double>(in, out, N * m, 1.0 / lambda, st);
@@ -88,7 +98,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
       DevBuf<double> mx, r;
       KRR_TRY(mx.alloc((size_t)N * m, s));
       KRR_TRY(r.alloc((size_t)N * m, s));
-      KRR_TRY(kmv_f64(Xd, N, d, kern, sigma, lambda, alpha, N, m, mx.p, N, s, part));
+      KRR_TRY(product(alpha, mx.p, s));
       entries += kmv_entries(N);
       KRR_TRY(residual_f64(Y, mx.p, r.p, N * m, s));
       std::vector<double> rn(m), yn(m);

@@ -101,6 +101,24 @@ def test_fp64_solve_matches_oracle_at_1e10_when_attainable(K):
     assert rel_err(alpha[0], ref.alpha[0]) < 1e-10
 
 
+def test_float_float_solve_tracks_fp64(K, c1):
+    """float64 PCG with the float-float product (entries within about 2^-46)
+    follows the float64-product iterates: equal to 1e-9 after 30 iterations,
+    and both reach tol 1e-10 within a few iterations of each other."""
+    w, ref_f, f = c1
+    a64, _ = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=1e-300, maxit=30,
+                             prec="fp64")
+    aff, iff = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=1e-300, maxit=30,
+                               prec="ff")
+    assert iff["iters"] == 30
+    assert rel_err(aff, a64) < 1e-9
+    _, i64 = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=w.tol, prec="fp64")
+    aff, iff = K.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, f, tol=w.tol, prec="ff")
+    assert iff["status"] == "KRR_OK" and abs(iff["iters"] - i64["iters"]) <= 3
+    rr = O.true_relres(w.X, w.kernel, w.sigma, w.lam, w.Y, aff)
+    assert rr.max() < 2 * w.tol
+
+
 def test_mixed_solve_matches_oracle(K, c1):
     w, ref_f, f = c1
     ref = O.krr_pcg_solve(w.X, w.kernel, w.sigma, w.Y, w.mu, ref_f.F, tol=1e-12)
