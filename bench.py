@@ -53,9 +53,12 @@ def parse():
     ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma", "mma_sync"],
                     help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the product's default tile instead of tuning it in the warm-up")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the composed plain float64 GPU path (about 45 s)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "serving"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c3", "c4", "serving", "kmv"],
                     help="c2: one RPCholesky + refined PCG solve per step (headline); "
                          "c1: the plain float64 solve; c3: the batched 8-setting x 2-shift "
                          "product; c4: KRILL build + solve; "
@@ -156,7 +159,8 @@ class ClockSampler:
 # column splits of the FMA and mma.sync kernels, the epilogue variant of the
 # tcgen05 kernel.  Any other shape or tile has no capture and reports None; a
 # change to the kernel invalidates the entry until it is captured again.
-KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768}
+KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768,
+                 ("tensor", 0, 100_000, 16, 4, 3): 22_435_840 + 0}
 
 # Register-operand mma.sync (m16n8k16, f16 inputs, f32 accumulator) measured by
 # this repository's probe on this machine's GB300 (independent MMAs, 2-8 CTAs of
@@ -328,8 +332,9 @@ def run_native(args):
         info["entries"] = entries_rpcholesky(w.N, rank_) + info["kernel_entries"]
         return info
 
-    # the product's column tile is tuned during the first warm-up step
-    K.krr_set_autotune(True)
+    # the product's tile (epilogue variant / column splits) is tuned during the
+    # first warm-up step
+    K.krr_set_autotune(not args.no_autotune)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -809,10 +814,75 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_kmv(args):
+    """The float32 fused product alone on the headline inputs (N = 1e5, d = 16,
+    the 5 % near-duplicate workload, m = 4, Gaussian sigma = 0.5), each step one
+    krr_kmatvec, its product launch timed with the library's CUDA events
+    (krr_set_profiling / krr_profile_collect): the kernel the headline step
+    spends most of its time in, reported against its roofline.  The command
+    the ncu captures of the product use."""
+    import torch
+    import paper_2304_12465_gb300 as K
+    from inputs import make_c2_mixed
+
+    dist, rank, world = dist_setup(args.gpus)
+    K.load()
+    K.krr_set_product_path(args.product_path)
+    w = make_c2_mixed(n=args.n)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X = torch.from_numpy(w.X).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    V = torch.randn((w.m, w.N), dtype=torch.float64, device=dev, generator=gen)
+    for _ in range(args.warmup):
+        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    K.krr_set_profiling(True)
+    K.krr_profile_collect(0)
+    stream = torch.cuda.current_stream()
+    ms, launch_ms = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        t, n = K.krr_profile_collect(0)
+        launch_ms.append(t / max(n, 1))
+    K.krr_set_profiling(False)
+    clk = clocks.stop()
+    call_ms = float(np.median(ms))
+    kmv_ms = float(np.median(launch_ms))
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    tile = (K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)[0]
+            if args.product_path == "tensor" else K.krr_autotune_choice(w.kernel, w.d, w.m, w.N))
+    result = {"metric": "fused product (A + lambda I) V launch time", "value": kmv_ms,
+              "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": f"fused product, N={w.N}, d={w.d}, m={w.m}, Gaussian "
+                                     f"sigma={w.sigma}, 5% near-duplicates",
+                         "product_path": args.product_path},
+              "call_ms": call_ms,
+              "note": "value: the product kernel's launch (CUDA events around it on the "
+                      "launching stream, median over steps); call_ms adds the point "
+                      "preparation, the reduction and the float64 conversions of krr_kmatvec",
+              "roofline": product_roofline(args.product_path, w, kmv_ms, tile, sm_max),
+              "clocks": clk}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "kmv":
+        run_kmv(args)
     elif args.workload == "serving":
         run_serving(args)
     elif args.workload in ("c1", "c3", "c4"):

@@ -601,6 +601,13 @@ KRR_API krr_status krr_autotune_variant(krr_kernel kern, int d, int m, int64_t N
  * summed device time in krr_info.kmv_ms / kmv_launches. */
 KRR_API void krr_set_profiling(int on);
 
+/* Summed device time (ms) and number of the fused-product launches recorded  */
+/* while profiling was on and not yet collected by a solve: which = 0 the     */
+/* float32 product, 1 the float64 product, 2 the float-float product.  The    */
+/* collected launches are forgotten.  Synchronises the recorded events.       */
+/* KRR_EINVAL for another which or NULL outputs.                              */
+KRR_API krr_status krr_profile_collect(int which, double *ms, int *launches);
+
 /* Message for the last failure on the calling thread ("" if none). */
 KRR_API const char *krr_last_error(void);
 

@@ -29,6 +29,7 @@ from .api import (  # noqa: F401
     krr_set_product_variant,
     krr_autotune_variant,
     krr_set_profiling,
+    krr_profile_collect,
     krr_sparse_sign,
     krr_version,
 )

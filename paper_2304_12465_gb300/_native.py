@@ -138,6 +138,7 @@ SIGNATURES = {
     "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
     "krr_set_product_path": (_int, [_int]),
     "krr_set_product_variant": (_int, [_int]),
+    "krr_profile_collect": (_int, [_int, C.POINTER(C.c_double), C.POINTER(_int)]),
     "krr_autotune_variant": (_int, [_int, _int, _int, _i64, C.POINTER(_int),
                                     C.POINTER(C.c_float)]),
     "krr_set_profiling": (None, [_int]),

@@ -404,6 +404,15 @@ def krr_autotune_variant(kern, d: int, m: int, N: int):
     return v.value, [float(x) for x in ms]
 
 
+def krr_profile_collect(which: int = 0):
+    """(summed ms, launches) of the recorded product launches of one kind
+    (0 float32, 1 float64, 2 float-float) since profiling was switched on."""
+    ms, n = C.c_double(), C.c_int()
+    check(load().krr_profile_collect(int(which), C.byref(ms), C.byref(n)),
+          "krr_profile_collect")
+    return ms.value, n.value
+
+
 def krr_set_profiling(on: bool) -> None:
     load().krr_set_profiling(1 if on else 0)
 

@@ -236,6 +236,13 @@ krr_status krr_set_product_path(int path) {
   return KRR_OK;
 }
 
+krr_status krr_profile_collect(int which, double *ms, int *launches) {
+  clear_error();
+  KRR_REQUIRE(which >= 0 && which <= 2 && ms && launches, "bad profile query");
+  kmv_profile_collect(which, ms, launches);
+  return KRR_OK;
+}
+
 krr_status krr_set_product_variant(int variant) {
   clear_error();
   return set_tc5_variant(variant);
