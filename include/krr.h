@@ -576,23 +576,35 @@ KRR_API krr_status krr_set_product_path(int path);
 
 /* Epilogue variant of the tcgen05 product (KRR_PRODUCT_TENSOR): 0 (default)  */
 /* = chosen per shape by the autotuner while krr_set_autotune is on (every    */
-/* valid variant timed once on the caller's stream at the first product of   */
-/* the shape), else variant 3; 1 = 8 epilogue warps with the next columns.    */
-/* Tensor Memory loads in flight while the current ones are computed; 2 = 16  */
-/* epilogue warps; 3 = 8 warps without that overlap; 4 = 16 warps with it;    */
-/* 5 = 8 warps, software-pipelined by one batch of columns (the ex2 of one    */
-/* batch on the MUFU while the FFMA2 sums of the previous batch run); 6 = 12  */
-/* epilogue warps on 96-column tiles with the overlap; 7 = the same without.  */
-/* Variants 2, 4, 5, 6 and 7 serve m <= 4 per launch (larger m fall back to   */
-/* 1).  Results differ between variants at the rounding level only (the      */
-/* order in which column groups are summed).  Process-wide.  KRR_EINVAL       */
-/* outside 0..7.                                                              */
+/* valid variant timed once on the caller's stream at the first product of    */
+/* the shape), else variant 3 (9 for 5..8 right-hand sides per launch of a    */
+/* square product).  Variants 1..7 sum over the right-hand sides with FFMA2   */
+/* on the FMA pipe: 1 = 8 epilogue warps with the next columns' Tensor Memory */
+/* loads in flight while the current ones are computed; 2 = 16 epilogue       */
+/* warps; 3 = 8 warps without that overlap; 4 = 16 warps with it; 5 = 8       */
+/* warps, software-pipelined by one batch of columns (the ex2 of one batch on */
+/* the MUFU while the FFMA2 sums of the previous batch run); 6 = 12 epilogue  */
+/* warps on 96-column tiles with the overlap; 7 = the same without.  Variants */
+/* 8..11 take those sums on the tensor cores (mma.sync m16n8k16 on the kernel */
+/* values, scaled by 2^14 and split into fp16 halves, times the right-hand    */
+/* sides, scaled per column by a power of two and split likewise): 8 = 8      */
+/* warps with the overlap, 9 = 8 warps without, 10 = 16 warps without, 11 =   */
+/* 16 warps with.  Their error is 2^-22 of each term plus 2^-39 of the        */
+/* column's largest |v| per term (the FMA variants: 2^-24 of each term), so   */
+/* they serve square products (krr_kmatvec, the solvers) only; prediction and */
+/* the restricted products keep 1..7.  Variants 2, 4..7, 10 and 11 serve m <= */
+/* 4 per launch.  A forced variant that does not serve a launch leaves that   */
+/* launch to the autotuner or the default.  Results differ between variants   */
+/* at the rounding level only.  Process-wide.  KRR_EINVAL outside             */
+/* 0..KRR_PRODUCT_VARIANTS.                                                   */
+#define KRR_PRODUCT_VARIANTS 11
 KRR_API krr_status krr_set_product_variant(int variant);
 
 /* The autotuner's choice for the square tcgen05 product of a shape (kernel,  */
 /* d, m, N): *variant (0 if the shape has not been tuned) and, when ms is not */
-/* NULL, the measured launch time of each of the 7 variants in milliseconds   */
-/* (0 for a variant that was not timed).                                      */
+/* NULL, the measured launch time of each of the KRR_PRODUCT_VARIANTS         */
+/* variants in milliseconds (ms[v - 1] for variant v; 0 for a variant that    */
+/* was not timed).                                                            */
 KRR_API krr_status krr_autotune_variant(krr_kernel kern, int d, int m, int64_t N, int *variant,
                                         float *ms);
 

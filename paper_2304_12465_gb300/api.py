@@ -390,6 +390,10 @@ def krr_set_product_path(path) -> None:
     check(load().krr_set_product_path(int(code)), "krr_set_product_path")
 
 
+# Epilogue variants of the tcgen05 product (KRR_PRODUCT_VARIANTS in krr.h).
+PRODUCT_VARIANTS = 11
+
+
 def krr_set_product_variant(variant: int) -> None:
     """Epilogue variant of the tcgen05 product (0: autotuned / default)."""
     check(load().krr_set_product_variant(int(variant)), "krr_set_product_variant")
@@ -398,7 +402,7 @@ def krr_set_product_variant(variant: int) -> None:
 def krr_autotune_variant(kern, d: int, m: int, N: int):
     """(chosen variant or 0, per-variant launch times in ms) for a shape."""
     v = C.c_int()
-    ms = (C.c_float * 7)()
+    ms = (C.c_float * PRODUCT_VARIANTS)()
     check(load().krr_autotune_variant(_kern(kern), int(d), int(m), int(N), C.byref(v), ms),
           "krr_autotune_variant")
     return v.value, [float(x) for x in ms]

@@ -257,11 +257,11 @@ krr_status krr_autotune_variant(krr_kernel kern, int d, int m, int64_t N, int *v
   const int mg = m > 8 ? 8 : m;
   const int M = mg <= 2 ? 2 : mg <= 4 ? 4 : 8;
   int best = 0;
-  float t[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  float t[KRR_PRODUCT_VARIANTS] = {};
   if (!tc5_tuned((int)kern, d, M, N, &best, t)) best = 0;
   *variant = best;
   if (ms)
-    for (int v = 0; v < 7; ++v) ms[v] = t[v];
+    for (int v = 0; v < KRR_PRODUCT_VARIANTS; ++v) ms[v] = t[v];
   return KRR_OK;
 }
 

@@ -21,10 +21,11 @@ namespace krr {
 // (kb = 2 nh + csep blocks of 16 halves each, stored K-block-major: block q
 // of point i at (q N + i) 16).  A coordinate or c outside the split's range
 // sets *bad.
+// cshift is added to c on both sides (7 for the Gaussian: D = log2 kappa + 14).
 __global__ void prepare_tc5_kernel(const double *__restrict__ X, int64_t N, int d, int nh,
                                    int csep, const double *__restrict__ mean, double scale,
-                                   __half *__restrict__ xa, __half *__restrict__ xb,
-                                   int *__restrict__ bad) {
+                                   double cshift, __half *__restrict__ xa,
+                                   __half *__restrict__ xb, int *__restrict__ bad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   // element t of block q of this point
@@ -44,7 +45,7 @@ __global__ void prepare_tc5_kernel(const double *__restrict__ X, int64_t N, int 
     at(xa, nh + k / 16, k % 16) = l;
     at(xb, nh + k / 16, k % 16) = l;
   }
-  const double c = -0.5 * nrm;
+  const double c = -0.5 * nrm + cshift;
   if (!(fabs(c) <= (double)T5_MAX_C)) out_of_range = true;
   const __half c1 = __double2half(c);
   const double r1 = c - (double)__half2float(c1);
@@ -122,7 +123,8 @@ krr_status prepare_points_tc5(const double *Xd, cudaStream_t s, PointsF32 &P, in
   KRR_TRY(bad.alloc(1, s));
   KRR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
   prepare_tc5_kernel<<<ceil_div(P.N, 256), 256, 0, s>>>(
-      Xd, P.N, P.d, nh, csep, P.mean.p, scale, reinterpret_cast<__half *>(P.xa5.p),
+      Xd, P.N, P.d, nh, csep, P.mean.p, scale, P.kern == KGAUSS ? 7.0 : 0.0,
+      reinterpret_cast<__half *>(P.xa5.p),
       reinterpret_cast<__half *>(P.xb5.p), bad.p);
   KRR_LAUNCH_CHECK();
   int h_bad = 0;
@@ -179,9 +181,9 @@ krr_status tc5_check_fault(cudaStream_t s) {
 
 // ------------------------------------------------------------ reduction
 __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int m, int M, int C,
-                                 int64_t T, int G, int J, int CG, float lambda,
-                                 const float *__restrict__ V, int64_t ldv, float *__restrict__ Y,
-                                 int64_t ldy) {
+                                 int64_t T, int G, int J, int CG, const int *__restrict__ vexp,
+                                 float lambda, const float *__restrict__ V, int64_t ldv,
+                                 float *__restrict__ Y, int64_t ldy) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nr) return;
   const int64_t rb = i / T5_RB;
@@ -195,6 +197,7 @@ __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int
       for (int cg = 0; cg < CG; ++cg)
         acc += (double)part[((((int64_t)b * J + j) * CG + cg) * M + c) * T5_RB + r];
     }
+    if (vexp) acc = ldexp(acc, -14 - vexp[c]);
     Y[(int64_t)c * ldy + i] =
         V ? (float)(acc + (double)lambda * (double)V[(int64_t)c * ldv + i]) : (float)acc;
   }
@@ -202,9 +205,11 @@ __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int
 
 // Right-hand sides of the column points as the kernel's shared tiles hold
 // them: for column tile t (of TN points), pair cp and column jl, {v_2cp,
-// v_2cp, v_2cp+1, v_2cp+1} of point t TN + jl (zero beyond Nc or m).
+// v_2cp, v_2cp+1, v_2cp+1} of point t TN + jl times vscale (zero beyond Nc
+// or m); vscale = 2^-14 for the Gaussian, whose kernel values come scaled by
+// 2^14.
 __global__ void t5_vdup_kernel(const float *__restrict__ V, int64_t ldv, int64_t Nc, int m,
-                               int MP, int C, int TN, float4 *__restrict__ vdup) {
+                               int MP, int C, int TN, float vscale, float4 *__restrict__ vdup) {
   const int64_t total = (int64_t)C * MP * TN;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -214,10 +219,94 @@ __global__ void t5_vdup_kernel(const float *__restrict__ V, int64_t ldv, int64_t
     const int64_t j = t * TN + jl;
     float va = 0.0f, vb = 0.0f;
     if (j < Nc) {
-      if (2 * cp < m) va = V[(int64_t)(2 * cp) * ldv + j];
-      if (2 * cp + 1 < m) vb = V[(int64_t)(2 * cp + 1) * ldv + j];
+      if (2 * cp < m) va = V[(int64_t)(2 * cp) * ldv + j] * vscale;
+      if (2 * cp + 1 < m) vb = V[(int64_t)(2 * cp + 1) * ldv + j] * vscale;
     }
     vdup[e] = make_float4(va, va, vb, vb);
+  }
+}
+
+// Largest |v| of each right-hand side (m <= 8) over this block's grid-stride
+// share of the Nc points: bmax[block][c].
+constexpr int T5_VMAX_BLOCKS = 256;
+__global__ void t5_vmax_kernel(const float *__restrict__ V, int64_t ldv, int64_t Nc, int m,
+                               float *__restrict__ bmax) {
+  __shared__ float red[8][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < 8; ++c) {
+    float mx = 0.0f;
+    if (c < m)
+      for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < Nc;
+           j += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(V[(int64_t)c * ldv + j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp][c] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    float mx = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w][threadIdx.x]);
+    bmax[blockIdx.x * 8 + threadIdx.x] = mx;
+  }
+}
+
+__device__ __forceinline__ uint32_t t5_pack_halves(__half lo, __half hi) {
+  return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+
+// Right-hand sides as mma.sync B fragments for the TV variants.  Column c is
+// scaled by s_c = 2^vexp[c], the power of two that brings its largest |v|
+// into [2^13, 2^14), and split into fp16 halves v s_c = v_hi + v_lo.  B slot n
+// of fragment f: v_hi of column n (n < M) and v_lo of column n - M (M <= n <
+// 2M) for M <= 4; v_hi (f = 0) or v_lo (f = 1) of column n for M = 8.  For
+// column tile t, batch bt of 16 columns, fragment f and lane 4 g + q, frag
+// holds {B(2q, g), B(2q + 1, g)}, {B(2q + 8, g), B(2q + 9, g)} over the
+// batch's columns (zero beyond Nc, m or 2M).  Every block derives the scales
+// from bmax (gmax blocks); block 0 also stores vexp for the reduction.
+__global__ void t5_vfrag_kernel(const float *__restrict__ V, int64_t ldv, int64_t Nc, int m,
+                                int M, int C, int TN, const float *__restrict__ bmax, int gmax,
+                                uint2 *__restrict__ frag, int *__restrict__ vexp) {
+  __shared__ float sc[8];
+  if (threadIdx.x < 8) {
+    float mx = 0.0f;
+    for (int q = 0; q < gmax; ++q) mx = fmaxf(mx, bmax[q * 8 + threadIdx.x]);
+    int e = 0;
+    if (mx > 0.0f && mx <= 3.4028234663852886e38f) {
+      int E = 0;
+      frexpf(mx, &E);   // mx < 2^E
+      e = min(max(14 - E, -126), 126);
+    }
+    sc[threadIdx.x] = ldexpf(1.0f, e);
+    if (blockIdx.x == 0) vexp[threadIdx.x] = e;
+  }
+  __syncthreads();
+  const int NB = (M == 8) ? 2 : 1;
+  const int nbat = TN / 16;
+  const int64_t total = (int64_t)C * nbat * NB * 32;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = (int)(e % 32);
+    const int f = (int)((e / 32) % NB);
+    const int bt = (int)((e / (32 * NB)) % nbat);
+    const int64_t t = e / ((int64_t)32 * NB * nbat);
+    const int g = lane >> 2, q = lane & 3;
+    int c = g;
+    bool lo = (f == 1), live = true;
+    if (NB == 1) {
+      lo = g >= M;
+      c = lo ? g - M : g;
+      live = g < 2 * M;
+    }
+    const int64_t j0 = t * TN + bt * 16;
+    auto slot = [&](int k) -> __half {
+      const int64_t j = j0 + k;
+      if (!live || c >= m || j >= Nc) return __float2half_rn(0.0f);
+      const float vs = V[(int64_t)c * ldv + j] * sc[c];
+      const __half h = __float2half_rn(vs);
+      return lo ? __float2half_rn(vs - __half2float(h)) : h;
+    };
+    frag[e] = make_uint2(t5_pack_halves(slot(2 * q), slot(2 * q + 1)),
+                         t5_pack_halves(slot(2 * q + 8), slot(2 * q + 9)));
   }
 }
 
@@ -227,14 +316,18 @@ __global__ void t5_vdup_kernel(const float *__restrict__ V, int64_t ldv, int64_t
 // the first product of that shape while autotuning is on, else the default.
 // Results of different variants differ only in the summation order of the
 // column groups (rounding level).
-constexpr int T5_DEFAULT_VARIANT = 3;
+static_assert(T5_NVARIANTS == KRR_PRODUCT_VARIANTS, "variant count of the ABI");
+// Untuned default: the FMA sums (3) up to 4 right-hand sides per launch, the
+// tensor-core sums (9) for 5..8, where they measured 2.96 ms against 4.35 ms
+// per product at N = 1e5, d = 16.
+static int t5_default_variant(int M, bool square) { return (M == 8 && square) ? 9 : 3; }
 static std::atomic<int> g_t5_variant{0};
 static std::mutex g_t5_mtx;
 struct T5Tune {
   int best = 0;
   float ms[T5_NVARIANTS + 1] = {};
 };
-static std::map<std::tuple<int, int, int, int, int64_t, int64_t>, T5Tune> g_t5_tuned;
+static std::map<std::tuple<int, int, int, int, int64_t, int64_t, bool>, T5Tune> g_t5_tuned;
 
 krr_status set_tc5_variant(int v) {
   KRR_REQUIRE(v >= 0 && v <= T5_NVARIANTS, "unknown product variant %d", v);
@@ -245,7 +338,7 @@ krr_status set_tc5_variant(int v) {
 bool tc5_tuned(int kern, int d, int M, int64_t N, int *best, float *ms) {
   const int nh = t5_nh(d), csep = t5_csep(d);
   std::lock_guard<std::mutex> lk(g_t5_mtx);
-  auto it = g_t5_tuned.find(std::make_tuple(kern, nh, csep, M, N, N));
+  auto it = g_t5_tuned.find(std::make_tuple(kern, nh, csep, M, N, N, true));
   if (it == g_t5_tuned.end()) return false;
   *best = it->second.best;
   if (ms)
@@ -275,10 +368,18 @@ static T5Geometry t5_geometry(int64_t Nr, int64_t Nc, int TN) {
   return g;
 }
 
-// Scratch of one launch: partial sums (room for 4 column groups), then the
-// right-hand-side quadruples (16-byte aligned).
+// Scratch of one launch: partial sums (room for 4 column groups), the
+// right-hand-side quadruples or B fragments (16-byte aligned), the block
+// maxima of V and the scale exponents (TV variants).
+static size_t t5_npart(const T5Geometry &g, int M) { return (size_t)g.G * g.J * 4 * M * T5_RB; }
+static size_t t5_nvdup(const T5Geometry &g, int M) {
+  return (size_t)g.C * g.TN * 4 * (M / 2);   // quadruples, or (fewer) B fragments
+}
 static size_t t5_scratch_floats(const T5Geometry &g, int M) {
-  return (size_t)g.G * g.J * 4 * M * T5_RB + (size_t)g.C * (M / 2) * g.TN * 4;
+  return t5_npart(g, M) + t5_nvdup(g, M) + T5_VMAX_BLOCKS * 8 + 8;
+}
+static int *t5_vexp(float *part, const T5Geometry &g, int M) {
+  return reinterpret_cast<int *>(part + t5_npart(g, M) + t5_nvdup(g, M) + T5_VMAX_BLOCKS * 8);
 }
 
 // Stages V for this geometry and launches the product; returns the launch's
@@ -286,55 +387,75 @@ static size_t t5_scratch_floats(const T5Geometry &g, int M) {
 static cudaError_t t5_launch(const PointsF32 &R, const PointsF32 &P, int M, int variant,
                              const T5Geometry &g, const float *Vg, int64_t ldv, int mg,
                              float *part, int *fault, cudaStream_t s, bool timed) {
-  const size_t npart = (size_t)g.G * g.J * 4 * M * T5_RB;
-  float4 *vdup = reinterpret_cast<float4 *>(part + npart);
-  const int64_t total = (int64_t)g.C * (M / 2) * g.TN;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  t5_vdup_kernel<<<blocks, 256, 0, s>>>(Vg, ldv, P.N, mg, M / 2, g.C, g.TN, vdup);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
+  float *vbuf = part + t5_npart(g, M);
+  cudaError_t e = cudaSuccess;
+  if (t5_variant_tv(variant)) {
+    float *bmax = vbuf + t5_nvdup(g, M);
+    const int gmax = (int)std::min<int64_t>((P.N + 255) / 256, T5_VMAX_BLOCKS);
+    t5_vmax_kernel<<<gmax, 256, 0, s>>>(Vg, ldv, P.N, mg, bmax);
+    count_launch();
+    const int NB = (M == 8) ? 2 : 1;
+    const int64_t total = (int64_t)g.C * (g.TN / 16) * NB * 32;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    t5_vfrag_kernel<<<blocks, 256, 0, s>>>(Vg, ldv, P.N, mg, M, g.C, g.TN, bmax, gmax,
+                                           reinterpret_cast<uint2 *>(vbuf), t5_vexp(part, g, M));
+    count_launch();
+  } else {
+    const int64_t total = (int64_t)g.C * (M / 2) * g.TN;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    t5_vdup_kernel<<<blocks, 256, 0, s>>>(Vg, ldv, P.N, mg, M / 2, g.C, g.TN,
+                                          P.kern == KGAUSS ? 0x1p-14f : 1.0f,
+                                          reinterpret_cast<float4 *>(vbuf));
+    count_launch();
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const T5Args args{vdup, P.N, part, g.C, g.T, g.J, fault};
+  const T5Args args{reinterpret_cast<const float4 *>(vbuf), P.N, part, g.C, g.T, g.J, fault};
   const int nh = P.nh5, csep = P.csep5, kb = t5_kb(nh, csep);
   // at least half of an SM's shared memory: one CTA per SM (each takes all
   // 512 TMEM columns)
   const size_t smem = std::max<size_t>(t5_smem_bytes(kb, M), 116 * 1024);
+  const bool tv = t5_variant_tv(variant), gauss = P.kern == KGAUSS;
   KmvTimer tm;
   if (timed) tm.begin(s);
-  e = (P.kern == KGAUSS)
-          ? launch_kmvtc5_gauss(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args)
-          : launch_kmvtc5_matern(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args);
+  if (tv)
+    e = gauss ? launch_kmvtc5_tv_gauss(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args)
+              : launch_kmvtc5_tv_matern(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args);
+  else
+    e = gauss ? launch_kmvtc5_gauss(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args)
+              : launch_kmvtc5_matern(nh, csep, M, variant, g.G, smem, s, R.ma5, P.mb5, args);
   if (timed) tm.end(s);
   count_launch();
   return e;
 }
 
 // Variant for this product: forced, cached, tuned now, or the default.
-static int choose_variant(const PointsF32 &R, const PointsF32 &P, int M, const float *Vg,
+static int choose_variant(const PointsF32 &R, const PointsF32 &P, bool square, int M,
+                          const float *Vg,
                           int64_t ldv, int mg, DevBuf<float> &part, int *fault, cudaStream_t s) {
   const int forced = g_t5_variant.load();
-  if (forced > 0 && t5_variant_valid(forced, M)) return forced;
-  const auto key = std::make_tuple(P.kern, P.nh5, P.csep5, M, R.N, P.N);
+  if (forced > 0 && t5_variant_valid(forced, M, square)) return forced;
+  const auto key = std::make_tuple(P.kern, P.nh5, P.csep5, M, R.N, P.N, square);
   {
     std::lock_guard<std::mutex> lk(g_t5_mtx);
     auto it = g_t5_tuned.find(key);
     if (it != g_t5_tuned.end()) return it->second.best;
   }
-  if (!autotune_on()) return T5_DEFAULT_VARIANT;
+  if (!autotune_on()) return t5_default_variant(M, square);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-    return T5_DEFAULT_VARIANT;   // timing would synchronise a capturing stream
+    return t5_default_variant(M, square);   // timing would synchronise a capturing stream
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     cudaGetLastError();
-    return T5_DEFAULT_VARIANT;
+    return t5_default_variant(M, square);
   }
   T5Tune tune;
   float best_ms = 1e30f;
-  tune.best = T5_DEFAULT_VARIANT;
+  tune.best = t5_default_variant(M, square);
   for (int v = 1; v <= T5_NVARIANTS; ++v) {
-    if (!t5_variant_valid(v, M)) continue;
+    if (!t5_variant_valid(v, M, square)) continue;
     const T5Geometry g = t5_geometry(R.N, P.N, t5_variant_tn(v));
     const size_t need = t5_scratch_floats(g, M);
     if (part.n < need && part.alloc(need, s) != KRR_OK) break;
@@ -377,7 +498,7 @@ krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool sq
     const int mg = std::min(8, m - c0);
     const int M = mg <= 2 ? 2 : mg <= 4 ? 4 : 8;
     const float *Vg = V + (int64_t)c0 * ldv;
-    const int variant = choose_variant(R, P, M, Vg, ldv, mg, part, fault, s);
+    const int variant = choose_variant(R, P, square, M, Vg, ldv, mg, part, fault, s);
     const T5Geometry g = t5_geometry(Nr, Nc, t5_variant_tn(variant));
     const size_t need = t5_scratch_floats(g, M);
     if (part.n < need) KRR_TRY(part.alloc(need, s));
@@ -387,9 +508,10 @@ krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool sq
       return KRR_ECUDA;
     }
     const int CG = t5_variant_ew(variant) / 4;
-    t5_reduce_kernel<<<ceil_div(Nr, 256), 256, 0, s>>>(part.p, Nr, mg, M, g.C, g.T, g.G, g.J, CG,
-                                                       lambda, square ? Vg : nullptr, ldv,
-                                                       Y + (int64_t)c0 * ldy, ldy);
+    t5_reduce_kernel<<<ceil_div(Nr, 256), 256, 0, s>>>(
+        part.p, Nr, mg, M, g.C, g.T, g.G, g.J, CG,
+        t5_variant_tv(variant) ? t5_vexp(part.p, g, M) : nullptr, lambda, square ? Vg : nullptr,
+        ldv, Y + (int64_t)c0 * ldy, ldy);
     KRR_LAUNCH_CHECK();
   }
   return KRR_OK;

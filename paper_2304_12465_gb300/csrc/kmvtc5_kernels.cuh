@@ -6,7 +6,10 @@
 //
 // Arithmetic.  Points are centred and scaled as for the float32 FMA product,
 // so that kappa = 2^D (Gaussian) or D = -q^2/2 (Matern) with
-// D = x_i . x_j + c_i + c_j and c = -|x|^2 / 2.  Each coordinate is split
+// D = x_i . x_j + c_i + c_j and c = -|x|^2 / 2; the Gaussian's operands carry
+// c + 7 instead of c, so that its D is log2 kappa + 14 and ex2 gives the
+// kernel value scaled by 2^14 (the FMA variants multiply by V scaled by
+// 2^-14, exactly; the TV variants need the headroom).  Each coordinate is split
 // into two halves x = h + l (h = fp16(x), l = fp16(x - h), |x - h - l| <=
 // 2^-22 |x|) and c into three fp16 pieces c1 + c2 + c3.  Each point has
 // 16-wide K-blocks [H_0..H_{NH-1} | L_0..L_{NH-1} | C], stored K-block-major
@@ -53,6 +56,8 @@
 // and the CTA waits (bounded) for its own TMA copies and MMAs in flight and
 // frees its Tensor Memory before returning.
 #pragma once
+
+#include <cuda_fp16.h>
 
 #include "blackwell.cuh"
 #include "kmv_kernels.cuh"
@@ -115,6 +120,40 @@ __device__ __forceinline__ float t5_kappa(uint32_t d) {
   return kappa_f32<KERN>(__uint_as_float(d));
 }
 
+// 2^14 kappa for the tensor-core sums (TV variants): the Gaussian's operands
+// carry the factor in their c-parts (D = log2 kappa + 14), the Matern
+// polynomial is scaled instead.
+template <int KERN>
+__device__ __forceinline__ float t5_kappa_scaled(uint32_t d) {
+  if constexpr (KERN == KMATERN) {
+    const float q = sqrt_approx(fmaxf(-2.0f * __uint_as_float(d), 0.0f));
+    const float e = ex2_approx(-1.4426950408889634f * q);
+    return fmaf(q, fmaf(q, 5461.3335f, 16384.0f), 16384.0f) * e;
+  } else {
+    return ex2_approx(__uint_as_float(d));
+  }
+}
+
+// Splits two non-negative values k0, k1 into fp16 halves k = hi + lo: hi keeps
+// the leading 11 significant bits (exact in fp16 for k >= 2^-14), lo = k - hi
+// (exact in float32) rounded to fp16; packed with k0 in the low half.
+__device__ __forceinline__ void t5_split_pair(float k0, float k1, uint32_t &hi, uint32_t &lo) {
+  const float h0 = __uint_as_float(__float_as_uint(k0) & 0xFFFFE000u);
+  const float h1 = __uint_as_float(__float_as_uint(k1) & 0xFFFFE000u);
+  const float2 l = __ffma2_rn(f2(h0, h1), f2(-1.0f, -1.0f), f2(k0, k1));
+  const __half2 hh = __floats2half2_rn(h0, h1), ll = __floats2half2_rn(l.x, l.y);
+  hi = *reinterpret_cast<const uint32_t *>(&hh);
+  lo = *reinterpret_cast<const uint32_t *>(&ll);
+}
+
+__device__ __forceinline__ void t5_mma_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
 // Epilogue variants: EW epilogue warps (8, 12 or 16; EW / 4 column groups of
 // TN / (EW / 4) columns per tile, TN the column tile: 128, or 96 for 12
 // warps), PIPE = 1 keeps the TMEM loads of the
@@ -122,8 +161,18 @@ __device__ __forceinline__ float t5_kappa(uint32_t d) {
 // (with PIPE) software-pipelines the epilogue by one batch of 16 columns:
 // the kernel values (ex2 on the MUFU) of batch b are formed while the FFMA2
 // accumulation of batch b - 1 runs on the FMA pipe, across tile boundaries,
-// so that the two pipes work at the same time instead of in turn.
-template <int KERN, int NH, int CSEP, int M, int EW, int PIPE, int LAG, int TN>
+// so that the two pipes work at the same time instead of in turn.  TV = 1
+// takes the sums over the right-hand sides on the tensor cores instead of the
+// FMA pipe: the 16x256b TMEM layout of a batch of 16 columns is the A-operand
+// fragment layout of mma.sync m16n8k16, so each kernel value, scaled by 2^14
+// and split into fp16 halves hi + lo, enters two MMAs (A = hi, A = lo) whose
+// B operand holds the right-hand sides split likewise, v s_c = v_hi + v_lo
+// with a power-of-two scale s_c per right-hand side (t5_vfrag_kernel): B
+// slots 0..M-1 the v_hi, M..2M-1 the v_lo (M <= 4), or one fragment of each
+// (M = 8).  Products of fp16 halves are exact in float32, so the result is
+// (hi + lo)(v_hi + v_lo) summed in float32 per tile, then added to the
+// segment total (two levels, as the FMA variants).
+template <int KERN, int NH, int CSEP, int M, int EW, int PIPE, int LAG, int TN, int TV = 0>
 __global__ void __launch_bounds__((EW + 2) * 32, 1)
 kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
               const __grid_constant__ CUtensorMap colmap, const T5Args a) {
@@ -132,6 +181,8 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
   constexpr int T5_TN = TN;
   constexpr int KB = 2 * NH + CSEP;
   constexpr int MP = M / 2;   // right-hand-side pairs
+  constexpr int NB = (M == 8) ? 2 : 1;   // B fragments per batch (TV)
+  constexpr int VQ = TV ? NB : MP;       // 16-byte right-hand-side words per column
   constexpr int T5_ST = t5_stages(KB, M);
   constexpr int T5_BAR_A_FULL = t5_bar_a_full();
   constexpr int T5_BAR_A_EMPTY = t5_bar_a_empty();
@@ -208,7 +259,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
   if (warp == T5_PRODUCER_WARP) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      constexpr uint32_t VBYTES = MP * T5_TN * 16;
+      constexpr uint32_t VBYTES = VQ * T5_TN * 16;
       int64_t kt = 0, issued_b = 0;
       int issued_a = 0;
       int64_t rb = rb_first;
@@ -228,7 +279,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
         if (!wait(T5_BAR_B_EMPTY + s, ph ^ 1u) || !wait(T5_BAR_V_EMPTY + s, ph ^ 1u)) break;
         bw::mbar_arrive_expect_tx(bar(T5_BAR_B_FULL + s), KB * T5_BLK + VBYTES);
         bw::tma_load_3d(sB + s * KB * T5_BLK, &colmap, bar(T5_BAR_B_FULL + s), 0, ct * T5_TN, 0);
-        bw::bulk_load(base + vOff + (uint32_t)s * VBYTES, a.vdup + (size_t)ct * MP * T5_TN,
+        bw::bulk_load(base + vOff + (uint32_t)s * VBYTES, a.vdup + (size_t)ct * VQ * T5_TN,
                       VBYTES, bar(T5_BAR_B_FULL + s));
         ++issued_b;
       }
@@ -318,7 +369,121 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           }
     };
     constexpr int NBT = T5_WCOLS / 16;   // batches of 16 columns per tile
-    if constexpr (LAG) {
+    if constexpr (TV) {
+      constexpr int NG = T5_RT * 2;      // m16 row groups of a warp: (row tile, half)
+      float yacc[NG][NB][4], ytot[NG][NB][4];
+#pragma unroll
+      for (int gr = 0; gr < NG; ++gr)
+#pragma unroll
+        for (int f = 0; f < NB; ++f)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) yacc[gr][f][i] = ytot[gr][f][i] = 0.0f;
+      int64_t kt = 0, rb = rb_first;
+      int ct = ct_first;
+      for (int64_t p = p_begin; p < p_end; ++p, ++kt, (++ct == a.C ? (ct = 0, ++rb) : 0)) {
+        const int s = (int)(kt % T5_ST);
+        const int buf = (int)(kt & 1);
+        const bool ok = __all_sync(0xffffffffu, wait(T5_BAR_D_FULL + buf, (uint32_t)((kt >> 1) & 1)) &&
+                                                    wait(T5_BAR_B_FULL + s, (uint32_t)((kt / T5_ST) & 1)));
+        if (!ok) break;
+        bw::tc_fence_after();
+        const uint2 *vf = reinterpret_cast<const uint2 *>(sV + (size_t)s * VQ * T5_TN);
+        const uint32_t tcol = tmem + (uint32_t)(buf * T5_RT * T5_TN + cg * T5_WCOLS);
+        uint32_t r[PIPE ? 2 : 1][32];   // [batch parity][row group][8]
+        auto load_batch = [&](int bt, uint32_t *rr) {
+#pragma unroll
+          for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf)
+              bw::tmem_ld_16x256b_x2(tcol + ((uint32_t)(32 * qd + 16 * hf) << 16) +
+                                         (uint32_t)(rt * T5_TN + bt * 16),
+                                     &rr[(rt * 2 + hf) * 8]);
+        };
+        auto release_buffer = [&]() {
+          bw::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) bw::mbar_arrive(bar(T5_BAR_D_EMPTY + buf));
+        };
+        if (PIPE) {
+          load_batch(0, r[0]);
+          bw::tmem_wait_ld32(r[0]);
+          if (NBT == 1) release_buffer();
+        }
+#pragma unroll
+        for (int bt = 0; bt < NBT; ++bt) {
+          uint32_t *cur = r[PIPE ? (bt & 1) : 0];
+          if (PIPE) {
+            if (bt + 1 < NBT) load_batch(bt + 1, r[(bt + 1) & 1]);
+          } else {
+            load_batch(bt, cur);
+            bw::tmem_wait_ld32(cur);
+            if (bt + 1 == NBT) release_buffer();
+          }
+          uint2 bf[NB];
+#pragma unroll
+          for (int f = 0; f < NB; ++f) bf[f] = vf[((cg * NBT + bt) * NB + f) * 32 + lane];
+#pragma unroll
+          for (int gr = 0; gr < NG; ++gr) {
+            // registers (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1), then the
+            // same for columns 8..15: fragments a0..a3 in order
+            const uint32_t *q = &cur[gr * 8];
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int pr = 0; pr < 4; ++pr)
+              t5_split_pair(t5_kappa_scaled<KERN>(q[2 * pr]), t5_kappa_scaled<KERN>(q[2 * pr + 1]),
+                            ah[pr], al[pr]);
+#pragma unroll
+            for (int f = 0; f < NB; ++f) {
+              t5_mma_16816(yacc[gr][f], al, bf[f]);
+              t5_mma_16816(yacc[gr][f], ah, bf[f]);
+            }
+          }
+          if (PIPE && bt + 1 < NBT) {
+            bw::tmem_wait_ld32(r[(bt + 1) & 1]);
+            if (bt + 2 == NBT) release_buffer();
+          }
+        }
+#pragma unroll
+        for (int gr = 0; gr < NG; ++gr)
+#pragma unroll
+          for (int f = 0; f < NB; ++f)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              ytot[gr][f][i] += yacc[gr][f][i];
+              yacc[gr][f][i] = 0.0f;
+            }
+        __syncwarp();
+        if (lane == 0) bw::mbar_arrive(bar(T5_BAR_V_EMPTY + s));
+        if (p + 1 == p_end || ct + 1 == a.C) {
+          // end of a segment: accumulator (g, 2t + e) / (g + 8, 2t + e) holds
+          // B slot 2t + e; add each v_hi slot's v_lo partner and write this
+          // warp's partial sums (scaled by 2^14 s_c; t5_reduce_kernel undoes it)
+          const int j = (int)(rb - rb_first);
+          float *out = a.part + (((int64_t)b * a.J + j) * T5_CG + cg) * (int64_t)M * T5_RB;
+#pragma unroll
+          for (int gr = 0; gr < NG; ++gr) {
+            float y[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              if constexpr (NB == 2)
+                y[i] = ytot[gr][0][i] + ytot[gr][1][i];
+              else
+                y[i] = ytot[gr][0][i] + __shfl_xor_sync(0xffffffffu, ytot[gr][0][i], M / 2);
+#pragma unroll
+              for (int f = 0; f < NB; ++f) ytot[gr][f][i] = 0.0f;
+            }
+            const int c0 = 2 * tq;
+            if (c0 < M) {
+              const int row = (gr >> 1) * T5_TM + 32 * qd + 16 * (gr & 1) + g;
+              out[c0 * T5_RB + row] = y[0];
+              out[(c0 + 1) * T5_RB + row] = y[1];
+              out[c0 * T5_RB + row + 8] = y[2];
+              out[(c0 + 1) * T5_RB + row + 8] = y[3];
+            }
+          }
+        }
+      }
+    } else if constexpr (LAG) {
       // segment end: the four lanes of a row group hold sums over different
       // columns; add them and write this warp's partial sums
       auto flush = [&](int64_t rbq) {
@@ -572,10 +737,12 @@ __host__ __device__ inline int t5_cta_of(int64_t p, int64_t T, int G) {
 
 // Y[c][i] = sum of the partial sums of row i over the CTAs covering its row
 // block (CTA order) and column groups, + lambda V[c][i] when V is given.
+// With vexp (TV variants) the partial sums of right-hand side c carry the
+// factor 2^(14 + vexp[c]), which is divided out in float64.
 __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int m, int M, int C,
-                                 int64_t T, int G, int J, int CG, float lambda,
-                                 const float *__restrict__ V, int64_t ldv, float *__restrict__ Y,
-                                 int64_t ldy);
+                                 int64_t T, int G, int J, int CG, const int *__restrict__ vexp,
+                                 float lambda, const float *__restrict__ V, int64_t ldv,
+                                 float *__restrict__ Y, int64_t ldy);
 
 }  // namespace krr
 
@@ -584,69 +751,96 @@ namespace krr {
 // Epilogue variants of the tcgen05 product: 1 = 8 warps with pipelined TMEM
 // loads, 2 = 16 warps, 3 = 8 warps without the pipelining, 4 = 16 warps with
 // it, 5 = 8 warps, pipelined and software-pipelined by one batch, 6 = 12 warps
-// on 96-column tiles with pipelined loads, 7 = the same without (the 12- and
-// 16-warp and software-pipelined variants serve M <= 4 only).
-constexpr int T5_NVARIANTS = 7;
+// on 96-column tiles with pipelined loads, 7 = the same without; 8..11 take
+// the sums over V on the tensor cores (TV): 8 = 8 warps with pipelined loads,
+// 9 = 8 warps without, 10 = 16 warps without, 11 = 16 warps with.  The 12-
+// and 16-warp and software-pipelined variants serve M <= 4 only.
+constexpr int T5_NVARIANTS = 11;
+__host__ __device__ constexpr bool t5_variant_tv(int v) { return v >= 8; }
 __host__ __device__ constexpr int t5_variant_ew(int v) {
-  return (v == 2 || v == 4) ? 16 : (v >= 6 ? 12 : 8);
+  return (v == 2 || v == 4 || v == 10 || v == 11) ? 16 : ((v == 6 || v == 7) ? 12 : 8);
 }
-__host__ __device__ constexpr int t5_variant_tn(int v) { return v >= 6 ? 96 : 128; }
-inline bool t5_variant_valid(int v, int M) {
-  return v >= 1 && v <= T5_NVARIANTS && (v == 1 || v == 3 || M <= 4);
+__host__ __device__ constexpr int t5_variant_tn(int v) { return (v == 6 || v == 7) ? 96 : 128; }
+// The tensor-core sums serve square products only: there every row's largest
+// kernel value is kappa_ii = 1, while a rectangular product (prediction,
+// restricted KRR) may have rows whose kernel values all lie below 2^-20,
+// where their fp16 halves (even scaled by 2^14) keep too few bits.
+inline bool t5_variant_valid(int v, int M, bool square) {
+  return v >= 1 && v <= T5_NVARIANTS && (v == 1 || v == 3 || v == 8 || v == 9 || M <= 4) &&
+         (square || !t5_variant_tv(v));
 }
 
 // Launches the instance for (nh, csep, M, variant); cudaErrorInvalidValue for
-// a shape without one.  Defined per kernel function in kmvtc5_gauss.cu /
-// kmvtc5_matern.cu.
+// a shape without one.  Defined per kernel function and family (TV or not) in
+// kmvtc5_gauss.cu, kmvtc5_matern.cu, kmvtc5_tv_gauss.cu, kmvtc5_tv_matern.cu.
 cudaError_t launch_kmvtc5_gauss(int nh, int csep, int M, int variant, int G, size_t smem,
                                 cudaStream_t s, const CUtensorMap &rowmap,
                                 const CUtensorMap &colmap, const T5Args &a);
 cudaError_t launch_kmvtc5_matern(int nh, int csep, int M, int variant, int G, size_t smem,
                                  cudaStream_t s, const CUtensorMap &rowmap,
                                  const CUtensorMap &colmap, const T5Args &a);
+cudaError_t launch_kmvtc5_tv_gauss(int nh, int csep, int M, int variant, int G, size_t smem,
+                                   cudaStream_t s, const CUtensorMap &rowmap,
+                                   const CUtensorMap &colmap, const T5Args &a);
+cudaError_t launch_kmvtc5_tv_matern(int nh, int csep, int M, int variant, int G, size_t smem,
+                                    cudaStream_t s, const CUtensorMap &rowmap,
+                                    const CUtensorMap &colmap, const T5Args &a);
 
-template <int KERN, int NH, int CS, int M, int EW, int PIPE, int LAG = 0, int TN = 128>
+template <int KERN, int NH, int CS, int M, int EW, int PIPE, int LAG = 0, int TN = 128, int TV = 0>
 cudaError_t launch_kmvtc5_one(int G, size_t smem, cudaStream_t s, const CUtensorMap &rowmap,
                               const CUtensorMap &colmap, const T5Args &a) {
-  auto k = kmvtc5_kernel<KERN, NH, CS, M, EW, PIPE, LAG, TN>;
+  auto k = kmvtc5_kernel<KERN, NH, CS, M, EW, PIPE, LAG, TN, TV>;
   if (raise_smem_limit(k, smem) != KRR_OK) return cudaErrorInvalidValue;
   k<<<G, (EW + 2) * 32, smem, s>>>(rowmap, colmap, a);
   return cudaGetLastError();
 }
 
-template <int KERN, int NH, int CS, int M>
+template <int KERN, int NH, int CS, int M, bool TVSET>
 cudaError_t launch_kmvtc5_m(int variant, int G, size_t smem, cudaStream_t s,
                             const CUtensorMap &rowmap, const CUtensorMap &colmap,
                             const T5Args &a) {
-  switch (variant) {
-    case 1: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1>(G, smem, s, rowmap, colmap, a);
-    case 3: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 0>(G, smem, s, rowmap, colmap, a);
-    case 2:
-      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 0>(G, smem, s, rowmap, colmap, a);
-      break;
-    case 4:
-      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 1>(G, smem, s, rowmap, colmap, a);
-      break;
-    case 5:
-      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1, 1>(G, smem, s, rowmap, colmap, a);
-      break;
-    case 6:
-      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 1, 0, 96>(G, smem, s, rowmap, colmap, a);
-      break;
-    case 7:
-      if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 0, 0, 96>(G, smem, s, rowmap, colmap, a);
-      break;
+  if constexpr (TVSET) {
+    switch (variant) {
+      case 8: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1, 0, 128, 1>(G, smem, s, rowmap, colmap, a);
+      case 9: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 0, 0, 128, 1>(G, smem, s, rowmap, colmap, a);
+      case 10:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 0, 0, 128, 1>(G, smem, s, rowmap, colmap, a);
+        break;
+      case 11:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 1, 0, 128, 1>(G, smem, s, rowmap, colmap, a);
+        break;
+    }
+  } else {
+    switch (variant) {
+      case 1: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1>(G, smem, s, rowmap, colmap, a);
+      case 3: return launch_kmvtc5_one<KERN, NH, CS, M, 8, 0>(G, smem, s, rowmap, colmap, a);
+      case 2:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 0>(G, smem, s, rowmap, colmap, a);
+        break;
+      case 4:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 16, 1>(G, smem, s, rowmap, colmap, a);
+        break;
+      case 5:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 8, 1, 1>(G, smem, s, rowmap, colmap, a);
+        break;
+      case 6:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 1, 0, 96>(G, smem, s, rowmap, colmap, a);
+        break;
+      case 7:
+        if constexpr (M <= 4) return launch_kmvtc5_one<KERN, NH, CS, M, 12, 0, 0, 96>(G, smem, s, rowmap, colmap, a);
+        break;
+    }
   }
   return cudaErrorInvalidValue;
 }
 
-template <int KERN>
+template <int KERN, bool TVSET>
 cudaError_t launch_kmvtc5(int nh, int csep, int M, int variant, int G, size_t smem,
                           cudaStream_t s, const CUtensorMap &rowmap, const CUtensorMap &colmap,
                           const T5Args &a) {
 #define KRR_T5_CASE(NH, CS, MM)                                                         \
   if (nh == NH && csep == CS && M == MM)                                              \
-    return launch_kmvtc5_m<KERN, NH, CS, MM>(variant, G, smem, s, rowmap, colmap, a);
+    return launch_kmvtc5_m<KERN, NH, CS, MM, TVSET>(variant, G, smem, s, rowmap, colmap, a);
   KRR_T5_CASE(1, 0, 2) KRR_T5_CASE(1, 0, 4) KRR_T5_CASE(1, 0, 8)
   KRR_T5_CASE(1, 1, 2) KRR_T5_CASE(1, 1, 4) KRR_T5_CASE(1, 1, 8)
   KRR_T5_CASE(2, 0, 2) KRR_T5_CASE(2, 0, 4) KRR_T5_CASE(2, 0, 8)

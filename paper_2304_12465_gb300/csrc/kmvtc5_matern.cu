@@ -7,7 +7,7 @@ cudaError_t launch_kmvtc5_matern(int nh, int csep, int M, int variant, int G, si
                                 cudaStream_t s,
                                  const CUtensorMap &rowmap, const CUtensorMap &colmap,
                                  const T5Args &a) {
-  return launch_kmvtc5<KMATERN>(nh, csep, M, variant, G, smem, s, rowmap, colmap, a);
+  return launch_kmvtc5<KMATERN, false>(nh, csep, M, variant, G, smem, s, rowmap, colmap, a);
 }
 
 }  // namespace krr

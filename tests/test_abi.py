@@ -94,16 +94,16 @@ def test_argument_validation_before_any_launch(lib):
 
 def test_product_path_selection(lib):
     """krr_set_product_path takes the three documented paths, and
-    krr_set_product_variant the variants 0..4 (host state only); anything else
-    is refused."""
+    krr_set_product_variant the variants 0..11 (host state only); anything
+    else is refused."""
     _einval(lib.krr_set_product_path(3), lib, "product path")
     _einval(lib.krr_set_product_path(-1), lib, "product path")
     assert lib.krr_set_product_path(2) == 0
     assert lib.krr_set_product_path(1) == 0
     assert lib.krr_set_product_path(0) == 0
-    _einval(lib.krr_set_product_variant(8), lib, "variant")
+    _einval(lib.krr_set_product_variant(12), lib, "variant")
     _einval(lib.krr_set_product_variant(-1), lib, "variant")
-    for v in range(8):
+    for v in range(12):
         assert lib.krr_set_product_variant(v) == 0
     assert lib.krr_set_product_variant(0) == 0
 
@@ -111,9 +111,9 @@ def test_product_path_selection(lib):
 def test_autotune_variant_report_untuned(lib):
     """Before any product has run, no shape is tuned: variant 0, zero times."""
     v = C.c_int(-1)
-    ms = (C.c_float * 7)(1, 1, 1, 1, 1, 1, 1)
+    ms = (C.c_float * 11)(*([1.0] * 11))
     assert lib.krr_autotune_variant(0, 16, 4, 100000, C.byref(v), ms) == 0
-    assert v.value == 0 and list(ms) == [0.0] * 7
+    assert v.value == 0 and list(ms) == [0.0] * 11
     _einval(lib.krr_autotune_variant(0, 33, 4, 100, C.byref(v), ms), lib, "shape")
 
 

@@ -48,11 +48,13 @@ def test_tcgen05_product_layouts(K, kern, N, d, m):
     assert np.all(np.abs(got - ref) <= 2e-5 * bound)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", list(range(1, 12)))
 @pytest.mark.parametrize("kern", TC_KERNS)
 def test_tcgen05_product_variants(K, kern, variant):
     """Every epilogue variant meets the bound; variants differ from each
-    other only at the rounding level (the order of the column-group sums)."""
+    other only at the rounding level (the order of the column-group sums, or
+    for 8..11 the tensor-core sums of split kernel values and right-hand
+    sides)."""
     X, V = _case(2500, 16, 4, 11 + kern)
     ref = O.kmatvec(X, kern, 0.8, 0.3, V)
     bound = f32_product_bound(X, kern, 0.8, 0.3, V)
@@ -64,6 +66,47 @@ def test_tcgen05_product_variants(K, kern, variant):
     assert np.all(np.abs(got - ref) <= 2e-5 * bound)
     base = K.krr_kmatvec(X, kern, 0.8, 0.3, V, prec="mixed")
     assert np.all(np.abs(got - base) <= 1e-5 * bound)
+
+
+@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("kern", TC_KERNS)
+@pytest.mark.parametrize("N,d,m", [(1, 1, 1), (127, 5, 2), (257, 16, 4), (383, 17, 8),
+                                   (1031, 27, 1), (2049, 32, 11), (4099, 3, 7)])
+def test_tcgen05_tensor_sums_layouts(K, kern, variant, N, d, m):
+    """The tensor-core sums over V (variants 8..11) on every split layout,
+    one or two launches, right-hand-side counts that fill one B fragment
+    (m <= 4: v_hi and v_lo slots side by side) or two (m = 5..8), and ragged
+    tile edges (zero right-hand sides beyond N)."""
+    X, V = _case(N, d, m, N * 5 + d + m + kern + variant)
+    ref = O.kmatvec(X, kern, 1.1, 0.5, V)
+    bound = f32_product_bound(X, kern, 1.1, 0.5, V)
+    try:
+        K.krr_set_product_variant(variant)
+        got = K.krr_kmatvec(X, kern, 1.1, 0.5, V, prec="mixed")
+    finally:
+        K.krr_set_product_variant(0)
+    assert np.all(np.abs(got - ref) <= 2e-5 * bound)
+
+
+@pytest.mark.parametrize("variant", [3, 8])
+def test_tcgen05_product_column_scales(K, variant):
+    """Right-hand sides of very different magnitudes, one of them zero: the
+    tensor-core sums scale each column by its own power of two (the FMA sums
+    need none); both meet the componentwise bound."""
+    X, V = _case(3001, 16, 5, 77)
+    V[0] *= 1e-30
+    V[1] *= 1e30
+    V[2] = 0.0
+    V[4] *= 3e-3
+    ref = O.kmatvec(X, O.GAUSSIAN, 0.9, 0.2, V)
+    bound = f32_product_bound(X, O.GAUSSIAN, 0.9, 0.2, V)
+    try:
+        K.krr_set_product_variant(variant)
+        got = K.krr_kmatvec(X, O.GAUSSIAN, 0.9, 0.2, V, prec="mixed")
+    finally:
+        K.krr_set_product_variant(0)
+    assert np.all(np.abs(got - ref) <= 2e-5 * bound)
+    assert np.all(got[2] == 0.0)
 
 
 def test_tcgen05_product_is_deterministic(K):
@@ -108,7 +151,7 @@ def test_tcgen05_near_duplicates(K):
 def test_tcgen05_autotuner_report(K):
     """With autotuning on, the first product of a shape times every valid
     variant; the report gives the choice and positive times for the timed
-    ones (variants 2 and 4-7 serve m <= 4 only)."""
+    ones (variants 2, 4-7, 10 and 11 serve m <= 4 only)."""
     X, V = _case(6001, 12, 8, 21)
     try:
         K.krr_set_autotune(True)
@@ -116,7 +159,8 @@ def test_tcgen05_autotuner_report(K):
     finally:
         K.krr_set_autotune(False)
     v, ms = K.krr_autotune_variant(O.GAUSSIAN, 12, 8, 6001)
-    assert v in (1, 3)
-    assert ms[0] > 0 and ms[2] > 0 and all(t == 0 for t in (ms[1], ms[3], ms[4], ms[5], ms[6]))
+    timed = {1, 3, 8, 9}
+    assert v in timed
+    assert all((ms[v - 1] > 0) == (v in timed) for v in range(1, 12))
     ref = O.kmatvec(X, O.GAUSSIAN, 0.9, 0.2, V)
     assert np.all(np.abs(got - ref) <= 2e-5 * f32_product_bound(X, O.GAUSSIAN, 0.9, 0.2, V))
