@@ -19,6 +19,9 @@ cudaError_t launch_kmvff_gauss(int DP, int M, dim3 g, cudaStream_t s, const KmvF
 cudaError_t launch_kmvff_laplace(int DP, int M, dim3 g, cudaStream_t s, const KmvFFArgs &a);
 cudaError_t launch_kmvff_matern(int DP, int M, dim3 g, cudaStream_t s, const KmvFFArgs &a);
 cudaError_t launch_kmv64_laplace(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
+cudaError_t launch_kmvffsym_gauss(int DP, int M, int G, cudaStream_t s, const KmvFFSymArgs &a);
+cudaError_t launch_kmvffsym_laplace(int DP, int M, int G, cudaStream_t s, const KmvFFSymArgs &a);
+cudaError_t launch_kmvffsym_matern(int DP, int M, int G, cudaStream_t s, const KmvFFSymArgs &a);
 cudaError_t launch_kmv64_matern(int DP, int M, dim3 g, cudaStream_t s, const Kmv64Args &a);
 
 cudaError_t launch_kmv32_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
@@ -47,6 +50,16 @@ cudaError_t launch_kmvff_any(int kern, int DP, int M, dim3 g, cudaStream_t s,
     case KGAUSS: return launch_kmvff_gauss(DP, M, g, s, a);
     case KLAPLACE: return launch_kmvff_laplace(DP, M, g, s, a);
     case KMATERN: return launch_kmvff_matern(DP, M, g, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kmvffsym_any(int kern, int DP, int M, int G, cudaStream_t s,
+                                const KmvFFSymArgs &a) {
+  switch (kern) {
+    case KGAUSS: return launch_kmvffsym_gauss(DP, M, G, s, a);
+    case KLAPLACE: return launch_kmvffsym_laplace(DP, M, G, s, a);
+    case KMATERN: return launch_kmvffsym_matern(DP, M, G, s, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -449,6 +462,56 @@ krr_status kmv_f64(const double *Xd, int64_t N, int d, int kern, double sigma,
   return KRR_OK;
 }
 
+__global__ void kmvffsym_reduce_kernel(const double *__restrict__ rowpart,
+                                       const double *__restrict__ colpart,
+                                       const int *__restrict__ seg0, int64_t N, int m, int M,
+                                       int RT, int nt, int64_t T, int G, int J, double lambda,
+                                       const double *__restrict__ V, int64_t ldv,
+                                       double *__restrict__ Y, int64_t ldy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int t = (int)(i / RT), r = (int)(i % RT);
+  const int64_t st = ffsym_start(t, nt);
+  const int b_lo = ffsym_cta_of(st, T, G), b_hi = ffsym_cta_of(st + (nt - t) - 1, T, G);
+  for (int c = 0; c < m; ++c) {
+    double acc = 0.0;
+    for (int b = b_lo; b <= b_hi; ++b)
+      acc += rowpart[(((int64_t)b * J + (t - seg0[b])) * M + c) * RT + r];
+    for (int I = 0; I < t; ++I)
+      acc += colpart[((ffsym_start(I, nt) + (t - I)) * M + c) * RT + r];
+    Y[(int64_t)c * ldy + i] = acc + lambda * V[(int64_t)c * ldv + i];
+  }
+}
+
+// Geometry of the symmetric float-float product: nt tiles of RT points, T
+// pairs of the upper triangle over G CTAs, J segments per CTA at most.
+struct FFSymGeometry {
+  int RT = 0, nt = 0, G = 0, J = 1;
+  int64_t T = 0;
+};
+
+static FFSymGeometry ffsym_geometry(int64_t N, int DP) {
+  FFSymGeometry g;
+  g.RT = KFF_THREADS * kmvff_rows_per_thread(DP);
+  g.nt = (int)((N + g.RT - 1) / g.RT);
+  g.T = (int64_t)g.nt * (g.nt + 1) / 2;
+  g.G = (int)std::min<int64_t>((int64_t)num_sms() * kmvff_min_blocks(DP), g.T);
+  for (int b = 0; b < g.G; ++b) {
+    const int64_t p0 = (int64_t)b * g.T / g.G, p1 = (int64_t)(b + 1) * g.T / g.G;
+    if (p1 > p0) g.J = std::max(g.J, ffsym_row(p1 - 1, g.nt) - ffsym_row(p0, g.nt) + 1);
+  }
+  return g;
+}
+
+// The symmetric product serves square products with up to 4 right-hand sides
+// per launch when there are at least 4 pairs per CTA (smaller problems keep
+// the column-split kernel, which fills the GPU better) and its column sums
+// (8 T M RT bytes) stay within 4 GiB.
+static bool ffsym_fits(const FFSymGeometry &g, int M) {
+  return M <= 4 && g.T >= 4 * (int64_t)g.G &&
+         (double)g.T * M * g.RT * 8.0 <= 4.0 * 1024 * 1024 * 1024;
+}
+
 // Y (Nr x m) = K(R, P) V (+ lambda V when R is P and lambda != 0): the
 // float-float product between a row point set R and a column set P prepared
 // with the same centre and scale.
@@ -467,9 +530,33 @@ krr_status kff_cross(const PointsFF &R, const PointsFF &P, double lambda, const 
     KRR_LAUNCH_CHECK();
   }
   const bool square = (&R == &P);
+  const FFSymGeometry sg = ffsym_geometry(N, P.dp);
   for (int c0 = 0; c0 < m; c0 += 16) {
     const int mg = (m - c0 < 16) ? (m - c0) : 16;
     const int M = pad_m(mg);
+    if (square && ffsym_fits(sg, M)) {
+      // rowpart | colpart | seg0
+      const size_t nrow = (size_t)sg.G * sg.J * M * sg.RT, ncol = (size_t)sg.T * M * sg.RT;
+      const size_t need = nrow + ncol + (sg.G + 1) / 2;
+      if (part.n < need) KRR_TRY(part.alloc(need, s));
+      int *seg0 = reinterpret_cast<int *>(part.p + nrow + ncol);
+      KmvFFSymArgs a{P.xh.p, P.xl.p, vh + (int64_t)c0 * N, vl + (int64_t)c0 * N, N, mg, sg.nt,
+                     sg.T, sg.J, ec, part.p, part.p + nrow, seg0};
+      KmvTimer tm(2);
+      tm.begin(s);
+      cudaError_t e = launch_kmvffsym_any(P.kern, P.dp, M, sg.G, s, a);
+      tm.end(s);
+      count_launch();
+      if (e != cudaSuccess) {
+        set_error("float-float product launch failed: %s", cudaGetErrorString(e));
+        return KRR_ECUDA;
+      }
+      kmvffsym_reduce_kernel<<<ceil_div(N, 256), 256, 0, s>>>(
+          part.p, part.p + nrow, seg0, N, mg, M, sg.RT, sg.nt, sg.T, sg.G, sg.J, lambda,
+          V + (int64_t)c0 * ldv, ldv, Y + (int64_t)c0 * ldy, ldy);
+      KRR_LAUNCH_CHECK();
+      continue;
+    }
     const int rows = KFF_THREADS * kmvff_rows_per_thread(P.dp);
     const int64_t row_tiles = (Nr + rows - 1) / rows;
     const int splits = choose_splits(row_tiles, N, KFF_TJ, 4, 6);

@@ -128,6 +128,50 @@ cudaError_t launch_kmvff_m(int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a)
   return cudaGetLastError();
 }
 
+struct KmvFFSymArgs {
+  const float *xh, *xl, *Vh, *Vl;
+  int64_t N;
+  int m;
+  int nt;      // row tiles
+  int64_t T;   // pairs of the upper triangle
+  int J;       // segments per CTA (maximum)
+  ExpFFConsts ec;
+  double *rowpart, *colpart;
+  int *seg0;   // first row tile of each CTA (written by the kernel)
+};
+
+template <int KERN, int DP>
+cudaError_t launch_kmvffsym_m(int M, int G, cudaStream_t s, const KmvFFSymArgs &a) {
+  switch (M) {
+#define KRR_CASE(MM)                                                                     \
+  case MM:                                                                               \
+    kmvffsym_kernel<KERN, DP, MM><<<G, KFF_THREADS, 0, s>>>(                             \
+        a.xh, a.xl, a.Vh, a.Vl, a.N, a.m, a.nt, a.T, a.J, a.ec, a.rowpart, a.colpart,    \
+        a.seg0);                                                                         \
+    break;
+    KRR_CASE(1) KRR_CASE(2) KRR_CASE(4)
+#undef KRR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KERN>
+cudaError_t launch_kmvffsym(int DP, int M, int G, cudaStream_t s, const KmvFFSymArgs &a) {
+  switch (DP) {
+    case 4: return launch_kmvffsym_m<KERN, 4>(M, G, s, a);
+    case 8: return launch_kmvffsym_m<KERN, 8>(M, G, s, a);
+    case 12: return launch_kmvffsym_m<KERN, 12>(M, G, s, a);
+    case 16: return launch_kmvffsym_m<KERN, 16>(M, G, s, a);
+    case 20: return launch_kmvffsym_m<KERN, 20>(M, G, s, a);
+    case 24: return launch_kmvffsym_m<KERN, 24>(M, G, s, a);
+    case 28: return launch_kmvffsym_m<KERN, 28>(M, G, s, a);
+    case 32: return launch_kmvffsym_m<KERN, 32>(M, G, s, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int KERN>
 cudaError_t launch_kmvff(int DP, int M, dim3 grid, cudaStream_t s, const KmvFFArgs &a) {
   switch (DP) {
@@ -151,5 +195,7 @@ cudaError_t launch_kmv64_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
                              const Kmv64Args &a);
 cudaError_t launch_kmvff_any(int kern, int DP, int M, dim3 grid, cudaStream_t s,
                              const KmvFFArgs &a);
+cudaError_t launch_kmvffsym_any(int kern, int DP, int M, int G, cudaStream_t s,
+                                const KmvFFSymArgs &a);
 
 }  // namespace krr

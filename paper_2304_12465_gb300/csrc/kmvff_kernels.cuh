@@ -125,6 +125,79 @@ __device__ __forceinline__ FF sqrt_ff(FF a) {
   return fast_two_sum(s, corr);
 }
 
+// kappa(x_i, x_j) in float-float from split points (xh + xl, pre-scaled):
+// direct coordinate differences, float-float exponential (and the Matern
+// polynomial).
+template <int KERN, int DP>
+__device__ __forceinline__ FF ff_kernel_value(const float (&ih)[DP], const float (&il)[DP],
+                                              const float *jh, const float *jl,
+                                              const float *__restrict__ cst,
+                                              const float *__restrict__ tab) {
+  FF arg;
+  if constexpr (KERN == KLAPLACE) {
+    FF s = {0.0f, 0.0f};
+    float lo = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      FF dd = two_sum(ih[k], -jh[k]);
+      dd.l = __fadd_rn(dd.l, __fsub_rn(il[k], jl[k]));
+      // sign of the unevaluated sum (dd.h is 0 when the high parts agree)
+      if (__fadd_rn(dd.h, dd.l) < 0.0f) {
+        dd.h = -dd.h;
+        dd.l = -dd.l;
+      }
+      const FF t = two_sum(s.h, dd.h);
+      s.h = t.h;
+      lo = __fadd_rn(lo, __fadd_rn(t.l, dd.l));
+    }
+    s = fast_two_sum(s.h, __fadd_rn(s.l, lo));
+    arg = {-s.h, -s.l};
+  } else {
+    // S = sum_k (x_ik - x_jk)^2 with exact differences (TwoSum) and exact
+    // squares (TwoProd): intermediates stay the size of S.
+    FF s = {0.0f, 0.0f};
+    float lo = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      FF dd = two_sum(ih[k], -jh[k]);
+      dd.l = __fadd_rn(dd.l, __fsub_rn(il[k], jl[k]));
+      const FF p = two_prod(dd.h, dd.h);
+      // d^2 = dh^2 + 2 dh dl + dl^2 (dl^2 matters when dh is 0 or tiny)
+      const float cross = __fmaf_rn(__fadd_rn(dd.h, dd.h), dd.l, __fmaf_rn(dd.l, dd.l, p.l));
+      const FF t = two_sum(s.h, p.h);
+      s.h = t.h;
+      lo = __fadd_rn(lo, __fadd_rn(t.l, cross));
+    }
+    s = fast_two_sum(s.h, lo);
+    if constexpr (KERN == KMATERN) {
+      // q = sqrt(S);  kappa = (1 + q + q^2/3) exp(-q)
+      const FF q = sqrt_ff(s);
+      arg = {-q.h, -q.l};
+    } else {
+      arg = {-0.5f * s.h, -0.5f * s.l};  // Gaussian: -|x - y|^2 / (2 sigma^2)
+    }
+  }
+  FF kv = exp_ff(arg, cst, tab);
+  if constexpr (KERN == KMATERN) {
+    const FF q = {-arg.h, -arg.l};
+    FF q2 = ff_mul(q, q);
+    const FF third = {0.3333333433f, -9.9341077e-09f};  // 1/3 = hi + lo
+    FF poly = ff_add({1.0f, 0.0f}, ff_add(q, ff_mul(q2, third)));
+    kv = ff_mul(poly, kv);
+  }
+  return kv;
+}
+
+// acc += a b for float-float acc and a, b = bh + bl (TwoProd + TwoSum, the
+// low-order products folded into the low part).
+__device__ __forceinline__ void ff_fma_acc(FF &acc, FF a, float bh, float bl) {
+  const FF p = two_prod(a.h, bh);
+  const float cross = __fmaf_rn(a.h, bl, __fmaf_rn(a.l, bh, p.l));
+  const FF t = two_sum(acc.h, p.h);
+  acc.h = t.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(t.l, cross));
+}
+
 constexpr int KFF_THREADS = 128;
 constexpr int KFF_TJ = 32;                // columns per shared tile
 
@@ -205,67 +278,9 @@ kmvff_kernel(const float *__restrict__ rh, const float *__restrict__ rl, int64_t
     for (int jj = 0; jj < jn; ++jj) {
 #pragma unroll
       for (int r = 0; r < KFF_RI; ++r) {
-        FF arg;
-        if constexpr (KERN == KLAPLACE) {
-          FF s = {0.0f, 0.0f};
-          float lo = 0.0f;
+        const FF kv = ff_kernel_value<KERN, DP>(ih[r], il[r], sxh[jj], sxl[jj], s_cst, s_tab);
 #pragma unroll
-          for (int k = 0; k < DP; ++k) {
-            FF dd = two_sum(ih[r][k], -sxh[jj][k]);
-            dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
-            // sign of the unevaluated sum (dd.h is 0 when the high parts agree)
-            if (__fadd_rn(dd.h, dd.l) < 0.0f) {
-              dd.h = -dd.h;
-              dd.l = -dd.l;
-            }
-            const FF t = two_sum(s.h, dd.h);
-            s.h = t.h;
-            lo = __fadd_rn(lo, __fadd_rn(t.l, dd.l));
-          }
-          s = fast_two_sum(s.h, __fadd_rn(s.l, lo));
-          arg = {-s.h, -s.l};
-        } else {
-          // S = sum_k (x_ik - x_jk)^2 with exact differences (TwoSum) and
-          // exact squares (TwoProd): intermediates stay the size of S.
-          FF s = {0.0f, 0.0f};
-          float lo = 0.0f;
-#pragma unroll
-          for (int k = 0; k < DP; ++k) {
-            FF dd = two_sum(ih[r][k], -sxh[jj][k]);
-            dd.l = __fadd_rn(dd.l, __fsub_rn(il[r][k], sxl[jj][k]));
-            const FF p = two_prod(dd.h, dd.h);
-            // d^2 = dh^2 + 2 dh dl + dl^2 (dl^2 matters when dh is 0 or tiny)
-            const float cross =
-                __fmaf_rn(__fadd_rn(dd.h, dd.h), dd.l, __fmaf_rn(dd.l, dd.l, p.l));
-            const FF t = two_sum(s.h, p.h);
-            s.h = t.h;
-            lo = __fadd_rn(lo, __fadd_rn(t.l, cross));
-          }
-          s = fast_two_sum(s.h, lo);
-          if constexpr (KERN == KMATERN) {
-            // q = sqrt(S);  kappa = (1 + q + q^2/3) exp(-q)
-            const FF q = sqrt_ff(s);
-            arg = {-q.h, -q.l};
-          } else {
-            arg = {-0.5f * s.h, -0.5f * s.l};  // Gaussian: -|x - y|^2 / (2 sigma^2)
-          }
-        }
-        FF kv = exp_ff(arg, s_cst, s_tab);
-        if constexpr (KERN == KMATERN) {
-          const FF q = {-arg.h, -arg.l};
-          FF q2 = ff_mul(q, q);
-          const FF third = {0.3333333433f, -9.9341077e-09f};  // 1/3 = hi + lo
-          FF poly = ff_add({1.0f, 0.0f}, ff_add(q, ff_mul(q2, third)));
-          kv = ff_mul(poly, kv);
-        }
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-          const FF p = two_prod(kv.h, svh[jj][c]);
-          const float cross = __fmaf_rn(kv.h, svl[jj][c], __fmaf_rn(kv.l, svh[jj][c], p.l));
-          const FF t = two_sum(acc[r][c].h, p.h);
-          acc[r][c].h = t.h;
-          acc[r][c].l = __fadd_rn(acc[r][c].l, __fadd_rn(t.l, cross));
-        }
+        for (int c = 0; c < M; ++c) ff_fma_acc(acc[r][c], kv, svh[jj][c], svl[jj][c]);
       }
     }
   }
@@ -280,5 +295,192 @@ kmvff_kernel(const float *__restrict__ rh, const float *__restrict__ rl, int64_t
     }
   }
 }
+
+
+// ---------------------------------------------------------------------------
+// Symmetric square product: K is symmetric, so each pair of row tiles (I, J),
+// J > I, is evaluated once and serves both (K V)_I (row sums, in registers)
+// and (K V)_J (column sums); a diagonal pair (I, I) gives row sums only.
+// The pairs of the upper triangle are numbered row-major (pair (I, J) is
+// ffsym_start(I, nt) + J - I) and CTA b of G takes the contiguous range
+// [b T / G, (b + 1) T / G); its pairs fall into segments of one row tile
+// each.  Row sums go to rowpart[b][segment][c][RT rows], the column sums of
+// pair p to colpart[p][c][RT columns], both as float64 (hi + lo), and
+// kmvffsym_reduce_kernel adds, for every row, its segments' row sums and
+// the column sums of the pairs above it, each in a fixed order.  About half
+// of the entries of the plain product, each with one more float-float
+// multiply-add per right-hand side and two shuffles per right-hand side per
+// column step (a rotating column accumulator, below).
+
+// Pairs before row tile I in the row-major upper triangle of nt tiles.
+__host__ __device__ inline int64_t ffsym_start(int64_t I, int64_t nt) {
+  return I * nt - I * (I - 1) / 2;
+}
+// Row tile of pair p: the largest I with ffsym_start(I) <= p.
+__host__ __device__ inline int ffsym_row(int64_t p, int nt) {
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (ffsym_start(mid, nt) <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// CTA whose pair range contains pair p.
+__host__ __device__ inline int ffsym_cta_of(int64_t p, int64_t T, int G) {
+  return (int)(((p + 1) * (int64_t)G + T - 1) / T) - 1;
+}
+
+template <int KERN, int DP, int M>
+__global__ void __launch_bounds__(KFF_THREADS, kmvff_min_blocks(DP))
+kmvffsym_kernel(const float *__restrict__ xh, const float *__restrict__ xl,
+                const float *__restrict__ Vh, const float *__restrict__ Vl, int64_t N, int m,
+                int nt, int64_t T, int J, ExpFFConsts ec, double *__restrict__ rowpart,
+                double *__restrict__ colpart, int *__restrict__ seg0) {
+  constexpr int RI = kmvff_rows_per_thread(DP);
+  constexpr int RT = KFF_THREADS * RI;            // points per tile
+  constexpr int NW = KFF_THREADS / 32;
+  static_assert(KFF_TJ == 32, "one staged column per lane");
+  // rows padded by one float: lanes read 32 different staged columns at once
+  __shared__ float sxh[KFF_TJ][DP + 1], sxl[KFF_TJ][DP + 1];
+  __shared__ float svh[KFF_TJ][M + 1], svl[KFF_TJ][M + 1];
+  __shared__ float s_cst[4], s_tab[64];
+  __shared__ FF scol[NW][KFF_TJ][M];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 4) s_cst[tid] = ec.c[tid];
+  if (tid < 64) s_tab[tid] = ec.tab[tid];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int64_t p_begin = (int64_t)b * T / G, p_end = (int64_t)(b + 1) * T / G;
+  if (p_begin >= p_end) return;
+  int I = ffsym_row(p_begin, nt);
+  int Jt = I + (int)(p_begin - ffsym_start(I, nt));
+  const int I_first = I;
+  if (tid == 0) seg0[b] = I_first;
+
+  float ih[RI][DP], il[RI][DP];
+  float vih[RI][M], vil[RI][M];
+  FF acc[RI][M];
+  auto load_rows = [&]() {
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+      const int64_t i = (int64_t)I * RT + tid + (int64_t)r * KFF_THREADS;
+      const bool ok = i < N;
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        ih[r][k] = ok ? xh[i * DP + k] : 0.0f;
+        il[r][k] = ok ? xl[i * DP + k] : 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        const bool okc = ok && c < m;
+        vih[r][c] = okc ? Vh[(int64_t)c * N + i] : 0.0f;
+        vil[r][c] = okc ? Vl[(int64_t)c * N + i] : 0.0f;
+        acc[r][c] = {0.0f, 0.0f};
+      }
+    }
+  };
+  load_rows();
+
+  for (int64_t p = p_begin; p < p_end; ++p) {
+    const bool diag = (Jt == I);
+    const int64_t jt0 = (int64_t)Jt * RT, jt1 = min(N, jt0 + RT);
+    for (int64_t j0 = jt0; j0 < jt1; j0 += KFF_TJ) {
+      __syncthreads();
+      for (int idx = tid; idx < KFF_TJ * DP; idx += KFF_THREADS) {
+        const int jj = idx / DP, k = idx % DP;
+        const int64_t j = j0 + jj;
+        const bool ok = j < jt1;
+        sxh[jj][k] = ok ? xh[j * DP + k] : 0.0f;
+        sxl[jj][k] = ok ? xl[j * DP + k] : 0.0f;
+      }
+      for (int idx = tid; idx < KFF_TJ * M; idx += KFF_THREADS) {
+        const int c = idx / KFF_TJ, jj = idx % KFF_TJ;
+        const int64_t j = j0 + jj;
+        const bool ok = (j < jt1) && (c < m);
+        svh[jj][c] = ok ? Vh[(int64_t)c * N + j] : 0.0f;
+        svl[jj][c] = ok ? Vl[(int64_t)c * N + j] : 0.0f;
+      }
+      __syncthreads();
+      const int jn = (int)min((int64_t)KFF_TJ, jt1 - j0);
+      if (diag) {
+#pragma unroll 1
+        for (int jj = 0; jj < jn; ++jj) {
+#pragma unroll
+          for (int r = 0; r < RI; ++r) {
+            const FF kv = ff_kernel_value<KERN, DP>(ih[r], il[r], sxh[jj], sxl[jj], s_cst, s_tab);
+#pragma unroll
+            for (int c = 0; c < M; ++c) ff_fma_acc(acc[r][c], kv, svh[jj][c], svl[jj][c]);
+          }
+        }
+      } else {
+        // Lane l takes the staged columns in the order (l + s) mod 32 and
+        // carries the column sum of its current column; after each step it
+        // passes that sum to lane l - 1, which takes the same column next.
+        // After 32 steps lane l holds the warp's sum for column (l + 31) mod
+        // 32.  Columns beyond the tile are zero points with zero right-hand
+        // sides: their row terms vanish and their column sums are dropped.
+        FF col[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) col[c] = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int st = 0; st < KFF_TJ; ++st) {
+          const int jj = (lane + st) & (KFF_TJ - 1);
+#pragma unroll
+          for (int r = 0; r < RI; ++r) {
+            const FF kv = ff_kernel_value<KERN, DP>(ih[r], il[r], sxh[jj], sxl[jj], s_cst, s_tab);
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              ff_fma_acc(acc[r][c], kv, svh[jj][c], svl[jj][c]);
+              ff_fma_acc(col[c], kv, vih[r][c], vil[r][c]);
+            }
+          }
+          if (st + 1 < KFF_TJ)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              col[c].h = __shfl_sync(0xffffffffu, col[c].h, (lane + 1) & 31);
+              col[c].l = __shfl_sync(0xffffffffu, col[c].l, (lane + 1) & 31);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) scol[warp][(lane + KFF_TJ - 1) & (KFF_TJ - 1)][c] = col[c];
+        __syncthreads();
+        // the warps' shares in warp order, one (column, rhs) per thread
+        for (int idx = tid; idx < KFF_TJ * M; idx += KFF_THREADS) {
+          const int jj = idx / M, c = idx % M;
+          if (jj < jn) {
+            FF t = scol[0][jj][c];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) t = ff_add(t, scol[w][jj][c]);
+            colpart[(p * M + c) * RT + (j0 - jt0) + jj] = (double)t.h + (double)t.l;
+          }
+        }
+      }
+    }
+    if (Jt + 1 == nt || p + 1 == p_end) {
+      // end of this row tile's segment
+      double *out = rowpart + (((int64_t)b * J + (I - I_first)) * M) * RT;
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+          out[c * RT + tid + r * KFF_THREADS] = (double)acc[r][c].h + (double)acc[r][c].l;
+      if (p + 1 < p_end) {
+        ++I;
+        Jt = I;
+        load_rows();
+      }
+    } else {
+      ++Jt;
+    }
+  }
+}
+
+// Y[c][i] = the row sums of the segments covering row i's tile (CTA order)
+// + the column sums of every pair (I, t) above it (I order) + lambda V[c][i].
+__global__ void kmvffsym_reduce_kernel(const double *__restrict__ rowpart,
+                                       const double *__restrict__ colpart,
+                                       const int *__restrict__ seg0, int64_t N, int m, int M,
+                                       int RT, int nt, int64_t T, int G, int J, double lambda,
+                                       const double *__restrict__ V, int64_t ldv,
+                                       double *__restrict__ Y, int64_t ldy);
 
 }  // namespace krr

@@ -7,4 +7,9 @@ cudaError_t launch_kmvff_laplace(int DP, int M, dim3 grid, cudaStream_t s, const
   return launch_kmvff<KLAPLACE>(DP, M, grid, s, a);
 }
 
+cudaError_t launch_kmvffsym_laplace(int DP, int M, int G, cudaStream_t s,
+                                  const KmvFFSymArgs &a) {
+  return launch_kmvffsym<KLAPLACE>(DP, M, G, s, a);
+}
+
 }  // namespace krr

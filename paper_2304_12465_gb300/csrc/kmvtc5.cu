@@ -414,7 +414,10 @@ static cudaError_t t5_launch(const PointsF32 &R, const PointsF32 &P, int M, int 
   const int nh = P.nh5, csep = P.csep5, kb = t5_kb(nh, csep);
   // at least half of an SM's shared memory: one CTA per SM (each takes all
   // 512 TMEM columns)
-  const size_t smem = std::max<size_t>(t5_smem_bytes(kb, M), 116 * 1024);
+  const int ew = t5_variant_ew(variant);
+  const size_t smem = std::max<size_t>(
+      t5_smem_bytes(kb, M, t5_tot_floats(ew, M, variant == 5, t5_variant_tv(variant))),
+      116 * 1024);
   const bool tv = t5_variant_tv(variant), gauss = P.kern == KGAUSS;
   KmvTimer tm;
   if (timed) tm.begin(s);

@@ -79,12 +79,26 @@ __host__ __device__ constexpr int t5_nh(int d) { return (d + 15) / 16; }
 __host__ __device__ constexpr int t5_csep(int d) { return (d % 16 == 0 || d % 16 > 10) ? 1 : 0; }
 __host__ __device__ constexpr int t5_kb(int nh, int csep) { return 2 * nh + csep; }
 
+// Floats of shared memory that hold the epilogue's running totals (the second
+// accumulation level) for the FMA variants whose registers would not hold
+// them (16 epilogue warps, or the software-pipelined variant, at M = 4): 8
+// per right-hand side per thread (2 row tiles x 2 row halves x a row pair).
+// 0 (totals in registers) otherwise.  At M = 8 with 8 warps the registers
+// spill about 270 bytes, which measured faster (4.49 ms against 4.64 ms at
+// N = 1e5) than the totals in shared memory and the two stages they cost.
+__host__ __device__ constexpr int t5_tot_floats(int EW, int M, int LAG, int TV) {
+  return (!TV && M == 4 && (EW == 16 || LAG)) ? EW * 32 * 8 * M : 0;
+}
+
 // Column-tile pipeline stages: as many as fit (at most 8) in about 200 KB of
-// shared memory beside the row operand, so that TMA latency is hidden.
-__host__ __device__ constexpr int t5_stages(int kb, int M) {
-  return ((204800 - 1024 - T5_RT * kb * T5_BLK) / (kb * T5_BLK + (M / 2) * T5_TN * 16)) > 8
+// shared memory beside the row operand and the totals, so that TMA latency is
+// hidden.
+__host__ __device__ constexpr int t5_stages(int kb, int M, int tot_floats = 0) {
+  return ((204800 - 1024 - T5_RT * kb * T5_BLK - 4 * tot_floats) /
+          (kb * T5_BLK + (M / 2) * T5_TN * 16)) > 8
              ? 8
-             : ((204800 - 1024 - T5_RT * kb * T5_BLK) / (kb * T5_BLK + (M / 2) * T5_TN * 16));
+             : ((204800 - 1024 - T5_RT * kb * T5_BLK - 4 * tot_floats) /
+                (kb * T5_BLK + (M / 2) * T5_TN * 16));
 }
 
 // Barrier indices in shared memory for ST stages.
@@ -99,9 +113,10 @@ __host__ __device__ constexpr int t5_bar_fin(int st) { return 6 + 3 * st; }
 __host__ __device__ constexpr int t5_nbar(int st) { return 7 + 3 * st; }
 
 // Shared memory of one CTA (bytes, including 1024 bytes of alignment slack).
-__host__ __device__ constexpr int t5_smem_bytes(int kb, int M) {
-  return 1024 + T5_RT * kb * T5_BLK + t5_stages(kb, M) * (kb * T5_BLK + (M / 2) * T5_TN * 16) +
-         8 * t5_nbar(t5_stages(kb, M)) + 16;
+__host__ __device__ constexpr int t5_smem_bytes(int kb, int M, int tot_floats = 0) {
+  return 1024 + T5_RT * kb * T5_BLK +
+         t5_stages(kb, M, tot_floats) * (kb * T5_BLK + (M / 2) * T5_TN * 16) + 4 * tot_floats +
+         8 * t5_nbar(t5_stages(kb, M, tot_floats)) + 16;
 }
 
 struct T5Args {
@@ -183,7 +198,8 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
   constexpr int MP = M / 2;   // right-hand-side pairs
   constexpr int NB = (M == 8) ? 2 : 1;   // B fragments per batch (TV)
   constexpr int VQ = TV ? NB : MP;       // 16-byte right-hand-side words per column
-  constexpr int T5_ST = t5_stages(KB, M);
+  constexpr int TOTF = t5_tot_floats(EW, M, LAG, TV);   // running totals in shared memory
+  constexpr int T5_ST = t5_stages(KB, M, TOTF);
   constexpr int T5_BAR_A_FULL = t5_bar_a_full();
   constexpr int T5_BAR_A_EMPTY = t5_bar_a_empty();
   constexpr int T5_BAR_B_FULL = t5_bar_b_full(T5_ST);
@@ -206,7 +222,9 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
   const uint32_t sB = sA + T5_RT * KB * T5_BLK;               // [stage][kb][128 x 32 B]
   const uint32_t vOff = sB + T5_ST * KB * T5_BLK - base;
   float4 *sV = reinterpret_cast<float4 *>(gbase + vOff);       // [stage][MP][128]
-  const uint32_t sBar = base + vOff + T5_ST * MP * T5_TN * 16;
+  const uint32_t totOff = vOff + T5_ST * MP * 128 * 16;
+  float4 *sTot = reinterpret_cast<float4 *>(gbase + totOff);   // [warp][2M][32 lanes]
+  const uint32_t sBar = base + totOff + 4 * TOTF;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(gbase + (sBar - base) + 8 * T5_NBAR);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
   auto bar = [&](int i) -> uint32_t { return sBar + 8u * (uint32_t)i; };
@@ -350,23 +368,69 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
     // (up to about 1e5 columns per row) adds one tile sum at a time to its
     // running total instead of one entry at a time
     float2 acc[T5_RT][2][M];        // [row tile][rows g,g+8 | g+16,g+24][rhs]
-    float2 tot[T5_RT][2][M];
+    // running totals: registers, or (TOTF > 0) this thread's 2M float4 in
+    // shared memory, float4 q holding acc entries 2q and 2q + 1 (flattened)
+    float2 tot[TOTF ? 1 : T5_RT][2][M];
+    float4 *mytot = sTot + warp * (2 * M) * 32 + lane;
 #pragma unroll
     for (int rt = 0; rt < T5_RT; ++rt)
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
-        for (int c = 0; c < M; ++c) acc[rt][hf][c] = tot[rt][hf][c] = f2(0.0f, 0.0f);
-    auto fold_tile = [&]() {
+        for (int c = 0; c < M; ++c) acc[rt][hf][c] = f2(0.0f, 0.0f);
+    if constexpr (TOTF > 0) {
+#pragma unroll
+      for (int q = 0; q < 2 * M; ++q) mytot[q * 32] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
 #pragma unroll
       for (int rt = 0; rt < T5_RT; ++rt)
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
-          for (int c = 0; c < M; ++c) {
-            tot[rt][hf][c] = __fadd2_rn(tot[rt][hf][c], acc[rt][hf][c]);
-            acc[rt][hf][c] = f2(0.0f, 0.0f);
-          }
+          for (int c = 0; c < M; ++c) tot[rt][hf][c] = f2(0.0f, 0.0f);
+    }
+    auto fold_tile = [&]() {
+      if constexpr (TOTF > 0) {
+        float2 *af = &acc[0][0][0];
+#pragma unroll
+        for (int q = 0; q < 2 * M; ++q) {
+          const float4 t = mytot[q * 32];
+          const float2 lo = __fadd2_rn(f2(t.x, t.y), af[2 * q]);
+          const float2 hi = __fadd2_rn(f2(t.z, t.w), af[2 * q + 1]);
+          mytot[q * 32] = make_float4(lo.x, lo.y, hi.x, hi.y);
+          af[2 * q] = af[2 * q + 1] = f2(0.0f, 0.0f);
+        }
+      } else {
+#pragma unroll
+        for (int rt = 0; rt < T5_RT; ++rt)
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              tot[rt][hf][c] = __fadd2_rn(tot[rt][hf][c], acc[rt][hf][c]);
+              acc[rt][hf][c] = f2(0.0f, 0.0f);
+            }
+      }
+    };
+    // running total of (rt, hf, c), cleared as it is read (segment end)
+    auto take_tot = [&](int rt, int hf, int c) -> float2 {
+      if constexpr (TOTF > 0) {
+        const int i = (rt * 2 + hf) * M + c;
+        float4 *t = mytot + (i >> 1) * 32;
+        const float4 v = *t;
+        if (i & 1) {
+          t->z = 0.0f;
+          t->w = 0.0f;
+          return f2(v.z, v.w);
+        }
+        t->x = 0.0f;
+        t->y = 0.0f;
+        return f2(v.x, v.y);
+      } else {
+        const float2 v = tot[rt][hf][c];
+        tot[rt][hf][c] = f2(0.0f, 0.0f);
+        return v;
+      }
     };
     constexpr int NBT = T5_WCOLS / 16;   // batches of 16 columns per tile
     if constexpr (TV) {
@@ -495,7 +559,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-              float2 v = tot[rt][hf][c];
+              float2 v = take_tot(rt, hf, c);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
               v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
@@ -505,7 +569,6 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
                 out[c * T5_RB + row] = v.x;
                 out[c * T5_RB + row + 8] = v.y;
               }
-              tot[rt][hf][c] = f2(0.0f, 0.0f);
             }
       };
       // kernel values of one batch: [ch][e][rt][hf] -> rows (g, g + 8) pair
@@ -705,7 +768,7 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
           for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-              float2 v = tot[rt][hf][c];
+              float2 v = take_tot(rt, hf, c);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
               v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
               v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
@@ -715,7 +778,6 @@ kmvtc5_kernel(const __grid_constant__ CUtensorMap rowmap,
                 out[c * T5_RB + row] = v.x;
                 out[c * T5_RB + row + 8] = v.y;
               }
-              tot[rt][hf][c] = f2(0.0f, 0.0f);
             }
       }
     }

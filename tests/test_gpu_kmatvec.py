@@ -125,6 +125,26 @@ def ff_error_bound(X, kern, sigma, lam, V):
     return 8.0 * ((A * eps) @ np.abs(V).T).T + 5e-14 * f32_product_bound(X, kern, sigma, lam, V)
 
 
+@pytest.mark.parametrize("kern", KERNS)
+@pytest.mark.parametrize("N,d,m", [(20077, 16, 4), (15500, 20, 3), (16500, 8, 1)])
+def test_float_float_symmetric_product(K, kern, N, d, m):
+    """Square float-float products large enough for the symmetric kernel (each
+    off-diagonal pair of point tiles evaluated once for both tiles' rows, the
+    column sums reduced per pair): ragged N, 256-point (d <= 16) and
+    128-point (d > 16) tiles, rows at tile edges and at random against the
+    oracle."""
+    rng = np.random.default_rng(N + d + m + kern)
+    X = rng.standard_normal((N, d)) * 0.5
+    V = rng.standard_normal((m, N))
+    got = K.krr_kmatvec(to_dev(X), kern, 0.9, 0.1, to_dev(V), prec="ff").cpu().numpy()
+    edges = np.array([0, 1, 127, 128, 255, 256, 511, 512, N // 2, N - 257, N - 256, N - 129,
+                      N - 128, N - 1])
+    rows = np.unique(np.concatenate([edges, rng.choice(N, 40, replace=False)]))
+    ref = O.kmatvec(X, kern, 0.9, 0.1, V, rows)
+    bound = f32_product_bound(X, kern, 0.9, 0.1, V, rows)
+    assert np.all(np.abs(got[:, rows] - ref) <= 2e-12 * bound)
+
+
 def test_float_float_near_duplicates_and_far_points(K):
     """Twins at 1e-7 and a far cluster (coordinates ~16 after scaling) whose
     cross entries underflow, against the float-float error model."""
