@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma", "mma_sync"],
                     help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
+    ap.add_argument("--no-pcg-graphs", action="store_true",
+                    help="step the PCG iterations one launch at a time (no CUDA graphs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the product's default tile instead of tuning it in the warm-up")
     ap.add_argument("--no-fp64", action="store_true",
@@ -313,6 +315,7 @@ def run_native(args):
     dist, rank, world = dist_setup(args.gpus)
     K.load()
     K.krr_set_product_path(args.product_path)
+    K.krr_set_pcg_graphs(not args.no_pcg_graphs)
     w = make_c2_mixed(n=args.n)
     dev = torch.device("cuda", torch.cuda.current_device())
     X = torch.from_numpy(w.X).to(dev)
@@ -408,6 +411,8 @@ def run_native(args):
                 "kmv64_launches": kmv64_n,
                 "kmvff_ms_per_launch": kmvff_ms / max(kmvff_n, 1),
                 "kmvff_launches": kmvff_n,
+                "graph_replays": [i["graph_replays"] for i in infos],
+                "host_checks": [i["host_checks"] for i in infos],
                 "kmv32_tile_autotuned": tile,
                 "kmv32_tile_kind": ("epilogue variant" if args.product_path == "tensor"
                                     else "column splits"),

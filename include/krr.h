@@ -107,7 +107,9 @@ typedef struct {
     double kmv64_ms;         /* summed device time of the float64 product     */
     double kmvff_ms;         /* summed device time of the float-float product */
     int kmvff_launches;      /* number of float-float fused-product launches  */
-    int reserved3;
+    int graph_replays;       /* CUDA-graph replays of PCG iteration chunks
+                                (see krr_set_pcg_graphs)                      */
+    int host_checks;         /* convergence flags read back by the host       */
 } krr_info;
 
 /* ------------------------------------------------------------------------ */
@@ -544,6 +546,20 @@ KRR_API void krr_server_destroy(krr_server *S);
 /* tuned product can differ from an untuned one at the rounding level; with   */
 /* a fixed choice, results are reproducible.                                  */
 KRR_API void krr_set_autotune(int on);
+
+/* CUDA-graph replay of the PCG iterations (engineering, not in the paper).  */
+/* While on (non-zero, the default) every PCG run of krr_pcg_solve,          */
+/* krr_pcg_solve_batched and krill_solve takes its first iteration one       */
+/* launch at a time, then captures chunks of 16, 4 and 1 whole iterations    */
+/* (preconditioner, PCG scalars and vectors, fused product) as CUDA graphs   */
+/* on a private stream and replays them on the caller's stream, reading the  */
+/* per-column convergence flags back once per replay (one host read per      */
+/* iteration when off).  Chunk lengths follow the residual's observed rate;  */
+/* iterations a replay runs after every column converged change nothing      */
+/* (converged columns freeze on the device) and are counted in the kernel    */
+/* entries.  Results are identical with and without graphs.  An operator    */
+/* that cannot be captured falls back to launch-at-a-time stepping.          */
+KRR_API void krr_set_pcg_graphs(int on);
 
 /* Split count chosen by the autotuner for a float32 product shape, or 0 if   */
 /* that shape has not been tuned (for the path krr_set_product_path selects). */

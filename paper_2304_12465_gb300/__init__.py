@@ -25,6 +25,7 @@ from .api import (  # noqa: F401
     krr_server_footprint,
     krr_autotune_choice,
     krr_set_autotune,
+    krr_set_pcg_graphs,
     krr_set_product_path,
     krr_set_product_variant,
     krr_autotune_variant,

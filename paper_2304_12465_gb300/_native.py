@@ -30,7 +30,8 @@ class KrrInfo(C.Structure):
                 ("t_solve_s", C.c_double), ("kmv_ms", C.c_double),
                 ("kmv_launches", C.c_int), ("kmv64_launches", C.c_int),
                 ("kmv64_ms", C.c_double), ("kmvff_ms", C.c_double),
-                ("kmvff_launches", C.c_int), ("reserved3", C.c_int)]
+                ("kmvff_launches", C.c_int), ("graph_replays", C.c_int),
+                ("host_checks", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_
@@ -135,6 +136,7 @@ SIGNATURES = {
     "krr_server_import": (_int, [_vp, _vp, C.c_size_t, _vp, _vp, _vp, C.POINTER(_i64)]),
     "krr_server_destroy": (None, [_vp]),
     "krr_set_autotune": (None, [_int]),
+    "krr_set_pcg_graphs": (None, [_int]),
     "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
     "krr_set_product_path": (_int, [_int]),
     "krr_set_product_variant": (_int, [_int]),

@@ -374,6 +374,11 @@ def krr_set_autotune(on: bool) -> None:
     load().krr_set_autotune(1 if on else 0)
 
 
+def krr_set_pcg_graphs(on: bool) -> None:
+    """CUDA-graph replay of the PCG iterations (on by default)."""
+    load().krr_set_pcg_graphs(1 if on else 0)
+
+
 def krr_autotune_choice(kern, d: int, m: int, N: int) -> int:
     """Split count the autotuner chose for a float32 product shape (0: none)."""
     v = C.c_int()

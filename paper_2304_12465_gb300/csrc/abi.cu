@@ -11,6 +11,7 @@
 
 #include "kmv.cuh"
 #include "krill.cuh"
+#include "pcg.cuh"
 #include "rpc.cuh"
 #include "solve.cuh"
 
@@ -66,7 +67,12 @@ bool is_device_ptr(const void *p) {
 static std::atomic<unsigned long long> g_launches{0};
 static thread_local bool g_count_launches = true;
 void set_launch_counting(bool on) { g_count_launches = on; }
+static thread_local CaptureLog *t_capture_log = nullptr;
 void count_launch() {
+  if (t_capture_log) {
+    ++t_capture_log->launches;
+    return;
+  }
   if (g_count_launches) g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -90,6 +96,9 @@ struct ProfEvent {
   int tag;
 };
 static std::vector<ProfEvent> g_prof_events;
+// launches timed inside replayed graphs, already converted to milliseconds
+static double g_prof_done_ms[3] = {0.0, 0.0, 0.0};
+static int g_prof_done_n[3] = {0, 0, 0};
 
 bool profiling_on() { return g_profiling; }
 
@@ -98,14 +107,47 @@ void KmvTimer::begin(cudaStream_t s) {
   if (!on) return;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  cudaEventRecord(a, s);
+  if (t_capture_log) cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+  else cudaEventRecord(a, s);
 }
 
 void KmvTimer::end(cudaStream_t s) {
   if (!on) return;
+  if (t_capture_log) {
+    // an event node of the graph being captured: timed after each replay
+    cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+    t_capture_log->timers.push_back({a, b, tag});
+    return;
+  }
   cudaEventRecord(b, s);
   std::lock_guard<std::mutex> lk(g_prof_mtx);
   g_prof_events.push_back({a, b, tag});
+}
+
+CaptureLog::~CaptureLog() {
+  for (auto &t : timers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+}
+
+void capture_log_begin(CaptureLog *log) { t_capture_log = log; }
+
+void capture_replayed(const CaptureLog &log) {
+  count_launches(log.launches);
+  if (log.timers.empty()) return;
+  std::lock_guard<std::mutex> lk(g_prof_mtx);
+  for (const auto &t : log.timers) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (t.tag >= 0 && t.tag < 3) {
+      g_prof_done_ms[t.tag] += ms;
+      g_prof_done_n[t.tag] += 1;
+    }
+  }
 }
 
 void kmv_profile_reset() {
@@ -115,12 +157,22 @@ void kmv_profile_reset() {
     cudaEventDestroy(e.b);
   }
   g_prof_events.clear();
+  for (int t = 0; t < 3; ++t) {
+    g_prof_done_ms[t] = 0.0;
+    g_prof_done_n[t] = 0;
+  }
 }
 
 void kmv_profile_collect(int tag, double *ms, int *launches) {
   std::lock_guard<std::mutex> lk(g_prof_mtx);
   double tot = 0.0;
   int n = 0;
+  if (tag >= 0 && tag < 3) {
+    tot = g_prof_done_ms[tag];
+    n = g_prof_done_n[tag];
+    g_prof_done_ms[tag] = 0.0;
+    g_prof_done_n[tag] = 0;
+  }
   std::vector<ProfEvent> keep;
   for (auto &e : g_prof_events) {
     if (e.tag != tag) {
@@ -216,6 +268,8 @@ extern "C" {
 const char *krr_last_error(void) { return g_error.c_str(); }
 
 void krr_set_autotune(int on) { set_autotune(on != 0); }
+
+void krr_set_pcg_graphs(int on) { set_pcg_graphs(on != 0); }
 
 krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N, int *splits) {
   clear_error();

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdarg>
 #include <cmath>
+#include <vector>
 
 #include "krr.h"
 
@@ -32,6 +33,28 @@ void count_launches(unsigned long long n);
 // Off while this thread captures a CUDA graph: its launches are counted when
 // the graph is launched.
 void set_launch_counting(bool on);
+
+// Capture log of a launch sequence recorded into a CUDA graph by this thread
+// (the PCG iteration chunks).  While it is active, count_launch() counts into
+// the log instead of the process total, and the fused-product timers of
+// krr_set_profiling record external event nodes into it; capture_replayed()
+// adds both to the process totals after each replay of the graph completed.
+struct CaptureTimer {
+  cudaEvent_t a, b;
+  int tag;
+};
+struct CaptureLog {
+  unsigned long long launches = 0;
+  std::vector<CaptureTimer> timers;
+  CaptureLog() = default;
+  CaptureLog(const CaptureLog &) = delete;
+  CaptureLog &operator=(const CaptureLog &) = delete;
+  ~CaptureLog();
+};
+// Makes `log` this thread's active capture log (nullptr: none).
+void capture_log_begin(CaptureLog *log);
+// After a replay of the graph has completed (its stream synchronised).
+void capture_replayed(const CaptureLog &log);
 
 #define KRR_LAUNCH_CHECK()          \
   do {                              \

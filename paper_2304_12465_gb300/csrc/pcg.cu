@@ -1,7 +1,10 @@
 // Alg. 1 preconditioner (Woodbury form of the paper's SVD form) and PCG
 // (Sec. 3: zero initial iterate, stop on the recursive relative residual),
 // plus the mixed-precision iterative refinement around a float32 inner PCG.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cmath>
 
 #include "dense.cuh"
 #include "kmv.cuh"
@@ -193,34 +196,40 @@ static krr_status launch_tall_n(const T *F, int64_t N, int rank, const double *v
 template <typename T>
 static krr_status nystrom_apply_impl(const T *F, int64_t N, int rank, const double *W,
                                      const double *Wt, double lambda, const T *R, int m, T *Z,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, PrecondWs *ws) {
   if (rank == 0) {
     // P = lambda I
     return launch_tall_n<T>(F, N, 0, nullptr, m, R, 1.0 / lambda, Z, s);
   }
   const int nb = ceil_div(N, TT_ROWS);
-  DevBuf<double> part, t, u, v;
-  KRR_TRY(part.alloc((size_t)nb * rank * m, s));
-  KRR_TRY(t.alloc((size_t)rank * m, s));
-  KRR_TRY(u.alloc((size_t)rank * m, s));
-  KRR_TRY(v.alloc((size_t)rank * m, s));
-  KRR_TRY(launch_tall_t<T>(F, N, rank, R, m, part.p, s));
-  tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 8), 256, 0, s>>>(part.p, nb, rank, m,
-                                                                    t.p);
+  PrecondWs local;
+  PrecondWs &w = ws ? *ws : local;
+  auto grow = [&](DevBuf<double> &b, size_t n) {
+    return b.n < n ? b.alloc(n, s) : KRR_OK;
+  };
+  KRR_TRY(grow(w.part, (size_t)nb * rank * m));
+  KRR_TRY(grow(w.t, (size_t)rank * m));
+  KRR_TRY(grow(w.u, (size_t)rank * m));
+  KRR_TRY(grow(w.v, (size_t)rank * m));
+  KRR_TRY(launch_tall_t<T>(F, N, rank, R, m, w.part.p, s));
+  tall_t_reduce_kernel<<<ceil_div((int64_t)rank * m, 8), 256, 0, s>>>(w.part.p, nb, rank, m,
+                                                                    w.t.p);
   KRR_LAUNCH_CHECK();
-  KRR_TRY(tri_apply_lower(Wt, rank, t.p, m, u.p, s));
-  KRR_TRY(tri_apply_lower_t(W, rank, u.p, m, v.p, s));
-  return launch_tall_n<T>(F, N, rank, v.p, m, R, 1.0 / lambda, Z, s);
+  KRR_TRY(tri_apply_lower(Wt, rank, w.t.p, m, w.u.p, s));
+  KRR_TRY(tri_apply_lower_t(W, rank, w.u.p, m, w.v.p, s));
+  return launch_tall_n<T>(F, N, rank, w.v.p, m, R, 1.0 / lambda, Z, s);
 }
 
 krr_status nystrom_apply_f64(const krr_factor *f, const NystromCore *c, const double *R,
-                             int m, double *Z, cudaStream_t s) {
-  return nystrom_apply_impl<double>(f->F, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s);
+                             int m, double *Z, cudaStream_t s, PrecondWs *ws) {
+  return nystrom_apply_impl<double>(f->F, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s,
+                                    ws);
 }
 
 krr_status nystrom_apply_f32(const krr_factor *f, const NystromCore *c, const float *R,
-                             int m, float *Z, cudaStream_t s) {
-  return nystrom_apply_impl<float>(c->F32, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s);
+                             int m, float *Z, cudaStream_t s, PrecondWs *ws) {
+  return nystrom_apply_impl<float>(c->F32, f->N, c->rank, c->W, c->Wt, c->lambda, R, m, Z, s,
+                                   ws);
 }
 
 // ------------------------------------------------------- core build
@@ -316,10 +325,14 @@ __global__ void pcg_alpha_kernel(const double *__restrict__ part, int nb, int m,
   sc->alpha[c] = a;
 }
 
-// Convergence test on the recursive residual.
-__global__ void pcg_resid_kernel(const double *__restrict__ part, int nb, int m, int it,
+// Convergence test on the recursive residual; advances the iteration
+// counter (one warp: every lane reads the counter before lane 0 writes it).
+__global__ void pcg_resid_kernel(const double *__restrict__ part, int nb, int m,
                                  PcgScalars *__restrict__ sc) {
   const int c = threadIdx.x;
+  const int it = sc->it + 1;
+  __syncwarp();
+  if (c == 0) sc->it = it;
   if (c >= m) return;
   const double rr = sum_parts(part, nb, c);
   if (sc->active[c]) {
@@ -355,7 +368,10 @@ __global__ void pcg_init_kernel(const double *__restrict__ part_bb,
   sc->iters[c] = 0;
   sc->relres[c] = (bb > 0.0) ? 1.0 : 0.0;
   sc->active[c] = (bb > 0.0) ? 1 : 0;
-  if (c == 0) sc->breakdown = 0;
+  if (c == 0) {
+    sc->breakdown = 0;
+    sc->it = 0;
+  }
 }
 
 // x += alpha p; r -= alpha q
@@ -393,6 +409,43 @@ static unsigned vec_grid(int64_t n) {
 }
 
 // ------------------------------------------------------------ PCG driver
+static std::atomic<bool> g_pcg_graphs{true};
+void set_pcg_graphs(bool on) { g_pcg_graphs.store(on); }
+bool pcg_graphs_on() { return g_pcg_graphs.load(); }
+static thread_local int t_pcg_replays = 0, t_pcg_checks = 0;
+void pcg_counters_take(int *replays, int *checks) {
+  if (replays) *replays = t_pcg_replays;
+  if (checks) *checks = t_pcg_checks;
+  t_pcg_replays = t_pcg_checks = 0;
+}
+
+namespace {
+// One captured chunk of PCG iterations.
+struct PcgChunk {
+  cudaGraphExec_t exec = nullptr;
+  CaptureLog log;
+  ~PcgChunk() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+// Iterations still needed by the slowest active column, estimated from its
+// residual's rate since the previous check (a large count when unknown).
+int pcg_remaining(const PcgScalars &h, const double *prev_rel, int prev_it, int m) {
+  double worst = 0.0;
+  for (int c = 0; c < m; ++c) {
+    if (!h.active[c]) continue;
+    const double rel = h.relres[c], tol = h.tol[c];
+    const int di = h.it - prev_it;
+    if (!(rel > 0.0) || !(prev_rel[c] > rel) || di <= 0 || !(tol > 0.0)) return 1 << 20;
+    const double rate = std::pow(rel / prev_rel[c], 1.0 / di);
+    const double need = std::log(tol / rel) / std::log(rate);
+    worst = std::max(worst, need);
+  }
+  return worst > (double)(1 << 20) ? (1 << 20) : (int)worst;
+}
+}  // namespace
+
 template <typename T>
 krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
                    const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats) {
@@ -418,40 +471,112 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
   pcg_init_kernel<<<1, 32, 0, s>>>(part1.p, part2.p, RED_BLOCKS, m, dtol.p, sc.p);
   KRR_LAUNCH_CHECK();
   KRR_CUDA_TRY(cudaMemcpyAsync(p.p, z.p, sizeof(T) * (size_t)N * m, cudaMemcpyDeviceToDevice, s));
+
+  // q = A p, alpha, x += alpha p, r -= alpha q, convergence test
+  auto step_a = [&](cudaStream_t st) -> krr_status {
+    KRR_TRY(ops.product(p.p, q.p, st));
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(p.p, q.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_alpha_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    pcg_update_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(x, r.p, p.p, q.p, N, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(r.p, r.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_resid_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  };
+  // z = M^-1 r, beta, p = z + beta p
+  auto step_b = [&](cudaStream_t st) -> krr_status {
+    KRR_TRY(ops.precond(r.p, z.p, st));
+    dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(r.p, z.p, N, m, part1.p);
+    KRR_LAUNCH_CHECK();
+    pcg_beta_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    pcg_dir_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(p.p, z.p, N, m, sc.p);
+    KRR_LAUNCH_CHECK();
+    return KRR_OK;
+  };
   PcgScalars h;
-  KRR_CUDA_TRY(cudaMemcpyAsync(&h, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-  KRR_CUDA_TRY(cudaStreamSynchronize(s));
-  int it = 0;
-  bool any = false;
-  for (int c = 0; c < m; ++c) any = any || h.active[c];
-  while (any && it < maxit) {
-    KRR_TRY(ops.product(p.p, q.p, s));
-    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(p.p, q.p, N, m, part1.p);
-    KRR_LAUNCH_CHECK();
-    pcg_alpha_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, sc.p);
-    KRR_LAUNCH_CHECK();
-    pcg_update_kernel<T><<<vec_grid(N * m), 256, 0, s>>>(x, r.p, p.p, q.p, N, m, sc.p);
-    KRR_LAUNCH_CHECK();
-    ++it;
-    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, r.p, N, m, part1.p);
-    KRR_LAUNCH_CHECK();
-    pcg_resid_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, it, sc.p);
-    KRR_LAUNCH_CHECK();
+  int checks = 0;
+  auto read_back = [&]() -> krr_status {
     KRR_CUDA_TRY(cudaMemcpyAsync(&h, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     KRR_CUDA_TRY(cudaStreamSynchronize(s));
-    any = false;
+    ++checks;
+    return KRR_OK;
+  };
+  auto any_active = [&]() {
+    bool any = false;
     for (int c = 0; c < m; ++c) any = any || h.active[c];
-    if (!any || it >= maxit) break;
-    KRR_TRY(ops.precond(r.p, z.p, s));
-    dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, z.p, N, m, part1.p);
-    KRR_LAUNCH_CHECK();
-    pcg_beta_kernel<<<1, 32, 0, s>>>(part1.p, RED_BLOCKS, m, sc.p);
-    KRR_LAUNCH_CHECK();
-    pcg_dir_kernel<T><<<vec_grid(N * m), 256, 0, s>>>(p.p, z.p, N, m, sc.p);
-    KRR_LAUNCH_CHECK();
+    return any;
+  };
+  KRR_TRY(read_back());
+  double prev_rel[PCG_MAX_M];
+  int prev_it = 0;
+  for (int c = 0; c < m; ++c) prev_rel[c] = h.relres[c];
+  // the first iteration runs eagerly: it makes the operator's and the
+  // preconditioner's first calls (allocations, the product's autotuning)
+  if (any_active() && maxit > 0) {
+    KRR_TRY(step_a(s));
+    KRR_TRY(read_back());
   }
+  int replays = 0;
+  bool graphs = pcg_graphs_on();
+  PcgChunk chunks[3];   // 16, 4 and 1 iterations
+  cudaStream_t cs = nullptr;
+  while (any_active() && h.it < maxit) {
+    const int left = maxit - h.it;
+    const int need = pcg_remaining(h, prev_rel, prev_it, m);
+    // replays may overshoot convergence (wasted but harmless iterations of
+    // frozen columns): aim at half the estimated need
+    const int want = std::min(left, std::max(1, need / 2));
+    const int ci = want >= 16 ? 0 : want >= 4 ? 1 : 2;
+    const int U = ci == 0 ? 16 : ci == 1 ? 4 : 1;
+    for (int c = 0; c < m; ++c) prev_rel[c] = h.relres[c];
+    prev_it = h.it;
+    if (graphs && !chunks[ci].exec) {
+      if (!cs) KRR_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      capture_log_begin(&chunks[ci].log);
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      krr_status st = KRR_OK;
+      if (e == cudaSuccess) {
+        for (int u = 0; u < U && st == KRR_OK; ++u) {
+          st = step_b(cs);
+          if (st == KRR_OK) st = step_a(cs);
+        }
+        e = cudaStreamEndCapture(cs, &g);
+      }
+      capture_log_begin(nullptr);
+      if (e == cudaSuccess && st == KRR_OK && g) e = cudaGraphInstantiate(&chunks[ci].exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess || st != KRR_OK || !chunks[ci].exec) {
+        // not capturable (an operator that synchronises or allocates on
+        // every call): step one launch at a time
+        cudaGetLastError();
+        clear_error();
+        graphs = false;
+      }
+    }
+    if (graphs) {
+      KRR_CUDA_TRY(cudaGraphLaunch(chunks[ci].exec, s));
+      ++replays;
+      KRR_TRY(read_back());
+      capture_replayed(chunks[ci].log);
+    } else {
+      KRR_TRY(step_b(s));
+      KRR_TRY(step_a(s));
+      KRR_TRY(read_back());
+    }
+  }
+  if (cs) cudaStreamDestroy(cs);
+  t_pcg_replays += replays;
+  t_pcg_checks += checks;
   if (stats) {
-    stats->products += it;
+    stats->products += h.it;
+    stats->graph_replays += replays;
+    stats->host_checks += checks;
     int mx = 0;
     double worst = 0.0;
     bool conv = true;

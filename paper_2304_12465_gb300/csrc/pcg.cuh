@@ -21,6 +21,7 @@ struct PcgScalars {
   int active[PCG_MAX_M];
   int iters[PCG_MAX_M];
   int breakdown;
+  int it;   // iterations taken (counted on the device)
 };
 
 // Operator and preconditioner of one PCG run, on m x N column-major blocks.
@@ -38,10 +39,25 @@ struct PcgStats {
   bool breakdown = false;
   int col_iters[PCG_MAX_M] = {0};
   double col_relres[PCG_MAX_M] = {0};
+  int graph_replays = 0;  // CUDA-graph chunks replayed
+  int host_checks = 0;    // convergence flags read back by the host
 };
+
+// CUDA-graph replay of the PCG iterations (krr_set_pcg_graphs; on by default).
+void set_pcg_graphs(bool on);
+bool pcg_graphs_on();
+// Graph replays and host read-backs of the convergence flags made by this
+// thread's pcg_run calls since the last call (which resets both).
+void pcg_counters_take(int *replays, int *checks);
 
 // Standard PCG with zero initial iterate; column c stops when its recursive
 // relative residual is <= tol_host[c] (each column has its own scalars).
+// After the first iteration the iterations run as replays of CUDA graphs of
+// 16, 4 or 1 iterations (their launches captured once per run), the
+// convergence flags read back once per replay; converged columns freeze on
+// the device, so the iterates are those of one-iteration-at-a-time stepping.
+// The operator and preconditioner must launch only on the stream they are
+// given and allocate only on their first call.
 template <typename T>
 krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
                    const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats);

@@ -26,12 +26,20 @@ krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, doubl
 krr_status nystrom_core(const krr_factor *f, double mu, int prec, cudaStream_t s,
                         const NystromCore **out);
 
-// Z = P^{-1} R for float64 blocks (m x N column-major, ld N).
+// Scratch of the preconditioner apply, kept by a caller that applies it
+// repeatedly (a PCG run): grown on first use, then reused, so the launches of
+// later applies touch fixed addresses and can be captured in a CUDA graph.
+struct PrecondWs {
+  DevBuf<double> part, t, u, v;
+};
+
+// Z = P^{-1} R for float64 blocks (m x N column-major, ld N); ws = nullptr
+// allocates the scratch for this call.
 krr_status nystrom_apply_f64(const krr_factor *f, const NystromCore *c, const double *R,
-                             int m, double *Z, cudaStream_t s);
+                             int m, double *Z, cudaStream_t s, PrecondWs *ws = nullptr);
 // Same with float32 blocks (mixed core).
 krr_status nystrom_apply_f32(const krr_factor *f, const NystromCore *c, const float *R,
-                             int m, float *Z, cudaStream_t s);
+                             int m, float *Z, cudaStream_t s, PrecondWs *ws = nullptr);
 
 void free_factor(krr_factor *f);
 

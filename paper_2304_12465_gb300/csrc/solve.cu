@@ -56,6 +56,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
                             krr_info *info) {
   const double lambda = mu * (double)N;
   auto t0 = std::chrono::steady_clock::now();
+  pcg_counters_take(nullptr, nullptr);
   const NystromCore *core = nullptr;
   // the float-float path applies the float64 preconditioner
   const int core_prec = (prec == KRR_PREC_FLOAT_FLOAT) ? (int)KRR_PREC_FP64 : prec;
@@ -82,9 +83,10 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
       return kmv_f64(Xd, N, d, kern, sigma, lambda, in, N, m, out, N, st, part);
     };
     PcgOps<double> ops;
+    PrecondWs pws;
     ops.product = product;
     ops.precond = [&](const double *in, double *out, cudaStream_t st) {
-      if (core) return nystrom_apply_f64(F, core, in, m, out, st);
+      if (core) return nystrom_apply_f64(F, core, in, m, out, st, &pws);
       return scale<double>(in, out, N * m, 1.0 / lambda, st);
     };
     PcgStats stats;
@@ -121,8 +123,9 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     ops.product = [&](const float *in, float *out, cudaStream_t st) {
       return kmv_f32(P, lam32, in, N, m, out, N, st, part32);
     };
+    PrecondWs pws;
     ops.precond = [&](const float *in, float *out, cudaStream_t st) {
-      if (core) return nystrom_apply_f32(F, core, in, m, out, st);
+      if (core) return nystrom_apply_f32(F, core, in, m, out, st, &pws);
       return scale<float>(in, out, N * m, 1.0 / lambda, st);
     };
     auto product64 = [&](const double *in, double *out, cudaStream_t st) {
@@ -186,6 +189,7 @@ krr_status pcg_solve_device(const double *Xd, int64_t N, int d, int kern, double
     info->kernel_entries = entries;
     info->t_build_s = t_build;
     info->t_solve_s = seconds_since(t1);
+    pcg_counters_take(&info->graph_replays, &info->host_checks);
   }
   if (final_status == KRR_ENOCONV)
     set_error("PCG did not reach the tolerance (relative residual %.3e > %.3e)", relres, tol);
@@ -289,6 +293,7 @@ krr_status pcg_solve_batched_device(const double *Xd, int64_t N, int d, int S,
                                     const double *mus, const double *Y, double tol, int maxit,
                                     double *alpha, cudaStream_t s, krr_info *info) {
   auto t0 = std::chrono::steady_clock::now();
+  pcg_counters_take(nullptr, nullptr);
   const int mt = S * ms;
   std::vector<double> lam(mt);
   std::vector<const NystromCore *> cores(mt, nullptr);
@@ -321,13 +326,14 @@ krr_status pcg_solve_batched_device(const double *Xd, int64_t N, int d, int S,
   ops.product = [&](const float *in, float *out, cudaStream_t st) {
     return kmv_batched_f32(Pb, S, kerns, sigmas, ms, lam_dev32.p, in, out, st, part32);
   };
+  PrecondWs pws;
   ops.precond = [&](const float *in, float *out, cudaStream_t st) {
     for (int q = 0; q < S; ++q)
       for (int c = 0; c < ms; ++c) {
         const int col = q * ms + c;
         const float *r = in + (int64_t)col * N;
         float *z = out + (int64_t)col * N;
-        if (cores[col]) KRR_TRY(nystrom_apply_f32(factors[q], cores[col], r, 1, z, st));
+        if (cores[col]) KRR_TRY(nystrom_apply_f32(factors[q], cores[col], r, 1, z, st, &pws));
         else KRR_TRY(scale<float>(r, z, N, 1.0 / lam[col], st));
       }
     return KRR_OK;
@@ -357,6 +363,7 @@ krr_status pcg_solve_batched_device(const double *Xd, int64_t N, int d, int S,
     info->kernel_entries = kmv_entries(N) * ((double)S * rs.products32 + (double)S * rs.products64);
     info->t_build_s = t_build;
     info->t_solve_s = seconds_since(t1);
+    pcg_counters_take(&info->graph_replays, &info->host_checks);
   }
   if (rs.status == KRR_ENOCONV)
     set_error("batched PCG did not reach the tolerance (%.3e > %.3e)", rs.relres, tol);
@@ -381,6 +388,7 @@ __global__ void add_f64_kernel(double *__restrict__ x, const double *__restrict_
 krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, double tol,
                               int maxit, double *beta, cudaStream_t s, krr_info *info) {
   auto t1 = std::chrono::steady_clock::now();
+  pcg_counters_take(nullptr, nullptr);
   const int k = P->k;
   DevBuf<double> b, tmp, r, dx, mx, u64, v64;
   KRR_TRY(b.alloc((size_t)k * m, s));
@@ -458,6 +466,7 @@ krr_status krill_solve_device(const krill_precond *P, const double *Y, int m, do
     info->kernel_entries = entries;
     info->t_build_s = P->build_s;
     info->t_solve_s = seconds_since(t1);
+    pcg_counters_take(&info->graph_replays, &info->host_checks);
   }
   if (breakdown && final_status != KRR_OK) {
     set_error("KRILL PCG breakdown");
@@ -502,8 +511,9 @@ krr_status escalate_refine(Escalation &e, cudaStream_t s) {
   ops.product = [&](const double *in, double *out, cudaStream_t st) {
     return kmv_ff(*e.Pff, e.lambda, in, N, m, out, N, st, *e.ffpart, *e.ffvsplit);
   };
+  PrecondWs pws;
   ops.precond = [&](const double *in, double *out, cudaStream_t st) {
-    return nystrom_apply_f64(&view, core, in, m, out, st);
+    return nystrom_apply_f64(&view, core, in, m, out, st, &pws);
   };
   // second stage: the float-float product's own rounding (about 2^-48 of
   // sum_j |a_ij x_j|) can reach the order of the residual; residuals then come
