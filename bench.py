@@ -377,8 +377,9 @@ def run_native(args):
     kmv_n = sum(i["kmv_launches"] for i in infos)
     per_launch_ms = kmv_ms / max(kmv_n, 1)
     sm_max = clk.get("sm_max_mhz") or 2070.0
+    variant_ms = None
     if args.product_path == "tensor":
-        tile = K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)[0]
+        tile, variant_ms = K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)
     else:
         tile = K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)
     kmv64_ms = sum(i["kmv64_ms"] for i in infos)
@@ -416,6 +417,7 @@ def run_native(args):
                 "kmv32_tile_autotuned": tile,
                 "kmv32_tile_kind": ("epilogue variant" if args.product_path == "tensor"
                                     else "column splits"),
+                "kmv32_variant_ms": variant_ms,
                 "product_path": args.product_path},
         "roofline": product_roofline(args.product_path, w, per_launch_ms, tile, sm_max),
         "clocks": clk,

@@ -140,6 +140,123 @@ krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k) {
   return KRR_OK;
 }
 
+// ------------------------------------------- float-float Schur update
+// C(M x N) -= A(M x K) B(K x N) for float64 data, with the products and sums
+// in float-float arithmetic on the float32 pipes (float64 runs at a small
+// fraction of the float32 rate on this GPU).  Each float64 input is split
+// into hi = fl32(a) and lo = fl32(a - hi) (48 bits) when its tile is staged;
+// a product is hi_a hi_b, split exactly into p + e with an FMA (Dekker's
+// TwoProduct), plus the cross terms hi_a lo_b + lo_a hi_b (lo_a lo_b, below
+// 2^-48 |a b|, is dropped); p enters the running sum through Knuth's
+// error-free TwoSum, the rounding error and e through a float32 correction.
+// The pair (sum, correction) is renormalised once per K tile.  Intrinsics
+// keep the compiler from contracting or reassociating the error-free steps.
+// Error: about 2^-48 sqrt(K) max_k |sum_{l<=k} a_il b_lj| per entry.
+__global__ void __launch_bounds__(G_THREADS)
+gemm_sub_ff_kernel(int M, int N, int K, const double *__restrict__ A, int64_t sai,
+                   int64_t sak, const double *__restrict__ B, int64_t sbk, int64_t sbj,
+                   double *__restrict__ C, int64_t ldc) {
+  __shared__ float Ah[GB_K][GB_M + 1], Al[GB_K][GB_M + 1];
+  __shared__ float Bh[GB_K][GB_N + 1], Bl[GB_K][GB_N + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.0f;
+  const bool a_kfast = (sak == 1 && sai != 1);
+  const bool b_kfast = (sbk == 1 && sbj != 1);
+  for (int k0 = 0; k0 < K; k0 += GB_K) {
+#pragma unroll
+    for (int e = 0; e < (GB_M * GB_K) / G_THREADS; ++e) {
+      const int idx = tid + e * G_THREADS;
+      int ii, kk;
+      if (a_kfast) { kk = idx % GB_K; ii = idx / GB_K; }
+      else { ii = idx % GB_M; kk = idx / GB_M; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      const double v = (gi < M && gk < K) ? A[(int64_t)gi * sai + (int64_t)gk * sak] : 0.0;
+      const float h = __double2float_rn(v);
+      Ah[kk][ii] = h;
+      Al[kk][ii] = __double2float_rn(v - (double)h);
+    }
+#pragma unroll
+    for (int e = 0; e < (GB_N * GB_K) / G_THREADS; ++e) {
+      const int idx = tid + e * G_THREADS;
+      int jj, kk;
+      if (b_kfast) { kk = idx % GB_K; jj = idx / GB_K; }
+      else { jj = idx % GB_N; kk = idx / GB_N; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      const double v = (gj < N && gk < K) ? B[(int64_t)gk * sbk + (int64_t)gj * sbj] : 0.0;
+      const float h = __double2float_rn(v);
+      Bh[kk][jj] = h;
+      Bl[kk][jj] = __double2float_rn(v - (double)h);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GB_K; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        ah[r] = Ah[kk][ty + 16 * r];
+        al[r] = Al[kk][ty + 16 * r];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        bh[c] = Bh[kk][tx + 16 * c];
+        bl[c] = Bl[kk][tx + 16 * c];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float p = __fmul_rn(ah[r], bh[c]);
+          float e = __fmaf_rn(ah[r], bh[c], -p);
+          e = __fmaf_rn(ah[r], bl[c], e);
+          e = __fmaf_rn(al[r], bh[c], e);
+          const float t = __fadd_rn(sh[r][c], p);
+          const float z = __fsub_rn(t, sh[r][c]);
+          const float err = __fadd_rn(__fsub_rn(sh[r][c], __fsub_rn(t, z)), __fsub_rn(p, z));
+          sh[r][c] = t;
+          sl[r][c] = __fadd_rn(sl[r][c], __fadd_rn(err, e));
+        }
+    }
+    __syncthreads();
+    // renormalise once per tile (TwoSum): the correction stays below an ulp
+    // of the sum, so its own roundings stay at the float-float level
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float t = __fadd_rn(sh[r][c], sl[r][c]);
+        const float z = __fsub_rn(t, sh[r][c]);
+        sl[r][c] = __fadd_rn(__fsub_rn(sh[r][c], __fsub_rn(t, z)), __fsub_rn(sl[r][c], z));
+        sh[r][c] = t;
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+      if (gi < M && gj < N) {
+        double *dst = C + (int64_t)gi + (int64_t)gj * ldc;
+        *dst = *dst - ((double)sh[r][c] + (double)sl[r][c]);
+      }
+    }
+}
+
+krr_status gemm_sub_ff(const Gemm<double> &g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return KRR_OK;
+  KRR_REQUIRE(g.alpha == -1.0 && g.beta == 1.0, "gemm_sub_ff: C -= A B only");
+  dim3 grid((g.M + GB_M - 1) / GB_M, (g.N + GB_N - 1) / GB_N, 1);
+  gemm_sub_ff_kernel<<<grid, G_THREADS, 0, s>>>(g.M, g.N, g.K, g.A, g.sai, g.sak, g.B, g.sbk,
+                                                g.sbj, g.C, g.ldc);
+  KRR_LAUNCH_CHECK();
+  return KRR_OK;
+}
+
 // ------------------------------------------------------------ Gram (F^T F)
 // Lower-triangular output tiles only.  float input: each K tile of GB_K
 // products is summed in float32, then added to float64 accumulators (one

@@ -25,6 +25,11 @@ struct Gemm {
 template <typename T>
 krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k = 1);
 
+// C -= A B (alpha = -1, beta = 1) for float64 data with float-float products
+// and sums on the float32 pipes: about 2^-48 sqrt(K) times the largest
+// partial sum per entry.
+krr_status gemm_sub_ff(const Gemm<double> &g, cudaStream_t s);
+
 // Lower triangle of C (r x r, column-major) = F^T F for F N x r column-major.
 // float F: float32 products summed in float32 over 16-term chunks, then in
 // float64; double F: float64.  The strict upper triangle of C is untouched.

@@ -87,25 +87,29 @@ __global__ void tall_t_reduce_kernel(const double *__restrict__ part, int nb, in
   if (lane == 0) t[(int64_t)c * rank + l] = acc;
 }
 
-// Triangular products with one warp per output row, reading contiguous
-// columns of a column-major rank x rank matrix Mt:
+// Triangular products with one block of TRI_THREADS threads per output row,
+// reading contiguous columns of a column-major rank x rank matrix Mt:
 //   UPPER == false: out[c][i] = sum_{l <= i} Mt[l + i rank] x[c][l]
 //   UPPER == true : out[c][i] = sum_{l >= i} Mt[l + i rank] x[c][l]
 // With Mt = W^T (W lower) the first is W x; with Mt = W the second is W^T x.
+// A row is split across four warps (a row of about rank / 2 entries per warp
+// would leave too few loads in flight to stream Mt); per column the warps'
+// sums are added in warp order.
+constexpr int TRI_THREADS = 128;
+
 template <bool UPPER>
-__global__ void tri_gemv_kernel(const double *__restrict__ Mt, int rank,
-                                const double *__restrict__ x, int m,
-                                double *__restrict__ out) {
-  const int warps = blockDim.x >> 5;
-  const int i = blockIdx.x * warps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= rank) return;
+__global__ void __launch_bounds__(TRI_THREADS)
+tri_gemv_kernel(const double *__restrict__ Mt, int rank, const double *__restrict__ x, int m,
+                double *__restrict__ out) {
+  __shared__ double red[TRI_THREADS / 32][16];
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = 0.0;
   const double *col = Mt + (int64_t)i * rank;
   const int lo = UPPER ? i : 0, hi = UPPER ? rank : i + 1;
-  for (int l = lo + lane; l < hi; l += 32) {
+  for (int l = lo + threadIdx.x; l < hi; l += TRI_THREADS) {
     const double w = col[l];
 #pragma unroll
     for (int c = 0; c < 16; ++c)
@@ -115,8 +119,15 @@ __global__ void tri_gemv_kernel(const double *__restrict__ Mt, int rank,
   for (int c = 0; c < 16; ++c) {
     if (c < m) {
       const double v = warp_sum(acc[c]);
-      if (lane == 0) out[(int64_t)c * rank + i] = v;
+      if (lane == 0) red[warp][c] = v;
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < TRI_THREADS / 32; ++w) t += red[w][threadIdx.x];
+    out[(int64_t)threadIdx.x * rank + i] = t;
   }
 }
 
@@ -618,14 +629,16 @@ __global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__
 
 krr_status tri_apply_lower(const double *Wt, int rank, const double *t, int m, double *u,
                            cudaStream_t s) {
-  tri_gemv_kernel<false><<<ceil_div(rank, 8), 256, 0, s>>>(Wt, rank, t, m, u);
+  if (rank == 0) return KRR_OK;
+  tri_gemv_kernel<false><<<rank, TRI_THREADS, 0, s>>>(Wt, rank, t, m, u);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
 
 krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
                              cudaStream_t s) {
-  tri_gemv_kernel<true><<<ceil_div(rank, 8), 256, 0, s>>>(W, rank, u, m, v);
+  if (rank == 0) return KRR_OK;
+  tri_gemv_kernel<true><<<rank, TRI_THREADS, 0, s>>>(W, rank, u, m, v);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }

@@ -176,6 +176,11 @@ __global__ void uniform_pivots_kernel(int64_t N, int k, uint64_t seed, unsigned 
 // the smallest index); npick = 1 is the paper's rule.  One CTA; pick j is the
 // largest (value, -index) strictly below pick j - 1 in that order.
 constexpr int GREEDY_THREADS = 1024;
+
+// Smallest N whose Schur updates take the float-float GEMM: the drop
+// threshold N 2^-52 max A_ii is then at least 7e-12, about 70 times the
+// float-float rounding of a partial sum of magnitude 1 over 1000 terms.
+constexpr int64_t kSchurFFMinN = 32768;
 __global__ void __launch_bounds__(GREEDY_THREADS)
 greedy_pick_kernel(const double *__restrict__ dres, int64_t N, double dfloor, int npick,
                    int64_t *__restrict__ cand, int *__restrict__ counts) {
@@ -457,7 +462,11 @@ krr_status rpcholesky_device(const double *Xd, int64_t N, int d, int kern, doubl
       g.A = f->F; g.sai = 1; g.sak = N;
       g.B = Fs.p; g.sbk = nc; g.sbj = 1;
       g.alpha = -1.0; g.beta = 1.0; g.C = G.p; g.ldc = N;
-      KRR_TRY(gemm(g, s));
+      // float-float on the float32 pipes where its rounding (about 1e-13 of
+      // the partial sums) stays two orders below the drop threshold
+      // N 2^-52 max A_ii; float64 below that size
+      if (N >= kSchurFFMinN) KRR_TRY(gemm_sub_ff(g, s));
+      else KRR_TRY(gemm(g, s));
     }
     block_chol_kernel<<<1, 256, (size_t)nc * nc * sizeof(double), s>>>(G.p, N, cand.p, nc, thr,
                                                                      Lb.p, kept.p, counts.p + 2);
