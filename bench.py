@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--product-path", default="tensor", choices=["tensor", "fma", "mma_sync"],
                     help="float32 product: inner products on the tensor cores, or all FMA")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end step")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the short runs of the other configurations (c1, c3, c4)")
     ap.add_argument("--no-pcg-graphs", action="store_true",
                     help="step the PCG iterations one launch at a time (no CUDA graphs)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -451,6 +453,15 @@ def run_native(args):
                                "status": i64["status"],
                                "speedup_mixed_vs_fp64": t64 / (total_ms / args.steps / 1e3)}
 
+    if rank == 0 and world == 1 and not args.no_configs:
+        # the other configurations, short runs (3 warm-up and 2 timed steps each):
+        # plain float64 (c1), the batched product (c3), KRILL (c4)
+        result["configs"] = {}
+        for name in ("c1", "c3", "c4"):
+            r = measure_config(K, name, 2, 3)
+            r.pop("metric", None)
+            result["configs"][name] = r
+
     # end to end through the C ABI with host buffers (copies inside the region)
     if args.no_e2e:
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -625,6 +636,19 @@ def run_serving(args):
 
 
 def run_config(args):
+    """The other configurations (--workload c1|c3|c4) as their own bench line."""
+    import paper_2304_12465_gb300 as K
+
+    dist, rank, world = dist_setup(args.gpus)
+    K.load()
+    res = measure_config(K, args.workload, args.steps, args.warmup, dist, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure_config(K, workload, steps, warmup, dist=None, rank=0, world=1):
     """The other configurations, one step each:
     c1 -- plain float64 path: RPCholesky (k = 200, B = 20) + float64 PCG to 1e-10,
           N = 4096, d = 8;
@@ -632,18 +656,16 @@ def run_config(args):
           tile generation, N = 500000, d = 8 (the product a batched PCG iteration runs);
     c4 -- KRILL: krill_build (sparse sign sketch, Gram, Cholesky) + krill_solve
           (refined PCG to 1e-6), N = 2e6, d = 20, k = 2000 centers.
-    value = kernel entries evaluated per second over the step."""
+    value = kernel entries evaluated per second over the step.  Returns the
+    result (rank 0) or None."""
     import torch
-    import paper_2304_12465_gb300 as K
     from inputs import make_c1_plain_fp64, make_c3_batched, make_c4_krill
 
-    dist, rank, world = dist_setup(args.gpus)
-    K.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     extra = {}
-    if args.workload == "c1":
+    if workload == "c1":
         w = make_c1_plain_fp64()
         X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
 
@@ -658,7 +680,7 @@ def run_config(args):
         desc = (f"plain float64 KRR, N={w.N}, d={w.d}, Gaussian sigma={w.sigma}, mu={w.mu}, "
                 f"RPCholesky k={w.k} B={w.block}, float64 PCG to {w.tol}")
         dtype = "f64"
-    elif args.workload == "c3":
+    elif workload == "c3":
         w = make_c3_batched()
         X = torch.from_numpy(w.X).to(dev)
         kerns = [k for k, _ in w.settings]
@@ -701,7 +723,7 @@ def run_config(args):
                 f"Gaussian sigma={w.sigma}, mu={w.mu}, sparse sign s=2k, tol {w.tol}")
         dtype = "f32+f64"
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -711,7 +733,7 @@ def run_config(args):
     clocks.start()
     launches0 = K.krr_launch_count()
     step_ms, entries, infos = [], 0.0, []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -727,39 +749,38 @@ def run_config(args):
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
     total_ms, entries = aggregate_ranks(dist, total_ms, entries, dev)
-    if rank == 0:
-        res = {"metric": METRIC, "value": entries / (total_ms / 1e3), "unit": UNIT,
-               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-               "config": {"workload": desc, "N": w.N, "d": w.d,
-                          "l2": "flushed between timed steps (512 MiB write)",
-                          "parallelism": "replicas" if world > 1 else "single GPU", **extra},
-               "clocks": clk, "gpu_launches": int(launches)}
-        if args.workload == "c3":
-            pairs = float(w.N) * w.N
-            sec = total_ms / args.steps / 1e3
-            sm_max = clk.get("sm_max_mhz") or 2070.0
-            peak_flop = 152 * 128 * 2 * sm_max * 1e6
-            peak_mufu = 152 * 32 * sm_max * 1e6
-            t_flop = pairs * extra["roofline_model"]["flop_per_pair"] / peak_flop
-            t_mufu = pairs * extra["roofline_model"]["mufu_per_pair"] / peak_mufu
-            res["roofline"] = {
-                "kernel": "kmvb_kernel (batched 8-setting product)", "bound": "alu",
-                "achieved": pairs * extra["roofline_model"]["flop_per_pair"] / sec / 1e12,
-                "peak": peak_flop / 1e12, "unit": "TFLOP/s",
-                "frac": max(t_flop, t_mufu) / sec, "traffic": None,
-                "peak_basis": f"FP32 152 x 128 x 2 x {sm_max:.0f} MHz and MUFU 152 x 32 "
-                              f"x {sm_max:.0f} MHz (derived); frac = the larger of the FP32 "
-                              f"and MUFU times over the measured time",
-                "fp32_time_s": t_flop, "mufu_time_s": t_mufu}
-        if infos and infos[0]:
-            res["solve"] = {k: [i.get(k) for i in infos] for k in
-                            ("iters", "outer_refinements", "rel_residual", "t_build_s",
-                             "t_solve_s")}
-        print(json.dumps(res), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    res = {"metric": METRIC, "value": entries / (total_ms / 1e3), "unit": UNIT,
+           "n_gpus": world, "steps": steps, "warmup": warmup,
+           "ms_per_step": total_ms / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": {"workload": desc, "N": w.N, "d": w.d,
+                      "l2": "flushed between timed steps (512 MiB write)",
+                      "parallelism": "replicas" if world > 1 else "single GPU", **extra},
+           "clocks": clk, "gpu_launches": int(launches)}
+    if workload == "c3":
+        pairs = float(w.N) * w.N
+        sec = total_ms / steps / 1e3
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_flop = 152 * 128 * 2 * sm_max * 1e6
+        peak_mufu = 152 * 32 * sm_max * 1e6
+        t_flop = pairs * extra["roofline_model"]["flop_per_pair"] / peak_flop
+        t_mufu = pairs * extra["roofline_model"]["mufu_per_pair"] / peak_mufu
+        res["roofline"] = {
+            "kernel": "kmvb_kernel (batched 8-setting product)", "bound": "alu",
+            "achieved": pairs * extra["roofline_model"]["flop_per_pair"] / sec / 1e12,
+            "peak": peak_flop / 1e12, "unit": "TFLOP/s",
+            "frac": max(t_flop, t_mufu) / sec, "traffic": None,
+            "peak_basis": f"FP32 152 x 128 x 2 x {sm_max:.0f} MHz and MUFU 152 x 32 "
+                          f"x {sm_max:.0f} MHz (derived); frac = the larger of the FP32 "
+                          f"and MUFU times over the measured time",
+            "fp32_time_s": t_flop, "mufu_time_s": t_mufu}
+    if infos and infos[0]:
+        res["solve"] = {k: [i.get(k) for i in infos] for k in
+                        ("iters", "outer_refinements", "rel_residual", "t_build_s",
+                         "t_solve_s")}
+    return res
 
 
 def cpu_baseline(w, target_s: float = 6.0):
