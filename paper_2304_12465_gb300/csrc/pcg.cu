@@ -44,29 +44,42 @@ tall_t_kernel(const T *__restrict__ F, int64_t N, int rank, const T *__restrict_
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
   const int l1 = min(rank, (int)(blockIdx.y + 1) * TT_COLS);
-  for (int l = (int)blockIdx.y * TT_COLS + warp; l < l1; l += blockDim.x >> 5) {
+  // two columns per pass: each R value read from shared memory serves both
+  for (int l = (int)blockIdx.y * TT_COLS + warp; l < l1; l += 2 * nw) {
+    const bool two = l + nw < l1;
     const T *col = F + (int64_t)l * N + n0;
-    T f[PER_LANE];
+    const T *col2 = col + (int64_t)nw * N;
+    T f[PER_LANE], g[PER_LANE];
 #pragma unroll
     for (int q = 0; q < PER_LANE; ++q) {
       const int n = lane + 32 * q;
       f[q] = (n < nr) ? col[n] : T(0);
+      g[q] = (two && n < nr) ? col2[n] : T(0);
     }
-    T acc[M];
+    T acc[M], acc2[M];
 #pragma unroll
-    for (int c = 0; c < M; ++c) acc[c] = T(0);
+    for (int c = 0; c < M; ++c) acc[c] = acc2[c] = T(0);
 #pragma unroll
     for (int q = 0; q < PER_LANE; ++q) {
 #pragma unroll
       for (int c = 0; c < M; ++c)
-        if (c < m) acc[c] = fma(f[q], sR[c][lane + 32 * q], acc[c]);
+        if (c < m) {
+          const T r = sR[c][lane + 32 * q];
+          acc[c] = fma(f[q], r, acc[c]);
+          acc2[c] = fma(g[q], r, acc2[c]);
+        }
     }
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       if (c < m) {
         const T v = warp_sum(acc[c]);
-        if (lane == 0) part[((int64_t)blockIdx.x * rank + l) * m + c] = (double)v;
+        const T v2 = warp_sum(acc2[c]);
+        if (lane == 0) {
+          part[((int64_t)blockIdx.x * rank + l) * m + c] = (double)v;
+          if (two) part[((int64_t)blockIdx.x * rank + l + nw) * m + c] = (double)v2;
+        }
       }
     }
   }
@@ -132,8 +145,9 @@ tri_gemv_kernel(const double *__restrict__ Mt, int rank, const double *__restric
 }
 
 // Z[c][n] = (R[c][n] - sum_l F[n + l N] v[c][l]) / lambda
-// One thread per row; the column loop loads LU values of F before using them
-// so that enough loads are in flight to stream F at HBM speed.  M as above.
+// One thread per row (blocks of TN_THREADS); the column loop loads LU
+// values of F before using them so that enough loads are in flight to stream
+// F at HBM speed.  M as above.
 template <typename T, int M>
 __global__ void __launch_bounds__(256)
 tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
@@ -189,16 +203,21 @@ static krr_status launch_tall_t(const T *F, int64_t N, int rank, const T *R, int
   return KRR_OK;
 }
 
+// Blocks of 64 threads: about ten per SM at N = 1e5, so the last wave of
+// blocks leaves few SMs idle (256-thread blocks left 2.6 per SM).
+constexpr int TN_THREADS = 64;
+
 template <typename T>
 static krr_status launch_tall_n(const T *F, int64_t N, int rank, const double *v, int m,
                                 const T *R, double inv_lambda, T *Z, cudaStream_t s) {
-  const unsigned grid = ceil_div(N, 256);
+  const unsigned grid = ceil_div(N, TN_THREADS);
+  constexpr int B = TN_THREADS;
   switch (tall_pad_m(m)) {
-    case 1: tall_n_kernel<T, 1><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
-    case 2: tall_n_kernel<T, 2><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
-    case 4: tall_n_kernel<T, 4><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
-    case 8: tall_n_kernel<T, 8><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
-    default: tall_n_kernel<T, 16><<<grid, 256, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 1: tall_n_kernel<T, 1><<<grid, B, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 2: tall_n_kernel<T, 2><<<grid, B, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 4: tall_n_kernel<T, 4><<<grid, B, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    case 8: tall_n_kernel<T, 8><<<grid, B, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
+    default: tall_n_kernel<T, 16><<<grid, B, 0, s>>>(F, N, rank, v, m, R, inv_lambda, Z); break;
   }
   KRR_LAUNCH_CHECK();
   return KRR_OK;
@@ -312,18 +331,22 @@ __global__ void dots_kernel(const T *__restrict__ a, const T *__restrict__ b, in
   }
 }
 
-__device__ double sum_parts(const double *part, int nb, int c) {
+// Sum of the nb block partials of column c by one warp: lane l adds partials
+// l, l + 32, ... in order, then a fixed shuffle tree (every lane gets the same
+// bits).  The scalar kernels below run one warp per column (32 m threads).
+__device__ double sum_parts(const double *part, int nb, int c, int lane) {
   double t = 0.0;
-  for (int b = 0; b < nb; ++b) t += part[(int64_t)c * nb + b];
-  return t;
+  for (int b = lane; b < nb; b += 32) t += part[(int64_t)c * nb + b];
+  return warp_sum(t);
 }
 
 // alpha_c = rz_c / (p_c . q_c) for active columns; breakdown flag otherwise.
 __global__ void pcg_alpha_kernel(const double *__restrict__ part, int nb, int m,
                                  PcgScalars *__restrict__ sc) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (c >= m) return;
-  const double pq = sum_parts(part, nb, c);
+  const double pq = sum_parts(part, nb, c, lane);
+  if (lane != 0) return;
   double a = 0.0;
   if (sc->active[c]) {
     if (!(pq > 0.0)) {
@@ -337,16 +360,16 @@ __global__ void pcg_alpha_kernel(const double *__restrict__ part, int nb, int m,
 }
 
 // Convergence test on the recursive residual; advances the iteration
-// counter (one warp: every lane reads the counter before lane 0 writes it).
+// counter (every thread reads it before thread 0 writes it).
 __global__ void pcg_resid_kernel(const double *__restrict__ part, int nb, int m,
                                  PcgScalars *__restrict__ sc) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int it = sc->it + 1;
-  __syncwarp();
-  if (c == 0) sc->it = it;
+  __syncthreads();
+  if (threadIdx.x == 0) sc->it = it;
   if (c >= m) return;
-  const double rr = sum_parts(part, nb, c);
-  if (sc->active[c]) {
+  const double rr = sum_parts(part, nb, c, lane);
+  if (lane == 0 && sc->active[c]) {
     const double rel = sqrt(rr / sc->bb[c]);
     sc->relres[c] = rel;
     sc->iters[c] = it;
@@ -356,9 +379,10 @@ __global__ void pcg_resid_kernel(const double *__restrict__ part, int nb, int m,
 
 __global__ void pcg_beta_kernel(const double *__restrict__ part, int nb, int m,
                                 PcgScalars *__restrict__ sc) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (c >= m) return;
-  const double rz = sum_parts(part, nb, c);
+  const double rz = sum_parts(part, nb, c, lane);
+  if (lane != 0) return;
   double b = 0.0;
   if (sc->active[c]) {
     b = rz / sc->rz[c];
@@ -370,11 +394,13 @@ __global__ void pcg_beta_kernel(const double *__restrict__ part, int nb, int m,
 __global__ void pcg_init_kernel(const double *__restrict__ part_bb,
                                 const double *__restrict__ part_rz, int nb, int m,
                                 const double *__restrict__ tol, PcgScalars *__restrict__ sc) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (c >= m) return;
-  const double bb = sum_parts(part_bb, nb, c);
+  const double bb = sum_parts(part_bb, nb, c, lane);
+  const double rz = sum_parts(part_rz, nb, c, lane);
+  if (lane != 0) return;
   sc->bb[c] = bb;
-  sc->rz[c] = sum_parts(part_rz, nb, c);
+  sc->rz[c] = rz;
   sc->tol[c] = tol[c];
   sc->iters[c] = 0;
   sc->relres[c] = (bb > 0.0) ? 1.0 : 0.0;
@@ -460,6 +486,7 @@ int pcg_remaining(const PcgScalars &h, const double *prev_rel, int prev_it, int 
 template <typename T>
 krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
                    const double *tol_host, int maxit, cudaStream_t s, PcgStats *stats) {
+  KRR_REQUIRE(m >= 1 && m <= PCG_MAX_M, "PCG: 1 to %d columns (got %d)", PCG_MAX_M, m);
   DevBuf<T> r, z, p, q;
   KRR_TRY(r.alloc((size_t)N * m, s));
   KRR_TRY(z.alloc((size_t)N * m, s));
@@ -479,7 +506,7 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
   KRR_LAUNCH_CHECK();
   dots_kernel<T><<<RED_BLOCKS, 256, 0, s>>>(r.p, z.p, N, m, part2.p);
   KRR_LAUNCH_CHECK();
-  pcg_init_kernel<<<1, 32, 0, s>>>(part1.p, part2.p, RED_BLOCKS, m, dtol.p, sc.p);
+  pcg_init_kernel<<<1, 32 * m, 0, s>>>(part1.p, part2.p, RED_BLOCKS, m, dtol.p, sc.p);
   KRR_LAUNCH_CHECK();
   KRR_CUDA_TRY(cudaMemcpyAsync(p.p, z.p, sizeof(T) * (size_t)N * m, cudaMemcpyDeviceToDevice, s));
 
@@ -488,13 +515,13 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
     KRR_TRY(ops.product(p.p, q.p, st));
     dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(p.p, q.p, N, m, part1.p);
     KRR_LAUNCH_CHECK();
-    pcg_alpha_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    pcg_alpha_kernel<<<1, 32 * m, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
     KRR_LAUNCH_CHECK();
     pcg_update_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(x, r.p, p.p, q.p, N, m, sc.p);
     KRR_LAUNCH_CHECK();
     dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(r.p, r.p, N, m, part1.p);
     KRR_LAUNCH_CHECK();
-    pcg_resid_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    pcg_resid_kernel<<<1, 32 * m, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
     KRR_LAUNCH_CHECK();
     return KRR_OK;
   };
@@ -503,7 +530,7 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
     KRR_TRY(ops.precond(r.p, z.p, st));
     dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(r.p, z.p, N, m, part1.p);
     KRR_LAUNCH_CHECK();
-    pcg_beta_kernel<<<1, 32, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
+    pcg_beta_kernel<<<1, 32 * m, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
     KRR_LAUNCH_CHECK();
     pcg_dir_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(p.p, z.p, N, m, sc.p);
     KRR_LAUNCH_CHECK();
@@ -535,7 +562,13 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
   int replays = 0;
   bool graphs = pcg_graphs_on();
   PcgChunk chunks[3];   // 16, 4 and 1 iterations
-  cudaStream_t cs = nullptr;
+  struct CaptureStream {
+    cudaStream_t s = nullptr;
+    ~CaptureStream() {
+      if (s) cudaStreamDestroy(s);
+    }
+  } capture_stream;
+  cudaStream_t &cs = capture_stream.s;
   while (any_active() && h.it < maxit) {
     const int left = maxit - h.it;
     const int need = pcg_remaining(h, prev_rel, prev_it, m);
@@ -581,7 +614,6 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
       KRR_TRY(read_back());
     }
   }
-  if (cs) cudaStreamDestroy(cs);
   t_pcg_replays += replays;
   t_pcg_checks += checks;
   if (stats) {
