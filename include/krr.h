@@ -636,6 +636,16 @@ KRR_API void krr_set_profiling(int on);
 /* KRR_EINVAL for another which or NULL outputs.                              */
 KRR_API krr_status krr_profile_collect(int which, double *ms, int *launches);
 
+/* Diagnostic of the device-side timeout path (engineering, not in the        */
+/* paper).  Launches one thread that waits, with the bounded mbarrier wait of */
+/* the tcgen05 product's roles, on a barrier that no arrival completes, for   */
+/* budget_cycles SM clock cycles (0 .. 2^31; 1e6 is about half a             */
+/* millisecond), then raises the device fault flag as a real timeout does.    */
+/* Synchronises stream.  Returns KRR_ETIMEOUT once the wait gave up and the   */
+/* flag was read and cleared -- the expected result; the context stays       */
+/* usable -- and KRR_EINVAL for a budget out of range.                        */
+KRR_API krr_status krr_check_bounded_wait(int64_t budget_cycles, void *stream);
+
 /* Message for the last failure on the calling thread ("" if none). */
 KRR_API const char *krr_last_error(void);
 

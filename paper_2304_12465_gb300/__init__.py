@@ -26,6 +26,7 @@ from .api import (  # noqa: F401
     krr_autotune_choice,
     krr_set_autotune,
     krr_set_pcg_graphs,
+    krr_check_bounded_wait,
     krr_set_product_path,
     krr_set_product_variant,
     krr_autotune_variant,

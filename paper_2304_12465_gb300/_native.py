@@ -137,6 +137,7 @@ SIGNATURES = {
     "krr_server_destroy": (None, [_vp]),
     "krr_set_autotune": (None, [_int]),
     "krr_set_pcg_graphs": (None, [_int]),
+    "krr_check_bounded_wait": (_int, [_i64, _vp]),
     "krr_autotune_choice": (_int, [_int, _int, _int, _i64, C.POINTER(_int)]),
     "krr_set_product_path": (_int, [_int]),
     "krr_set_product_variant": (_int, [_int]),

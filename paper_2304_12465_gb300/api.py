@@ -379,6 +379,15 @@ def krr_set_pcg_graphs(on: bool) -> None:
     load().krr_set_pcg_graphs(1 if on else 0)
 
 
+def krr_check_bounded_wait(budget_cycles: int = 1_000_000, stream=None) -> str:
+    """Runs a device-side bounded wait that cannot complete; returns the
+    status name ('KRR_ETIMEOUT' when the timeout path worked)."""
+    st = load().krr_check_bounded_wait(int(budget_cycles), _stream(stream))
+    if st not in (N_.KRR_OK, N_.KRR_ETIMEOUT):
+        check(st, "krr_check_bounded_wait")
+    return N_.STATUS_NAMES[st]
+
+
 def krr_autotune_choice(kern, d: int, m: int, N: int) -> int:
     """Split count the autotuner chose for a float32 product shape (0: none)."""
     v = C.c_int()

@@ -271,6 +271,11 @@ void krr_set_autotune(int on) { set_autotune(on != 0); }
 
 void krr_set_pcg_graphs(int on) { set_pcg_graphs(on != 0); }
 
+krr_status krr_check_bounded_wait(int64_t budget_cycles, void *stream) {
+  clear_error();
+  return tc5_wait_selftest((long long)budget_cycles, (cudaStream_t)stream);
+}
+
 krr_status krr_autotune_choice(krr_kernel kern, int d, int m, int64_t N, int *splits) {
   clear_error();
   KRR_REQUIRE(splits, "splits is NULL");

@@ -68,6 +68,8 @@ bool autotune_on();
 // Raises KRR_ETIMEOUT (and clears the flag) when a bounded device-side wait
 // of the tcgen05 product gave up since the last check; synchronises s.
 krr_status tc5_check_fault(cudaStream_t s);
+// Runs a bounded wait that cannot complete; KRR_ETIMEOUT once it gave up.
+krr_status tc5_wait_selftest(long long budget, cudaStream_t s);
 
 struct KmvTcArgs {
   const uint4 *xs;

@@ -179,6 +179,29 @@ krr_status tc5_check_fault(cudaStream_t s) {
   return KRR_OK;
 }
 
+// Diagnostic of the bounded waits: one thread waits on an mbarrier that no
+// arrival ever completes, for `budget` SM clock cycles, with the routine the
+// product's roles use, then takes the timeout path (the fault flag).
+__global__ void t5_wait_selftest_kernel(int *fault, long long budget) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = bw::smem_u32(&bar);
+  bw::mbar_init(b, 1);
+  abort_flag = 0;
+  bw::fence_mbar_init();
+  if (!bw::mbar_wait_abortable(b, 0, budget, &abort_flag)) atomicOr(fault, 1);
+}
+
+krr_status tc5_wait_selftest(long long budget, cudaStream_t s) {
+  KRR_REQUIRE(budget >= 0 && budget <= (1LL << 31), "wait budget: 0 to 2^31 cycles");
+  int *f = fault_ptr();
+  KRR_REQUIRE(f != nullptr, "no fault flag on this device");
+  t5_wait_selftest_kernel<<<1, 32, 0, s>>>(f, budget);
+  KRR_LAUNCH_CHECK();
+  return tc5_check_fault(s);
+}
+
 // ------------------------------------------------------------ reduction
 __global__ void t5_reduce_kernel(const float *__restrict__ part, int64_t Nr, int m, int M, int C,
                                  int64_t T, int G, int J, int CG, const int *__restrict__ vexp,

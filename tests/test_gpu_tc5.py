@@ -164,3 +164,17 @@ def test_tcgen05_autotuner_report(K):
     assert all((ms[v - 1] > 0) == (v in timed) for v in range(1, 12))
     ref = O.kmatvec(X, O.GAUSSIAN, 0.9, 0.2, V)
     assert np.all(np.abs(got - ref) <= 2e-5 * f32_product_bound(X, O.GAUSSIAN, 0.9, 0.2, V))
+
+
+def test_bounded_wait_gives_up_and_reports(K):
+    """The product's bounded mbarrier wait, on a barrier that nothing
+    completes, gives up after its budget (about half a millisecond here),
+    raises the device fault flag, and the host reads KRR_ETIMEOUT; the flag is
+    cleared and the context stays usable: the next product is correct."""
+    assert K.krr_check_bounded_wait(1_000_000) == "KRR_ETIMEOUT"
+    assert K.krr_check_bounded_wait(0) == "KRR_ETIMEOUT"
+    X, V = _case(700, 16, 4, 77)
+    ref = O.kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V)
+    bound = f32_product_bound(X, O.GAUSSIAN, 1.1, 0.5, V)
+    got = K.krr_kmatvec(X, O.GAUSSIAN, 1.1, 0.5, V, prec="mixed")
+    assert np.all(np.abs(got - ref) <= 2e-5 * bound)
