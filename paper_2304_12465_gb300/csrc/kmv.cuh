@@ -54,10 +54,12 @@ krr_status prepare_points_tc5(const double *Xd, cudaStream_t s, PointsF32 &P, in
 
 // tcgen05 product Y (R.N x m) = K(R, P) V, + lambda V when square (R is P);
 // both point sets carry tcgen05 operands prepared with the same centre and
-// scale.  V: m x ldv over P's points; Y: m x ldy over R's points.
+// scale.  V: m x ldv over P's points; Y: m x ldy over R's points.  quiet:
+// the process's forced variant or the default one, never tuned or timed (the
+// serving engine's products, launched into captured graphs).
 krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool square,
                    const float *V, int64_t ldv, int m, float *Y, int64_t ldy, cudaStream_t s,
-                   DevBuf<float> &part);
+                   DevBuf<float> &part, bool quiet = false);
 
 // Epilogue variant of the tcgen05 product (see krr_set_product_variant), and
 // the autotuner's choice and per-variant times for a square shape.

@@ -458,9 +458,11 @@ static cudaError_t t5_launch(const PointsF32 &R, const PointsF32 &P, int M, int 
 // Variant for this product: forced, cached, tuned now, or the default.
 static int choose_variant(const PointsF32 &R, const PointsF32 &P, bool square, int M,
                           const float *Vg,
-                          int64_t ldv, int mg, DevBuf<float> &part, int *fault, cudaStream_t s) {
+                          int64_t ldv, int mg, DevBuf<float> &part, int *fault, cudaStream_t s,
+                          bool quiet) {
   const int forced = g_t5_variant.load();
   if (forced > 0 && t5_variant_valid(forced, M, square)) return forced;
+  if (quiet) return t5_default_variant(M, square);
   const auto key = std::make_tuple(P.kern, P.nh5, P.csep5, M, R.N, P.N, square);
   {
     std::lock_guard<std::mutex> lk(g_t5_mtx);
@@ -513,7 +515,7 @@ static int choose_variant(const PointsF32 &R, const PointsF32 &P, bool square, i
 
 krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool square,
                    const float *V, int64_t ldv, int m, float *Y, int64_t ldy, cudaStream_t s,
-                   DevBuf<float> &part) {
+                   DevBuf<float> &part, bool quiet) {
   const int64_t Nr = R.N, Nc = P.N;
   if (Nr == 0 || Nc == 0 || m == 0) return KRR_OK;
   KRR_REQUIRE(R.nh5 > 0 && P.nh5 == R.nh5 && P.csep5 == R.csep5 && R.kern == P.kern,
@@ -524,11 +526,11 @@ krr_status kmv_tc5(const PointsF32 &R, const PointsF32 &P, float lambda, bool sq
     const int mg = std::min(8, m - c0);
     const int M = mg <= 2 ? 2 : mg <= 4 ? 4 : 8;
     const float *Vg = V + (int64_t)c0 * ldv;
-    const int variant = choose_variant(R, P, square, M, Vg, ldv, mg, part, fault, s);
+    const int variant = choose_variant(R, P, square, M, Vg, ldv, mg, part, fault, s, quiet);
     const T5Geometry g = t5_geometry(Nr, Nc, t5_variant_tn(variant));
     const size_t need = t5_scratch_floats(g, M);
     if (part.n < need) KRR_TRY(part.alloc(need, s));
-    cudaError_t e = t5_launch(R, P, M, variant, g, Vg, ldv, mg, part.p, fault, s, true);
+    cudaError_t e = t5_launch(R, P, M, variant, g, Vg, ldv, mg, part.p, fault, s, !quiet);
     if (e != cudaSuccess) {
       set_error("tcgen05 product launch failed: %s", cudaGetErrorString(e));
       return KRR_ECUDA;

@@ -547,14 +547,30 @@ struct ProductBranches {
   cudaEvent_t join[SERVE_BRANCHES] = {};
 };
 
+// The product of one slot that runs as its own tcgen05 launch (ServeSlotDesc::
+// tc5): y = K p without the shift, written as the slot's single split of
+// partial sums, so the grouped reduction adds lambda p as for the others.
+struct Tc5Job {
+  const PointsF32 *P;
+  const float *p;
+  float *y;
+  int m;
+  DevBuf<float> *scratch;
+};
+
+// Kernels one tcgen05 job launches per iteration (right-hand-side staging,
+// product, segment reduction per group of 8 right-hand sides).
+static int tc5_job_kernels(const Tc5Job &j) { return 3 * ((j.m + 7) / 8); }
+
 // (A + lambda I) p partial sums of every slot of T: one launch per variant
-// present (Th: host copy of the table at T), forked onto parallel branches and
-// joined back into s.
+// present (Th: host copy of the table at T) and one tcgen05 product per job,
+// forked onto parallel branches and joined back into s.
 static krr_status serve_launch_product(const ServeTable *T, const ServeTable *Th,
-                                       const ProductBranches &B, cudaStream_t s) {
-  const int nc = Th->nclasses;
-  if (nc == 0) return KRR_OK;
-  const int nb = nc < SERVE_BRANCHES ? nc : SERVE_BRANCHES;
+                                       const ProductBranches &B,
+                                       const std::vector<Tc5Job> &jobs, cudaStream_t s) {
+  const int nc = Th->nclasses, nj = (int)jobs.size();
+  if (nc + nj == 0) return KRR_OK;
+  const int nb = nc + nj < SERVE_BRANCHES ? nc + nj : SERVE_BRANCHES;
   KRR_CUDA_TRY(cudaEventRecord(B.fork, s));
   for (int b = 0; b < nb; ++b) KRR_CUDA_TRY(cudaStreamWaitEvent(B.side[b], B.fork, 0));
   for (int c = 0; c < nc; ++c) {
@@ -570,6 +586,11 @@ static krr_status serve_launch_product(const ServeTable *T, const ServeTable *Th
     count_launch();
     KRR_CUDA_TRY(e);
   }
+  for (int j = 0; j < nj; ++j) {
+    const Tc5Job &J = jobs[j];
+    KRR_TRY(kmv_tc5(*J.P, *J.P, 0.0f, false, J.p, J.P->N, J.m, J.y, J.P->N,
+                    B.side[(nc + j) % nb], *J.scratch, true));
+  }
   for (int b = 0; b < nb; ++b) {
     KRR_CUDA_TRY(cudaEventRecord(B.join[b], B.side[b]));
     KRR_CUDA_TRY(cudaStreamWaitEvent(s, B.join[b], 0));
@@ -581,12 +602,13 @@ static krr_status serve_launch_product(const ServeTable *T, const ServeTable *Th
 // single-solve loop: product, alpha, update, convergence test,
 // preconditioner, beta, direction.
 static krr_status serve_launch_iterations(const ServeTable *T, const ServeTable *Th,
-                                          const ProductBranches &B, int U, cudaStream_t s,
-                                          PhaseEvents *pe = nullptr) {
+                                          const ProductBranches &B,
+                                          const std::vector<Tc5Job> &jobs, int U,
+                                          cudaStream_t s, PhaseEvents *pe = nullptr) {
   const unsigned g = serve_vec_grid();
   if (pe) KRR_TRY(pe->mark(s));
   for (int it = 0; it < U; ++it) {
-    KRR_TRY(serve_launch_product(T, Th, B, s));
+    KRR_TRY(serve_launch_product(T, Th, B, jobs, s));
     if (pe) KRR_TRY(pe->mark(s));
     serve_reduce_kernel<<<g, SERVE_VB, 0, s>>>(T);
     KRR_LAUNCH_CHECK();
@@ -701,6 +723,7 @@ struct Slot {
   void *arena = nullptr;
   krr::DevBuf<double> ffpart;
   krr::DevBuf<float> ffvsplit;
+  krr::DevBuf<float> t5scratch;   // segment partials and staged p of a tcgen05 product
   double *Y64 = nullptr, *alpha64 = nullptr, *r64 = nullptr, *mx64 = nullptr;
   ServeSlotDesc desc{};
   // refinement bookkeeping (as the single-solve driver)
@@ -741,6 +764,9 @@ namespace krr {
 // solve's steps are not paced by the largest slot's iterations.
 constexpr int SERVE_LANES = 2;
 constexpr double SERVE_FAST_LANE_FLOP = 4e10;   // float32 product flop per iteration
+// Smallest N whose Gaussian / Matern product runs as the slot's own tcgen05
+// launch (one CTA per SM over the slot's tiles) instead of a grouped launch.
+constexpr int64_t SERVE_TC5_MIN_N = 32768;
 
 struct Lane {
   cudaStream_t s = nullptr;
@@ -754,6 +780,7 @@ struct Lane {
   bool dirty = true;                    // slot set changed since the table was written
   bool busy = false;                    // a step is in flight
   std::vector<Slot *> members;          // slots of the step in flight
+  std::vector<Tc5Job> tc5;              // tcgen05 products of the table's slots
 };
 }  // namespace krr
 
@@ -813,6 +840,14 @@ static void table_add(ServeTable *T, const ServeSlotDesc &d) {
     T->nclasses = 0;
   }
   T->slot[s] = d;
+  T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
+  T->tt_off[s + 1] = T->tt_off[s] + d.nbt * ((d.rank + SERVE_TT_COLS - 1) / SERVE_TT_COLS);
+  T->ttr_off[s + 1] = T->ttr_off[s] + (d.rank > 0 ? d.rank * d.m : 0);
+  T->tri_off[s + 1] = T->tri_off[s] + d.rank;
+  T->col_off[s + 1] = T->col_off[s] + d.m;
+  T->nslots = s + 1;
+  // a tcgen05 slot's product is a launch of its own (Tc5Job)
+  if (d.tc5) return;
   // the slot joins the product launch of its variant
   int c = 0;
   while (c < T->nclasses && T->cls[c].variant != d.variant) ++c;
@@ -826,12 +861,6 @@ static void table_add(ServeTable *T, const ServeSlotDesc &d) {
   C.slot[C.nslots] = s;
   C.off[C.nslots + 1] = C.off[C.nslots] + d.row_tiles * d.splits * d.halves;
   C.nslots += 1;
-  T->vec_off[s + 1] = T->vec_off[s] + d.nbv;
-  T->tt_off[s + 1] = T->tt_off[s] + d.nbt * ((d.rank + SERVE_TT_COLS - 1) / SERVE_TT_COLS);
-  T->ttr_off[s + 1] = T->ttr_off[s] + (d.rank > 0 ? d.rank * d.m : 0);
-  T->tri_off[s + 1] = T->tri_off[s] + d.rank;
-  T->col_off[s + 1] = T->col_off[s] + d.m;
-  T->nslots = s + 1;
 }
 
 template <typename T>
@@ -868,14 +897,18 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   const int M = serve_pad_m(m);
   // inner products on the tensor cores where the tile code has a variant and
   // the coordinates fit the half split
-  if (product_path() != 1) KRR_TRY(prepare_points_tc(Xd, s, sl->P32, false));
+  // large slots take the single-problem tcgen05 product as a launch of their own
+  const bool want_tc5 = product_path() == 0 && N >= SERVE_TC5_MIN_N;
+  if (product_path() != 1) KRR_TRY(prepare_points_tc(Xd, s, sl->P32, want_tc5));
+  const bool tc5 = want_tc5 && sl->P32.nh5 > 0;
   const int kc = sl->P32.kc16;
   const int rank = sl->core ? sl->core->rank : 0;
   const int64_t chunk = serve_chunk(N);
   // a tensor-core M = 16 slot runs its product as two halves of 8 columns
   const int rows = kc > 0 ? kmvtc_rows_per_cta(kc, M > 8 ? 8 : M)
                           : KMV_THREADS * kmv32_rows_per_thread(dp, M);
-  D.halves = (kc > 0 && M > 8) ? 2 : 1;
+  D.halves = (kc > 0 && M > 8 && !tc5) ? 2 : 1;
+  D.tc5 = tc5 ? 1 : 0;
   D.xt = sl->P32.xt.p;
   D.cn = sl->P32.cn.p;
   D.xs = kc > 0 ? sl->P32.xs16.p : nullptr;
@@ -887,9 +920,9 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   D.M = M;
   D.dp = dp;
   D.kern = sl->kern;
-  D.variant = kc > 0 ? serve_variant_tc(sl->kern, kc, M) : serve_variant(sl->kern, dp, M);
-  D.row_tiles = (int)((N + rows - 1) / rows);
-  D.splits = (int)((N + chunk - 1) / chunk);
+  D.variant = tc5 ? -1 : kc > 0 ? serve_variant_tc(sl->kern, kc, M) : serve_variant(sl->kern, dp, M);
+  D.row_tiles = tc5 ? 0 : (int)((N + rows - 1) / rows);
+  D.splits = tc5 ? 1 : (int)((N + chunk - 1) / chunk);
   const double lambda = sl->mu * (double)N;
   D.lam32 = (float)lambda;
   D.inv_lam = 1.0 / lambda;
@@ -950,6 +983,11 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
     KRR_CUDA_TRY(cudaMemcpyAsync(sl->r64, sl->Y64, nm * 8, cudaMemcpyDeviceToDevice, s));
   }
   KRR_CUDA_TRY(cudaMemsetAsync(D.p, 0, nm * 4, s));
+  // a first tcgen05 product here sizes its scratch and raises the kernel's
+  // shared-memory limit, so that the lane's captured steps allocate nothing
+  if (D.tc5)
+    KRR_TRY(kmv_tc5(sl->P32, sl->P32, 0.0f, false, D.p, N, m, D.part, N, s, sl->t5scratch,
+                    true));
   KRR_CUDA_TRY(cudaStreamSynchronize(s));
   if (sl->resume) {
     std::vector<double>().swap(sl->saved_alpha);
@@ -961,6 +999,9 @@ static krr_status build_slot(krr_server *S, Slot *sl, cudaStream_t s) {
   rebind(sl->P32.mean, S->s_free);
   rebind(sl->P32.xs16, S->s_free);
   rebind(sl->P32.cs16, S->s_free);
+  rebind(sl->P32.xa5, S->s_free);
+  rebind(sl->P32.xb5, S->s_free);
+  rebind(sl->t5scratch, S->s_free);
   rebind(sl->Pff.xh, S->s_free);
   rebind(sl->Pff.xl, S->s_free);
   rebind(sl->Pff.ch, S->s_free);
@@ -1067,6 +1108,10 @@ static void release_device(krr_server *S, Slot *sl) {
   sl->P32.xs16.release();
   sl->P32.cs16.release();
   sl->P32.kc16 = 0;
+  sl->P32.xa5.release();
+  sl->P32.xb5.release();
+  sl->P32.nh5 = 0;
+  sl->t5scratch.release();
   sl->Pff.xh.release();
   sl->Pff.xl.release();
   sl->Pff.ch.release();
@@ -1292,8 +1337,9 @@ static void admit(krr_server *S) {
 static krr_status launch_step(krr_server *S, Lane &L) {
   const int U = S->cfg.iters_per_step;
   const ServeTable *Th = L.table_host;
-  const unsigned long long kernels =
-      (unsigned long long)U * (SERVE_KERNELS_PER_ITER - 1 + Th->nclasses);
+  unsigned long long per_iter = SERVE_KERNELS_PER_ITER - 1 + Th->nclasses;
+  for (const Tc5Job &j : L.tc5) per_iter += tc5_job_kernels(j);
+  const unsigned long long kernels = (unsigned long long)U * per_iter;
   if (S->cfg.use_graph) {
     if (!L.graph) {
       // the launch sequence depends on the variants present: captured again
@@ -1301,7 +1347,7 @@ static krr_status launch_step(krr_server *S, Lane &L) {
       cudaGraph_t g = nullptr;
       set_launch_counting(false);
       KRR_CUDA_TRY(cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal));
-      krr_status st = serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s);
+      krr_status st = serve_launch_iterations(L.table_dev, Th, L.branches, L.tc5, U, L.s);
       cudaError_t e = cudaStreamEndCapture(L.s, &g);
       set_launch_counting(true);
       if (st != KRR_OK) {
@@ -1325,9 +1371,9 @@ static krr_status launch_step(krr_server *S, Lane &L) {
       pe.ev.push_back(e);
     }
     pe.next = 0;
-    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s, &pe));
+    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, L.tc5, U, L.s, &pe));
   } else {
-    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, U, L.s));
+    KRR_TRY(serve_launch_iterations(L.table_dev, Th, L.branches, L.tc5, U, L.s));
   }
   S->steps += 1;
   S->step_kernels += (int64_t)kernels;
@@ -1408,7 +1454,12 @@ static krr_status server_step(krr_server *S, int64_t *unfinished) {
     if (L.dirty) {
       ServeTable *T = L.table_host;
       T->nslots = 0;
-      for (Slot *sl : inner) table_add(T, sl->desc);
+      L.tc5.clear();
+      for (Slot *sl : inner) {
+        table_add(T, sl->desc);
+        if (sl->desc.tc5)
+          L.tc5.push_back({&sl->P32, sl->desc.p, sl->desc.part, sl->m, &sl->t5scratch});
+      }
       KRR_CUDA_TRY(cudaMemcpyAsync(L.table_dev, T, table_bytes(T->nslots),
                                    cudaMemcpyHostToDevice, L.s));
       L.dirty = false;

@@ -67,6 +67,8 @@ struct ServeSlotDesc {
   const float *cs;   // N
   int kc;            // 16-coordinate blocks, 0 for the FMA product
   int halves;        // product items per (row tile, split): 2 for a tensor-core M = 16
+  int tc5;           // 1: the slot's product is its own tcgen05 launch (large
+                     // Gaussian / Matern slots), writing part as one split
   float *part;       // splits x M x N partial sums
   int64_t N;
   int64_t chunk;     // columns per split

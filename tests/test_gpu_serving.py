@@ -253,3 +253,40 @@ def test_escalated_request(K):
         done = {ids[d["id"]]: d for d in srv.drain()}
     np.testing.assert_array_equal(done["hard"]["alpha"], res["alpha"])
     assert done["easy"]["status_name"] == "KRR_OK"
+
+
+def test_large_requests_on_tcgen05_product(K, data):
+    """Requests of N >= 32768 with the Gaussian or Matern kernel take the
+    single-problem tcgen05 product as launches of their own (m = 10 as groups
+    of 8 and 2 right-hand sides): each result is the same bit for bit alone
+    and among other requests, and sampled rows of the oracle's float64
+    residual meet the tolerance."""
+    big = [dict(N=40_000, d=16, kernel=O.GAUSSIAN, sigma=0.7, mu=1e-6, m=4, seed=31, k=400),
+           dict(N=36_000, d=8, kernel=O.MATERN52, sigma=1.0, mu=1e-5, m=10, seed=32, k=360)]
+    bdata = [make_serving_request(r) for r in big]
+    alone_big = []
+    with K.KrrServer(max_slots=4, iters_per_step=4) as srv:
+        for r, (X, Y) in zip(big, bdata):
+            submit(srv, r, X, Y)
+            (res,) = srv.drain()
+            assert res["status_name"] == "KRR_OK", res
+            alone_big.append(res)
+    with K.KrrServer(max_slots=6, iters_per_step=4) as srv:
+        ids = {submit(srv, r, X, Y): i for i, (r, (X, Y)) in enumerate(zip(big, bdata))}
+        small = {submit(srv, REQS[i], *data[i]): None for i in (0, 2)}
+        done = srv.drain()
+    assert len(done) == len(ids) + len(small)
+    for res in done:
+        if res["id"] not in ids:
+            assert res["status_name"] == "KRR_OK"
+            continue
+        i = ids[res["id"]]
+        np.testing.assert_array_equal(res["alpha"], alone_big[i]["alpha"])
+        assert res["iters"] == alone_big[i]["iters"]
+    for r, (X, Y), res in zip(big, bdata, alone_big):
+        rows = np.sort(np.random.default_rng(1).choice(r["N"], 48, replace=False))
+        lam = r["mu"] * r["N"]
+        Rs = Y[:, rows] - O.kmatvec(X, r["kernel"], r["sigma"], lam, res["alpha"], rows)
+        ynorm = np.linalg.norm(Y, axis=1)
+        assert np.all(np.abs(Rs) <= TOL * ynorm[:, None]), r
+        assert res["rel_residual"] <= TOL
