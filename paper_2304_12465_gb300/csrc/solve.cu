@@ -33,6 +33,10 @@ static krr_status scale(const T *in, T *out, int64_t n, double a, cudaStream_t s
 
 // Relative tolerance floor of one inner float32 PCG solve.
 constexpr double kInnerFloor = 1e-4;
+// Share of the outer tolerance an inner solve aims at: the true residual
+// after the correction follows the inner recursive one to within the float32
+// products' rounding, so half the remaining need leaves a factor-2 margin.
+constexpr double kInnerTarget = 0.5;
 
 struct RefineStats {
   int iters = 0, outer = 0, products32 = 0, products64 = 0;
@@ -234,7 +238,7 @@ krr_status refine_solve(const PcgOps<float> &ops,
     if (outer >= max_outer || budget <= 0) break;
     if (outer > 0 && worst > 0.5 * prev_worst) break;  // refinement stagnated
     prev_worst = worst;
-    // inner tolerances: aim a little below what the outer test needs, but
+    // inner tolerances: aim below what the outer test needs (kInnerTarget), but
     // stop each float32 solve at kInnerFloor -- below that its recursive
     // residual keeps falling while the true residual is held up by float32
     // products, so the iterations are better spent after the next float64
@@ -243,7 +247,7 @@ krr_status refine_solve(const PcgOps<float> &ops,
     KRR_TRY(convert_f64_to_f32(r64.p, b32.p, N * m, s));
     for (int c = 0; c < m; ++c) {
       const double rel = (yn[c] > 0) ? rn[c] / yn[c] : 0.0;
-      inner_tol[c] = (rel > tol) ? std::max(0.3 * tol / rel, kInnerFloor) : 1.0;
+      inner_tol[c] = (rel > tol) ? std::max(kInnerTarget * tol / rel, kInnerFloor) : 1.0;
       // columns already converged get a zero right-hand side (no work)
       if (!(rel > tol))
         KRR_CUDA_TRY(cudaMemsetAsync(b32.p + (int64_t)c * N, 0, sizeof(float) * N, s));
