@@ -161,11 +161,15 @@ gemm_sub_ff_kernel(int M, int N, int K, const double *__restrict__ A, int64_t sa
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
-  float sh[4][4], sl[4][4];
+  // outputs (row ty + 16 r, columns tx + 16 (2 h) and tx + 16 (2 h + 1)) as
+  // packed pairs: every step below is one FMUL2 / FFMA2 / FADD2 for two
+  // outputs, x - y written as fma(y, -1, x) (the same single rounding)
+  float2 sh[4][2], sl[4][2];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.0f;
+    for (int h = 0; h < 2; ++h) sh[r][h] = sl[r][h] = make_float2(0.0f, 0.0f);
+  const float2 m1 = make_float2(-1.0f, -1.0f);
   const bool a_kfast = (sak == 1 && sai != 1);
   const bool b_kfast = (sbk == 1 && sbj != 1);
   for (int k0 = 0; k0 < K; k0 += GB_K) {
@@ -196,30 +200,37 @@ gemm_sub_ff_kernel(int M, int N, int K, const double *__restrict__ A, int64_t sa
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GB_K; ++kk) {
-      float ah[4], al[4], bh[4], bl[4];
+      float2 ah[4], nah[4], nal[4], bh[2], bl[2];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        ah[r] = Ah[kk][ty + 16 * r];
-        al[r] = Al[kk][ty + 16 * r];
+        const float a = Ah[kk][ty + 16 * r], al = Al[kk][ty + 16 * r];
+        ah[r] = make_float2(a, a);
+        nah[r] = make_float2(-a, -a);
+        nal[r] = make_float2(-al, -al);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        bh[c] = Bh[kk][tx + 16 * c];
-        bl[c] = Bl[kk][tx + 16 * c];
+      for (int h = 0; h < 2; ++h) {
+        bh[h] = make_float2(Bh[kk][tx + 32 * h], Bh[kk][tx + 32 * h + 16]);
+        bl[h] = make_float2(Bl[kk][tx + 32 * h], Bl[kk][tx + 32 * h + 16]);
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float p = __fmul_rn(ah[r], bh[c]);
-          float e = __fmaf_rn(ah[r], bh[c], -p);
-          e = __fmaf_rn(ah[r], bl[c], e);
-          e = __fmaf_rn(al[r], bh[c], e);
-          const float t = __fadd_rn(sh[r][c], p);
-          const float z = __fsub_rn(t, sh[r][c]);
-          const float err = __fadd_rn(__fsub_rn(sh[r][c], __fsub_rn(t, z)), __fsub_rn(p, z));
-          sh[r][c] = t;
-          sl[r][c] = __fadd_rn(sl[r][c], __fadd_rn(err, e));
+        for (int h = 0; h < 2; ++h) {
+          // p = hi_a hi_b; en = -(hi_a hi_b - p) - hi_a lo_b - lo_a hi_b (the
+          // negated product error and cross terms, each step exact or
+          // rounded once as in the scalar form)
+          const float2 p = __fmul2_rn(ah[r], bh[h]);
+          float2 en = __ffma2_rn(nah[r], bh[h], p);
+          en = __ffma2_rn(nah[r], bl[h], en);
+          en = __ffma2_rn(nal[r], bh[h], en);
+          // TwoSum(sh, p)
+          const float2 t = __fadd2_rn(sh[r][h], p);
+          const float2 z = __ffma2_rn(sh[r][h], m1, t);
+          const float2 tz = __ffma2_rn(z, m1, t);
+          const float2 err = __fadd2_rn(__ffma2_rn(tz, m1, sh[r][h]), __ffma2_rn(z, m1, p));
+          sh[r][h] = t;
+          sl[r][h] = __fadd2_rn(sl[r][h], __ffma2_rn(en, m1, err));
         }
     }
     __syncthreads();
@@ -228,23 +239,27 @@ gemm_sub_ff_kernel(int M, int N, int K, const double *__restrict__ A, int64_t sa
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float t = __fadd_rn(sh[r][c], sl[r][c]);
-        const float z = __fsub_rn(t, sh[r][c]);
-        sl[r][c] = __fadd_rn(__fsub_rn(sh[r][c], __fsub_rn(t, z)), __fsub_rn(sl[r][c], z));
-        sh[r][c] = t;
+      for (int h = 0; h < 2; ++h) {
+        const float2 t = __fadd2_rn(sh[r][h], sl[r][h]);
+        const float2 z = __ffma2_rn(sh[r][h], m1, t);
+        sl[r][h] = __fadd2_rn(__ffma2_rn(__ffma2_rn(z, m1, t), m1, sh[r][h]),
+                              __ffma2_rn(z, m1, sl[r][h]));
+        sh[r][h] = t;
       }
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
-      if (gi < M && gj < N) {
-        double *dst = C + (int64_t)gi + (int64_t)gj * ldc;
-        *dst = *dst - ((double)sh[r][c] + (double)sl[r][c]);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int gi = i0 + ty + 16 * r, gj = j0 + tx + 32 * h + 16 * e;
+        if (gi < M && gj < N) {
+          double *dst = C + (int64_t)gi + (int64_t)gj * ldc;
+          const float hi = e ? sh[r][h].y : sh[r][h].x, lo = e ? sl[r][h].y : sl[r][h].x;
+          *dst = *dst - ((double)hi + (double)lo);
+        }
       }
-    }
 }
 
 krr_status gemm_sub_ff(const Gemm<double> &g, cudaStream_t s) {

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256)
 tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__restrict__ v,
               int m, const T *__restrict__ R, double inv_lambda, T *__restrict__ Z) {
   constexpr int LCH = 256;
-  constexpr int LU = 16;
+  constexpr int LU = 32;
   __shared__ T sv[LCH][M];
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool ok = n < N;
@@ -181,8 +181,11 @@ tall_n_kernel(const T *__restrict__ F, int64_t N, int rank, const double *__rest
     }
   }
   if (ok) {
-    for (int c = 0; c < m; ++c)
-      Z[(int64_t)c * N + n] = (T)(((double)R[(int64_t)c * N + n] - (double)acc[c]) * inv_lambda);
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      if (c < m)
+        Z[(int64_t)c * N + n] =
+            (T)(((double)R[(int64_t)c * N + n] - (double)acc[c]) * inv_lambda);
   }
 }
 
