@@ -57,6 +57,9 @@ def parse():
                     help="skip the short runs of the other configurations (c1, c3, c4)")
     ap.add_argument("--no-pcg-graphs", action="store_true",
                     help="step the PCG iterations one launch at a time (no CUDA graphs)")
+    ap.add_argument("--product-variant", type=int, default=0,
+                    help="force an epilogue variant of the tcgen05 product (0: autotuned "
+                         "or default)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the product's default tile instead of tuning it in the warm-up")
     ap.add_argument("--no-fp64", action="store_true",
@@ -164,7 +167,8 @@ class ClockSampler:
 # tcgen05 kernel.  Any other shape or tile has no capture and reports None; a
 # change to the kernel invalidates the entry until it is captured again.
 KMV32_TRAFFIC = {("fma", 0, 100_000, 16, 4, 50): 8_748_117 + 16_672_768,
-                 ("tensor", 0, 100_000, 16, 4, 3): 22_435_840 + 0}
+                 ("tensor", 0, 100_000, 16, 4, 1): 22_511_616 + 0,
+                 ("tensor", 0, 100_000, 16, 4, 3): 22_520_320 + 0}
 
 # Register-operand mma.sync (m16n8k16, f16 inputs, f32 accumulator) measured by
 # this repository's probe on this machine's GB300 (independent MMAs, 2-8 CTAs of
@@ -856,6 +860,7 @@ def run_kmv(args):
     dist, rank, world = dist_setup(args.gpus)
     K.load()
     K.krr_set_product_path(args.product_path)
+    K.krr_set_product_variant(args.product_variant)
     w = make_c2_mixed(n=args.n)
     dev = torch.device("cuda", torch.cuda.current_device())
     X = torch.from_numpy(w.X).to(dev)
@@ -885,8 +890,10 @@ def run_kmv(args):
     call_ms = float(np.median(ms))
     kmv_ms = float(np.median(launch_ms))
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    tile = (K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)[0]
-            if args.product_path == "tensor" else K.krr_autotune_choice(w.kernel, w.d, w.m, w.N))
+    if args.product_path == "tensor":
+        tile = args.product_variant or K.krr_autotune_variant(w.kernel, w.d, w.m, w.N)[0] or 3
+    else:
+        tile = K.krr_autotune_choice(w.kernel, w.d, w.m, w.N)
     result = {"metric": "fused product (A + lambda I) V launch time", "value": kmv_ms,
               "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
