@@ -57,6 +57,8 @@ def parse():
                     help="skip the short runs of the other configurations (c1, c3, c4)")
     ap.add_argument("--no-pcg-graphs", action="store_true",
                     help="step the PCG iterations one launch at a time (no CUDA graphs)")
+    ap.add_argument("--kmv-prec", default="mixed", choices=["mixed", "ff"],
+                    help="kmv workload: the float32 product (mixed) or the float-float one")
     ap.add_argument("--product-variant", type=int, default=0,
                     help="force an epilogue variant of the tcgen05 product (0: autotuned "
                          "or default)")
@@ -867,23 +869,24 @@ def run_kmv(args):
     gen = torch.Generator(device=dev).manual_seed(5)
     V = torch.randn((w.m, w.N), dtype=torch.float64, device=dev, generator=gen)
     for _ in range(args.warmup):
-        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec=args.kmv_prec)
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
+    which = 2 if args.kmv_prec == "ff" else 0   # product timer: float-float or float32
     K.krr_set_profiling(True)
-    K.krr_profile_collect(0)
+    K.krr_profile_collect(which)
     stream = torch.cuda.current_stream()
     ms, launch_ms = [], []
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec="mixed")
+        K.krr_kmatvec(X, w.kernel, w.sigma, w.lam, V, prec=args.kmv_prec)
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-        t, n = K.krr_profile_collect(0)
+        t, n = K.krr_profile_collect(which)
         launch_ms.append(t / max(n, 1))
     K.krr_set_profiling(False)
     clk = clocks.stop()
@@ -904,7 +907,8 @@ def run_kmv(args):
               "note": "value: the product kernel's launch (CUDA events around it on the "
                       "launching stream, median over steps); call_ms adds the point "
                       "preparation, the reduction and the float64 conversions of krr_kmatvec",
-              "roofline": product_roofline(args.product_path, w, kmv_ms, tile, sm_max),
+              "roofline": (product_roofline(args.product_path, w, kmv_ms, tile, sm_max)
+                           if args.kmv_prec == "mixed" else None),
               "clocks": clk}
     if rank == 0:
         print(json.dumps(result), flush=True)
