@@ -58,3 +58,15 @@ def test_mma_sync_path_uses_its_own_tensor_peak():
 def test_laplace_has_no_tensor_path():
     r = bench.product_roofline("tensor", wl(1, 16, 4), 5.0, 50, 2070.0)
     assert r["kernel"].startswith("kmv32_kernel") and "tensor" not in r["pipes"]
+
+
+def test_traffic_reported_for_captured_tiles_only():
+    # the ncu DRAM bytes of the tcgen05 product at the headline shape were
+    # captured for the two epilogue variants the autotuner picks there; any
+    # other tile or shape reports None
+    w = wl(0, 16, 4)
+    for tile in (1, 3):
+        r = bench.product_roofline("tensor", w, 2.31, tile, 2070.0)
+        assert r["traffic"] is not None and 20e6 < r["traffic"] < 25e6
+    assert bench.product_roofline("tensor", w, 2.31, 2, 2070.0)["traffic"] is None
+    assert bench.product_roofline("tensor", wl(0, 16, 4, N=50_000), 0.6, 3, 2070.0)["traffic"] is None
