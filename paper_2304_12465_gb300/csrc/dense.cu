@@ -274,8 +274,11 @@ krr_status gemm_sub_ff(const Gemm<double> &g, cudaStream_t s) {
 
 // ------------------------------------------------------------ Gram (F^T F)
 // Lower-triangular output tiles only.  float input: each K tile of GB_K
-// products is summed in float32, then added to float64 accumulators (one
-// float64 add per GB_K float32 FMAs); double input: float64 throughout.
+// products is summed in float32, then added to a float-float accumulator
+// (Knuth's TwoSum, the rounding errors gathered in a float32 correction that
+// is folded back every 8 tiles) -- float64 adds, at a small fraction of the
+// float32 rate on this GPU, bounded the kernel; double input: float64
+// throughout.
 template <typename T>
 __global__ void __launch_bounds__(G_THREADS)
 gram_lower_kernel(const T *__restrict__ F, int64_t N, int r, int kslice,
@@ -290,12 +293,18 @@ gram_lower_kernel(const T *__restrict__ F, int64_t N, int r, int kslice,
   const int i0 = ti * GB_M, j0 = tj * GB_N;
   const int64_t kb = (int64_t)blockIdx.y * kslice;
   const int64_t ke = min(N, kb + kslice);
+  constexpr bool FLT = sizeof(T) == 4;
   double acc[4][4];
+  float sh[4][4], sl[4][4];   // float-float accumulators (float input)
   T acc32[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) {
+      acc[a][b] = 0.0;
+      sh[a][b] = sl[a][b] = 0.0f;
+    }
+  int chunk = 0;
   for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
 #pragma unroll
     for (int e = 0; e < (GB_M * GB_K) / G_THREADS; ++e) {
@@ -322,10 +331,32 @@ gram_lower_kernel(const T *__restrict__ F, int64_t N, int r, int kslice,
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc32[a][b] = fma(av[a], bv[b], acc32[a][b]);
     }
+    if constexpr (FLT) {
+      ++chunk;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += (double)acc32[a][b];
+        for (int b = 0; b < 4; ++b) {
+          const float c = (float)acc32[a][b];
+          const float t = __fadd_rn(sh[a][b], c);
+          const float z = __fsub_rn(t, sh[a][b]);
+          const float err = __fadd_rn(__fsub_rn(sh[a][b], __fsub_rn(t, z)), __fsub_rn(c, z));
+          sh[a][b] = t;
+          sl[a][b] = __fadd_rn(sl[a][b], err);
+          if ((chunk & 7) == 0) {
+            // fold the correction back (TwoSum), keeping it below an ulp of the sum
+            const float t2 = __fadd_rn(sh[a][b], sl[a][b]);
+            const float z2 = __fsub_rn(t2, sh[a][b]);
+            sl[a][b] = __fadd_rn(__fsub_rn(sh[a][b], __fsub_rn(t2, z2)), __fsub_rn(sl[a][b], z2));
+            sh[a][b] = t2;
+          }
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += (double)acc32[a][b];
+    }
     __syncthreads();
   }
   double *o = part + (int64_t)blockIdx.y * r * r;
@@ -334,7 +365,9 @@ gram_lower_kernel(const T *__restrict__ F, int64_t N, int r, int kslice,
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
-      if (gi < r && gj <= gi) o[(int64_t)gi + (int64_t)gj * r] = acc[a][b];
+      if (gi < r && gj <= gi)
+        o[(int64_t)gi + (int64_t)gj * r] =
+            FLT ? (double)sh[a][b] + (double)sl[a][b] : acc[a][b];
     }
 }
 
