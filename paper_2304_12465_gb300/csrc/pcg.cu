@@ -110,26 +110,26 @@ __global__ void tall_t_reduce_kernel(const double *__restrict__ part, int nb, in
 // sums are added in warp order.
 constexpr int TRI_THREADS = 128;
 
-template <bool UPPER>
+template <bool UPPER, int M>
 __global__ void __launch_bounds__(TRI_THREADS)
 tri_gemv_kernel(const double *__restrict__ Mt, int rank, const double *__restrict__ x, int m,
                 double *__restrict__ out) {
-  __shared__ double red[TRI_THREADS / 32][16];
+  __shared__ double red[TRI_THREADS / 32][M];
   const int i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc[16];
+  double acc[M];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int c = 0; c < M; ++c) acc[c] = 0.0;
   const double *col = Mt + (int64_t)i * rank;
   const int lo = UPPER ? i : 0, hi = UPPER ? rank : i + 1;
   for (int l = lo + threadIdx.x; l < hi; l += TRI_THREADS) {
     const double w = col[l];
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
+    for (int c = 0; c < M; ++c)
       if (c < m) acc[c] = fma(w, x[(int64_t)c * rank + l], acc[c]);
   }
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
+  for (int c = 0; c < M; ++c) {
     if (c < m) {
       const double v = warp_sum(acc[c]);
       if (lane == 0) red[warp][c] = v;
@@ -141,6 +141,21 @@ tri_gemv_kernel(const double *__restrict__ Mt, int rank, const double *__restric
 #pragma unroll
     for (int w = 0; w < TRI_THREADS / 32; ++w) t += red[w][threadIdx.x];
     out[(int64_t)threadIdx.x * rank + i] = t;
+  }
+}
+
+// Launches tri_gemv_kernel specialised on m rounded up to 1, 2, 4, 8 or 16
+// (a runtime column count costs the unrolled loops their full 16-wide work).
+template <bool UPPER>
+static void launch_tri_gemv(const double *Mt, int rank, const double *x, int m, double *out,
+                            cudaStream_t s) {
+  const int p = m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
+  switch (p) {
+    case 1: tri_gemv_kernel<UPPER, 1><<<rank, TRI_THREADS, 0, s>>>(Mt, rank, x, m, out); break;
+    case 2: tri_gemv_kernel<UPPER, 2><<<rank, TRI_THREADS, 0, s>>>(Mt, rank, x, m, out); break;
+    case 4: tri_gemv_kernel<UPPER, 4><<<rank, TRI_THREADS, 0, s>>>(Mt, rank, x, m, out); break;
+    case 8: tri_gemv_kernel<UPPER, 8><<<rank, TRI_THREADS, 0, s>>>(Mt, rank, x, m, out); break;
+    default: tri_gemv_kernel<UPPER, 16><<<rank, TRI_THREADS, 0, s>>>(Mt, rank, x, m, out); break;
   }
 }
 
@@ -665,7 +680,7 @@ __global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__
 krr_status tri_apply_lower(const double *Wt, int rank, const double *t, int m, double *u,
                            cudaStream_t s) {
   if (rank == 0) return KRR_OK;
-  tri_gemv_kernel<false><<<rank, TRI_THREADS, 0, s>>>(Wt, rank, t, m, u);
+  launch_tri_gemv<false>(Wt, rank, t, m, u, s);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
@@ -673,7 +688,7 @@ krr_status tri_apply_lower(const double *Wt, int rank, const double *t, int m, d
 krr_status tri_apply_lower_t(const double *W, int rank, const double *u, int m, double *v,
                              cudaStream_t s) {
   if (rank == 0) return KRR_OK;
-  tri_gemv_kernel<true><<<rank, TRI_THREADS, 0, s>>>(W, rank, u, m, v);
+  launch_tri_gemv<true>(W, rank, u, m, v, s);
   KRR_LAUNCH_CHECK();
   return KRR_OK;
 }
