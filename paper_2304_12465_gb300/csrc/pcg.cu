@@ -429,16 +429,19 @@ __global__ void pcg_init_kernel(const double *__restrict__ part_bb,
   }
 }
 
-// x += alpha p; r -= alpha q
+// x += alpha p; r -= alpha q (column by column: no per-element division)
 template <typename T>
 __global__ void pcg_update_kernel(T *__restrict__ x, T *__restrict__ r,
                                   const T *__restrict__ p, const T *__restrict__ q, int64_t N,
                                   int m, const PcgScalars *__restrict__ sc) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / N);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int c = 0; c < m; ++c) {
     const double a = sc->alpha[c];
-    if (a != 0.0) {
+    if (a == 0.0) continue;
+    const int64_t off = (int64_t)c * N;
+    for (int64_t i = i0; i < N; i += stride) {
+      const int64_t e = off + i;
       x[e] = (T)((double)x[e] + a * (double)p[e]);
       r[e] = (T)((double)r[e] - a * (double)q[e]);
     }
@@ -449,10 +452,16 @@ __global__ void pcg_update_kernel(T *__restrict__ x, T *__restrict__ r,
 template <typename T>
 __global__ void pcg_dir_kernel(T *__restrict__ p, const T *__restrict__ z, int64_t N, int m,
                                const PcgScalars *__restrict__ sc) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / N);
-    if (sc->active[c]) p[e] = (T)((double)z[e] + sc->beta[c] * (double)p[e]);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int c = 0; c < m; ++c) {
+    if (!sc->active[c]) continue;
+    const double b = sc->beta[c];
+    const int64_t off = (int64_t)c * N;
+    for (int64_t i = i0; i < N; i += stride) {
+      const int64_t e = off + i;
+      p[e] = (T)((double)z[e] + b * (double)p[e]);
+    }
   }
 }
 
@@ -535,7 +544,7 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
     KRR_LAUNCH_CHECK();
     pcg_alpha_kernel<<<1, 32 * m, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
     KRR_LAUNCH_CHECK();
-    pcg_update_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(x, r.p, p.p, q.p, N, m, sc.p);
+    pcg_update_kernel<T><<<vec_grid(N), 256, 0, st>>>(x, r.p, p.p, q.p, N, m, sc.p);
     KRR_LAUNCH_CHECK();
     dots_kernel<T><<<RED_BLOCKS, 256, 0, st>>>(r.p, r.p, N, m, part1.p);
     KRR_LAUNCH_CHECK();
@@ -550,7 +559,7 @@ krr_status pcg_run(const PcgOps<T> &ops, int64_t N, int m, const T *b, T *x,
     KRR_LAUNCH_CHECK();
     pcg_beta_kernel<<<1, 32 * m, 0, st>>>(part1.p, RED_BLOCKS, m, sc.p);
     KRR_LAUNCH_CHECK();
-    pcg_dir_kernel<T><<<vec_grid(N * m), 256, 0, st>>>(p.p, z.p, N, m, sc.p);
+    pcg_dir_kernel<T><<<vec_grid(N), 256, 0, st>>>(p.p, z.p, N, m, sc.p);
     KRR_LAUNCH_CHECK();
     return KRR_OK;
   };
