@@ -168,3 +168,16 @@ def test_server_checkpoint_validation(lib):
     _einval(lib.krr_server_import(None, None, 0, None, None, None, C.byref(rid)), lib, "NULL")
     pr = N_.RequestProgress()
     _einval(lib.krr_server_progress(None, 0, C.byref(pr)), lib, "NULL")
+
+
+def test_bounded_wait_budget_validated_before_any_launch(lib):
+    """krr_check_bounded_wait refuses a budget outside 0 .. 2^31 cycles with
+    KRR_EINVAL before it touches the device (no GPU needed)."""
+    _einval(lib.krr_check_bounded_wait(-1, None), lib, "wait budget")
+    _einval(lib.krr_check_bounded_wait((1 << 31) + 1, None), lib, "wait budget")
+
+
+def test_pcg_graph_switch_is_host_state(lib):
+    """krr_set_pcg_graphs only sets host state (callable without a GPU)."""
+    lib.krr_set_pcg_graphs(0)
+    lib.krr_set_pcg_graphs(1)
