@@ -31,8 +31,9 @@ krr_status gemm(const Gemm<T> &g, cudaStream_t s, int split_k = 1);
 krr_status gemm_sub_ff(const Gemm<double> &g, cudaStream_t s);
 
 // Lower triangle of C (r x r, column-major) = F^T F for F N x r column-major.
-// float F: float32 products summed in float32 over 16-term chunks, then in
-// float64; double F: float64.  The strict upper triangle of C is untouched.
+// float F: float32 products summed in float32 over 16-term chunks, the chunk
+// sums in float-float (slices added in float64); double F: float64.  The
+// strict upper triangle of C is untouched.
 template <typename T>
 krr_status gram_lower(const T *F, int64_t N, int r, double *C, cudaStream_t s);
 
